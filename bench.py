@@ -1,0 +1,355 @@
+"""Benchmark: pair-interactions/s of the element-model leap-frog step.
+
+One step = the whole hot path of one kick-drift-kick step of a binary system:
+opening kick + drift (FP64) with the FP32 copy and contact-grid binning, the
+O(N^2) FP32 pair term, the FP64 contact term, the closing kick.  Default
+workload: the 1,048,576-element binary (786,432 donor + 262,144 accretor
+elements, q = 0.2, uniform spheres of 0.95 r_L and 0.4 r_L), synthetic
+initial conditions from the library's seeded recipe.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload binary_1m|binary_64k|binary_1k]
+
+Under torchrun each rank runs its own copy of the workload (weak scaling, no
+data-path collective); rank 0 prints one JSON line.  ``--impl reference``
+times the FP64 CPU oracle on the host cores on a bounded sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# name: (n_donor, n_accretor, q, f_donor, f_accretor, eps, dt, expand_rate, expand_steps)
+WORKLOADS = {
+    "binary_1k": (512, 512, 0.5, 0.8, 0.5, 0.01, 1e-3, 0.0, -1),
+    "binary_64k": (49152, 16384, 0.3, 0.9, 0.5, 0.005, 5e-4, 0.25 / 10000, 10000),
+    "binary_1m": (786432, 262144, 0.2, 0.95, 0.4, 0.005, 2.5e-4, 0.0, -1),
+}
+METRIC = "pair-interactions/s"
+L2_BYTES = 129e6
+# MUFU (special-function unit) issue rate per SM per clock and MUFU ops per pair
+MUFU_PER_SM_CLK = 16
+MUFU_PER_PAIR = 2
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        uu = {r[0] for r in rows}
+        if self.uuid and any(self.uuid in u for u in uu):
+            rows = [r for r in rows if self.uuid in r[0]]
+        elif len(uu) > 1:
+            rows = rows  # all GPUs of the host
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        sm = np.array([num(r[1]) for r in rows])
+        smax = np.nanmax([num(r[2]) for r in rows])
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = []
+        for k, name in enumerate(names):
+            if any(r[5 + k].lower().startswith("active") for r in rows):
+                reasons.append(name)
+        return {"sm_mhz": float(np.nanmedian(sm)), "sm_max_mhz": float(smax),
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": float(np.nanmax([num(r[3]) for r in rows]))}
+
+
+def _workload(name):
+    nd, na, q, fd, fa, eps, dt, rate, cap = WORKLOADS[name]
+    return dict(n_donor=nd, n_accretor=na, q=q, f_donor=fd, f_accretor=fa, eps=eps, dt=dt,
+                expand_rate=rate, expand_steps=cap, sigma_v=1e-3, seed=0)
+
+
+def _config(name, w, extra=None):
+    n = w["n_donor"] + w["n_accretor"]
+    cfg = {"workload": name, "n": n, "n_donor": w["n_donor"], "n_accretor": w["n_accretor"],
+           "q": w["q"], "f_donor": w["f_donor"], "f_accretor": w["f_accretor"], "eps": w["eps"],
+           "dt": w["dt"], "beta": 0.5, "pairs_per_step": n * n}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+def _oracle_sample(w, target_s=10.0, seed_rows=11):
+    """Time the FP64 oracle's direct sum on a bounded sample of rows of the
+    workload (all j for each sampled i).  Returns pairs/s, cores, sample text."""
+    from oracle import oracle
+    import synth
+    x, v, m, R, g = oracle.make_ic(w["n_donor"], w["n_accretor"], w["q"], f_donor=w["f_donor"],
+                                   f_accretor=w["f_accretor"], sigma_v=w["sigma_v"],
+                                   seed=w["seed"])
+    n = len(m)
+    # calibrate on a small sample, then size the timed sample to ~target_s
+    rows = (synth.u01(seed_rows, 1, 64) * n).astype(np.int64)
+    t0 = time.perf_counter()
+    oracle.forces_rows(rows, x, v, m, R, g, G=1.0, eps=w["eps"], beta=0.5)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    nrows = int(min(n, max(64, 64 * target_s / dt)))
+    rows = (synth.u01(seed_rows, 2, nrows) * n).astype(np.int64)
+    t0 = time.perf_counter()
+    oracle.forces_rows(rows, x, v, m, R, g, G=1.0, eps=w["eps"], beta=0.5)
+    el = time.perf_counter() - t0
+    pairs = float(nrows) * n
+    return pairs / el, oracle.num_threads(), (
+        f"FP64 oracle direct sum (Eqs. 4-6) for {nrows} sampled elements against all {n} "
+        f"elements ({pairs:.3e} pairs, {el:.1f} s)"), (x, v, m, R, g), el
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    w = _workload(args.workload)
+    n = w["n_donor"] + w["n_accretor"]
+    from oracle import oracle
+    import synth
+    x, v, m, R, g = oracle.make_ic(w["n_donor"], w["n_accretor"], w["q"], f_donor=w["f_donor"],
+                                   f_accretor=w["f_accretor"], sigma_v=w["sigma_v"],
+                                   seed=w["seed"])
+    # rows per step: about 10 s of CPU work per step on the host cores, capped
+    rows = (synth.u01(3, 1, 32) * n).astype(np.int64)
+    t0 = time.perf_counter()
+    oracle.forces_rows(rows, x, v, m, R, g, G=1.0, eps=w["eps"], beta=0.5)
+    per_row = max((time.perf_counter() - t0) / 32, 1e-9)
+    budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    nrows = int(min(n, max(32, budget / per_row)))
+    times = []
+    for s in range(args.warmup + args.steps):
+        rows = (synth.u01(3, 10 + s, nrows) * n).astype(np.int64)
+        t0 = time.perf_counter()
+        oracle.forces_rows(rows, x, v, m, R, g, G=1.0, eps=w["eps"], beta=0.5)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    el = float(np.sum(times))
+    pairs = float(nrows) * n * args.steps
+    value = pairs / el
+    sample = (f"each step: FP64 oracle direct sum (Eqs. 4-6) for {nrows} sampled elements "
+              f"against all {n}")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(args.workload, w, {"sample_rows_per_step": nrows}),
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    from paper_2303_12166_gb300 import build as b
+    b.build()
+    from paper_2303_12166_gb300 import nbody as nbm
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    w = _workload(args.workload)
+    n = w["n_donor"] + w["n_accretor"]
+    stream = torch.cuda.Stream(device=dev)
+    desc = nbm.nb_desc_default(n_donor=w["n_donor"], n_accretor=w["n_accretor"], q=w["q"],
+                               f_donor=w["f_donor"], f_accretor=w["f_accretor"],
+                               expand_rate=w["expand_rate"], expand_steps=w["expand_steps"],
+                               sigma_v=w["sigma_v"], seed=w["seed"], stream=rank)
+    params = nbm.nb_params_default(eps=w["eps"], dt=w["dt"], beta=0.5,
+                                   force_prec=64 if args.fp64 else 32)
+    sysm = nbm.System(desc, params, stream=stream)
+
+    sysm.step(args.warmup)
+    sysm.sync()
+    sysm.profile(True)
+    sysm.profile_read(reset=True)
+
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    with ClockSampler(uuid if rank == 0 else None) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        sysm.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+    sysm.sync()
+    ms = ev0.elapsed_time(ev1)
+    prof = sysm.profile_read(reset=True)
+    sysm.profile(False)
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    pairs_step = float(n) * float(n)
+    value = pairs_step * args.steps * ws / (ms_max * 1e-3)
+
+    # roofline of the pair kernel: MUFU-bound pairs/s of the device
+    props = torch.cuda.get_device_properties(dev)
+    peaks, peak_src = _measured_peaks()
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_pairs = props.multi_processor_count * sm_max_mhz * 1e6 * MUFU_PER_SM_CLK / MUFU_PER_PAIR
+    pair_ms = prof["pair_ms"] / max(prof["pair_launches"], 1)
+    achieved = pairs_step / (pair_ms * 1e-3)
+
+    # end to end through the public API with host buffers: per step, upload
+    # the state, one step, read the state back
+    e2e = None
+    if not args.no_e2e:
+        xv, a, meta = sysm.get_state()
+        steps_e2e = max(1, min(args.steps, 3))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(steps_e2e):
+            sysm.set_state(xv, a, meta)
+            sysm.step(1)
+            xv, a, meta = sysm.get_state()
+        el = time.perf_counter() - t0
+        e2e = {"value": pairs_step * steps_e2e * ws / el, "unit": "pairs/s",
+               "h2d_bytes_per_step": int(n * (48 + 24)), "d2h_bytes_per_step": int(n * (48 + 24)),
+               "steps": steps_e2e}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, cores, sample, _, _ = _oracle_sample(w, target_s=args.cpu_seconds)
+        cpu = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+               "sample": sample}
+
+    working_set = sysm.info.device_bytes
+    sysm.close()
+    if rank == 0:
+        cfg = _config(args.workload, w, {
+            "force_prec": 64 if args.fp64 else 32,
+            "l2": f"no flush: per-step working set {working_set / 1e6:.0f} MB > L2 129 MB"
+            if working_set > L2_BYTES else f"working set {working_set / 1e6:.0f} MB",
+            "parallelism": f"replicas x{ws}"})
+        line = {
+            "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.fp64 else "f32", "data": "synthetic", "config": cfg,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_pairs,
+                         "unit": "pairs/s", "frac": achieved / peak_pairs, "traffic": None,
+                         "peak_basis": f"{props.multi_processor_count} SMs x {sm_max_mhz:.0f} MHz "
+                                       f"({peak_src} sm_max_mhz) x {MUFU_PER_SM_CLK} MUFU/clk/SM / "
+                                       f"{MUFU_PER_PAIR} MUFU per pair",
+                         "kernel": "pair_f32_kernel",
+                         "kernel_ms": pair_ms},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(prof["kernels"]),
+            "phase_ms": {"pair": prof["pair_ms"], "contact": prof["contact_ms"],
+                         "update": prof["update_ms"]},
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="binary_1m", choices=sorted(WORKLOADS))
+    ap.add_argument("--fp64", action="store_true", help="FP64 pair term (comparison path)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

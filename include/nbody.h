@@ -1,0 +1,233 @@
+/*
+ * nbody.h -- C ABI of the GB300 element-model N-body library.
+ *
+ * The model (Goderya et al., arXiv:2303.12166, methodology section): each
+ * star of a binary is a set of equal-mass spherical "elements" with a common
+ * radius per star.  Every pair of elements attracts with the softened law of
+ * Eq. 4; elements that overlap repel with a force proportional to their
+ * overlap volume (Eq. 5 while they approach, Eq. 6 -- reduced by beta --
+ * while they separate); a leap-frog integrator advances the system; the
+ * donor's element radius grows to push it through its Roche lobe (Eq. 3).
+ *
+ * Conventions for every call:
+ *   - Every call returns an nb_status; nothing throws across the ABI.  On
+ *     NB_ECUDA (or any other error) nb_last_error() returns a message for the
+ *     calling thread.
+ *   - Handles are opaque and owned by the library until nb_destroy /
+ *     nb_batch_destroy / nb_server_destroy.
+ *   - Input arrays are owned by the caller and copied during the call; they
+ *     are never retained.  Output arrays are allocated by the caller.
+ *   - "stream" arguments are cudaStream_t values passed as void*; 0 means the
+ *     legacy default stream.  All device work of a handle runs on its stream,
+ *     in stream order.
+ *   - The library allocates the device memory of a handle itself
+ *     (cudaMallocAsync on the handle's stream) and frees it on destroy.
+ *   - Units: any consistent set; the defaults use G = 1, total mass 1 and
+ *     separation 1, so the circular orbit has angular frequency 1.
+ *   - Particle order: donor elements first, indices [0, n_donor), then the
+ *     accretor's, [n_donor, n_donor + n_accretor).
+ */
+#ifndef NBODY_H
+#define NBODY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NB_ABI_VERSION 1
+
+typedef enum nb_status {
+    NB_OK = 0,
+    NB_EINVAL = 1,      /* invalid argument or parameter */
+    NB_ENOMEM = 2,      /* device or host allocation failed */
+    NB_EBUDGET = 3,     /* request does not fit the server's memory budget */
+    NB_ECUDA = 4,       /* CUDA runtime error; text in nb_last_error() */
+    NB_ENONFINITE = 5,  /* a position or velocity became NaN or infinite */
+    NB_ETIMEOUT = 6,    /* a device-side wait gave up (bounded spin) */
+    NB_PENDING = 7,     /* nb_poll: request not finished yet */
+    NB_ENOTFOUND = 8    /* unknown ticket / index */
+} nb_status;
+
+/* nb_params.flags */
+#define NB_GRAVITY_ONLY 1u  /* drop the contact repulsion (gamma = 0) */
+#define NB_NO_SPIN      2u  /* initial velocities: orbital motion only, no corotation */
+
+/* Physical and numerical parameters (Eqs. 4-6 and the leap-frog step). */
+typedef struct nb_params {
+    double G;            /* gravitational constant of Eq. 4 */
+    double eps;          /* Eq. 4 softening; added to r (not r^2) */
+    double dt;           /* leap-frog time step */
+    double beta;         /* Eq. 6 reduction fraction while a contact separates */
+    double kappa_gamma;  /* repulsion strength of star s:
+                            gamma_s = kappa_gamma G m_s^2 N_s^(2/3) / R_s^5,
+                            m_s, R_s the element mass and initial radius */
+    double rl_coeff;     /* coefficient of Eq. 3's denominator (printed: 0.69) */
+    int32_t force_prec;  /* 32: FP32 pair sum with compensated tile sums
+                            (default); 64: FP64 pair sum (comparison path) */
+    uint32_t flags;      /* NB_GRAVITY_ONLY | NB_NO_SPIN */
+} nb_params;
+
+/* One binary system.  Without xv_in the initial state follows this recipe:
+ * total mass 1, separation sep, q = m_donor/m_accretor, accretor centre at
+ * x = -sep q/(1+q), donor centre at x = +sep/(1+q), orbit about +z with
+ * omega = sqrt(G/sep^3).  Each star is a uniform ball of radius
+ * f * r_L * sep (r_L from Eq. 3: r_L(q) for the donor, r_L(1/q) for the
+ * accretor); element mass = star mass / count, element radius = star
+ * radius * count^(-1/3).  Points are drawn uniformly in the ball (rejection
+ * from the cube) from SplitMix64(seed, stream); velocities are rigid
+ * corotation (or orbital motion only, NB_NO_SPIN) plus sigma_v Gaussian
+ * jitter (Box-Muller), with the mass-weighted mean velocity removed. */
+typedef struct nb_desc {
+    int64_t n_donor;       /* donor elements, >= 0 */
+    int64_t n_accretor;    /* accretor elements, >= 0; n_donor + n_accretor >= 1 */
+    double q;              /* donor mass / accretor mass, > 0 */
+    double sep;            /* orbital separation a, > 0 */
+    double f_donor;        /* donor radius / r_L(q), > 0 */
+    double f_accretor;     /* accretor radius / r_L(1/q), > 0 */
+    double expand_rate;    /* donor growth, in units of r_L(q) sep per step:
+                              R*_d(k) = r_L (f_donor + expand_rate min(k, cap)) */
+    int64_t expand_steps;  /* cap of the growth in steps; < 0: no cap */
+    double sigma_v;        /* velocity jitter (standard deviation per axis) */
+    uint64_t seed;         /* SplitMix64 seed */
+    uint64_t stream;       /* SplitMix64 stream */
+    const double* xv_in;   /* optional host array, n x 6 (x,y,z,vx,vy,vz) in
+                              particle order; replaces the drawn state */
+    const double* mrg_in;  /* optional host array, n x 3 (mass, radius,
+                              gamma) per element; replaces the star-derived
+                              values (growth still scales donor radii) */
+} nb_desc;
+
+/* FP64 diagnostics of a system's state (computed on the GPU). */
+typedef struct nb_diag {
+    int64_t step;          /* completed leap-frog steps */
+    double time;           /* step * dt */
+    double e_kin;          /* 1/2 sum m v^2 */
+    double e_grav;         /* -sum_{i<j} G m_i m_j / (r + eps)  (Eq. 4 potential) */
+    double e_rep;          /* sum over contacts of gamma_ij U(r; R_ij),
+                              U = pi (R^4 - 4/3 R^3 r + R^2 r^2/2 - r^4/48) */
+    double e_tot;          /* e_kin + e_grav + e_rep */
+    double p[3];           /* total momentum */
+    double l[3];           /* total angular momentum about the origin */
+    double com[3];         /* centre of mass */
+    double com_donor[3];   /* centre of mass of the donor's elements */
+    double com_accretor[3];
+    double separation;     /* |com_donor - com_accretor| */
+    double r_donor;        /* donor element radius scale at this step
+                              (current radius / initial radius) */
+    int64_t n_past_L1;     /* donor elements on the accretor's side of the
+                              plane through L1 (Eq. 2) normal to the axis */
+    double m_past_L1;      /* their mass */
+    int64_t n_nonfinite;   /* elements with a non-finite position/velocity */
+} nb_diag;
+
+/* Checkpoint metadata returned by nb_get_state and accepted by nb_set_state. */
+typedef struct nb_ckpt_meta {
+    int64_t n;             /* element count */
+    int64_t step;          /* completed steps */
+    double origin[3];      /* reference point of the FP32 relative coordinates */
+} nb_ckpt_meta;
+
+/* Static facts of a system. */
+typedef struct nb_info {
+    int64_t n, n_donor, n_accretor;
+    double m_donor, m_accretor;        /* element masses */
+    double r_donor0, r_accretor;       /* element radii (donor: initial) */
+    double gamma_donor, gamma_accretor;
+    double rl_donor, rl_accretor;      /* Eq. 3 radii, units of sep */
+    double x_L1;                       /* L1 distance from the accretor, units of sep */
+    int64_t device_bytes;              /* device memory held by the handle */
+} nb_info;
+
+/* Device time per phase, measured with CUDA events recorded on the handle's
+ * stream around each launch while profiling is enabled (nb_profile). */
+typedef struct nb_prof {
+    int64_t pair_launches;     /* launches of the O(N^2) pair kernel */
+    double pair_ms;            /* their summed device time */
+    int64_t contact_launches;  /* contact passes (grid build + repulsion) */
+    double contact_ms;
+    int64_t update_launches;   /* kick / drift kernels */
+    double update_ms;
+    int64_t kernels;           /* kernels enqueued by step/force calls */
+    double pairs;              /* pair interactions evaluated by the pair kernel */
+} nb_prof;
+
+typedef struct nb_system* nb_system_t;
+
+/* ---- library ---------------------------------------------------------- */
+int nb_abi_version(void);
+const char* nb_status_str(nb_status s);
+/* last error message of the calling thread ("" if none) */
+const char* nb_last_error(void);
+/* fill defaults: G=1, eps=0.01, dt=1e-3, beta=0.5, kappa_gamma=8,
+ * rl_coeff=0.69, force_prec=32, flags=0 */
+nb_status nb_params_default(nb_params* p);
+/* fill defaults: 512+512 elements, q=0.5, sep=1, f_donor=0.8,
+ * f_accretor=0.5, no growth, sigma_v=1e-3, seed=0, stream=0 */
+nb_status nb_desc_default(nb_desc* d);
+/* Eq. 3: Roche-lobe radius in units of the separation for mass ratio q
+ * (this star / companion) and denominator coefficient coeff. */
+double nb_roche_rL(double q, double coeff);
+/* Inner Lagrangian point of Eq. 2: distance from the star of mass m1 toward
+ * the star of mass m2 = q m1, in units of the separation. */
+double nb_roche_L1(double q);
+
+/* ---- single system ---------------------------------------------------- */
+
+/* Build a system (initial conditions on the host, FP64), copy it to the
+ * device on `stream` and evaluate the initial acceleration a^0 (Eqs. 4-6).
+ * Returns once the work is enqueued; *out is valid immediately. */
+nb_status nb_create_system(const nb_desc* desc, const nb_params* params,
+                           void* stream, nb_system_t* out);
+
+/* Release all device memory (after the stream's pending work) and the handle. */
+void nb_destroy(nb_system_t sys);
+
+nb_status nb_get_info(nb_system_t sys, nb_info* out);
+
+/* One evaluation of Eqs. 4-6 at the current state (x^k, v^k) with the
+ * radii of step k.  acc_out: n x 3 doubles (ax, ay, az per element), host
+ * memory if out_on_device == 0, else device memory on the handle's device.
+ * The stored acceleration used by the integrator is not changed.  Blocks
+ * until the result is in acc_out. */
+nb_status nb_forces(nb_system_t sys, double* acc_out, int out_on_device);
+
+/* Enqueue nsteps leap-frog steps (kick-drift-kick):
+ *   v^{k+1/2} = v^k + a^k dt/2;  x^{k+1} = x^k + v^{k+1/2} dt;
+ *   a^{k+1} = F(x^{k+1}, v^{k+1/2}, radii of step k+1);
+ *   v^{k+1} = v^{k+1/2} + a^{k+1} dt/2.
+ * Asynchronous: returns after enqueueing on the handle's stream. */
+nb_status nb_step(nb_system_t sys, int64_t nsteps);
+
+/* Wait for the handle's stream; report NB_ENONFINITE or NB_ETIMEOUT if a
+ * kernel flagged one since the last call. */
+nb_status nb_sync(nb_system_t sys);
+
+/* FP64 diagnostics (blocks). */
+nb_status nb_diagnostics(nb_system_t sys, nb_diag* out);
+
+/* Copy the FP64 state to the host: xv_out n x 6 (x,y,z,vx,vy,vz), a_out
+ * n x 3 (the stored a^k, may be NULL), meta (may be NULL).  Blocks. */
+nb_status nb_get_state(nb_system_t sys, double* xv_out, double* a_out, nb_ckpt_meta* meta);
+
+/* Replace the state from a checkpoint.  xv_in n x 6; a_in n x 3 or NULL
+ * (then a^k is re-evaluated from x^k, v^k); meta->n must match; meta->step
+ * and meta->origin are restored, so a resumed run repeats an uninterrupted
+ * one bit for bit when a_in is given. */
+nb_status nb_set_state(nb_system_t sys, const double* xv_in, const double* a_in,
+                       const nb_ckpt_meta* meta);
+
+/* Enable (1) or disable (0) per-phase event timing of subsequent calls;
+ * while enabled, multi-step calls are not captured in CUDA graphs. */
+nb_status nb_profile(nb_system_t sys, int enable);
+
+/* Wait for the stream and return the accumulated times; reset != 0 clears
+ * them afterwards.  Counts kernels and pairs even when timing is off. */
+nb_status nb_profile_read(nb_system_t sys, nb_prof* out, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NBODY_H */

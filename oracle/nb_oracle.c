@@ -145,47 +145,65 @@ double orc_lens_U(double r, double R)
 /* Eqs. 4-6: acceleration of every element by direct summation.             */
 /* x, v: n*3 row-major; m, R, gam: n.  a: n*3 output.                       */
 /* ------------------------------------------------------------------------ */
+/* acceleration of element i (one row of the direct sum) */
+static void orc_accel_row(int64_t i, int64_t n, const double *x, const double *v,
+                          const double *m, const double *R, const double *gam, double G,
+                          double eps, double beta, double *ai)
+{
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    int64_t j;
+    for (j = 0; j < n; ++j) {
+        double dx = x[3 * j + 0] - x[3 * i + 0];
+        double dy = x[3 * j + 1] - x[3 * i + 1];
+        double dz = x[3 * j + 2] - x[3 * i + 2];
+        double d2 = dx * dx + dy * dy + dz * dz;
+        double r, F, f;
+        if (!(d2 > 0.0)) continue;               /* i == j or coincident */
+        r = sqrt(d2);
+        /* Eq. 4: softened attraction, epsilon added to r */
+        F = G * m[i] * m[j] / ((r + eps) * (r + eps));
+        if (r < R[i] + R[j]) {
+            /* Eqs. 5/6: repulsion, full while converging, times beta
+             * while diverging */
+            double Rij = 0.5 * (R[i] + R[j]);
+            double gij = 0.5 * (gam[i] + gam[j]);
+            double dvx = v[3 * j + 0] - v[3 * i + 0];
+            double dvy = v[3 * j + 1] - v[3 * i + 1];
+            double dvz = v[3 * j + 2] - v[3 * i + 2];
+            double closing = dx * dvx + dy * dvy + dz * dvz;
+            double c = (closing < 0.0) ? 1.0 : beta;
+            F -= c * gij * orc_lens_V(r, Rij);
+        }
+        /* F > 0 pulls i toward j; acceleration = F/m_i along dx/r */
+        f = F / (m[i] * r);
+        ax += f * dx;
+        ay += f * dy;
+        az += f * dz;
+    }
+    ai[0] = ax;
+    ai[1] = ay;
+    ai[2] = az;
+}
+
 void orc_forces(int64_t n, const double *x, const double *v, const double *m,
                 const double *R, const double *gam, double G, double eps,
                 double beta, double *a)
 {
     int64_t i;
 #pragma omp parallel for schedule(static)
-    for (i = 0; i < n; ++i) {
-        double ax = 0.0, ay = 0.0, az = 0.0;
-        int64_t j;
-        for (j = 0; j < n; ++j) {
-            double dx = x[3 * j + 0] - x[3 * i + 0];
-            double dy = x[3 * j + 1] - x[3 * i + 1];
-            double dz = x[3 * j + 2] - x[3 * i + 2];
-            double d2 = dx * dx + dy * dy + dz * dz;
-            double r, F, f;
-            if (!(d2 > 0.0)) continue;               /* i == j or coincident */
-            r = sqrt(d2);
-            /* Eq. 4: softened attraction, epsilon added to r */
-            F = G * m[i] * m[j] / ((r + eps) * (r + eps));
-            if (r < R[i] + R[j]) {
-                /* Eqs. 5/6: repulsion, full while converging, times beta
-                 * while diverging */
-                double Rij = 0.5 * (R[i] + R[j]);
-                double gij = 0.5 * (gam[i] + gam[j]);
-                double dvx = v[3 * j + 0] - v[3 * i + 0];
-                double dvy = v[3 * j + 1] - v[3 * i + 1];
-                double dvz = v[3 * j + 2] - v[3 * i + 2];
-                double closing = dx * dvx + dy * dvy + dz * dvz;
-                double c = (closing < 0.0) ? 1.0 : beta;
-                F -= c * gij * orc_lens_V(r, Rij);
-            }
-            /* F > 0 pulls i toward j; acceleration = F/m_i along dx/r */
-            f = F / (m[i] * r);
-            ax += f * dx;
-            ay += f * dy;
-            az += f * dz;
-        }
-        a[3 * i + 0] = ax;
-        a[3 * i + 1] = ay;
-        a[3 * i + 2] = az;
-    }
+    for (i = 0; i < n; ++i)
+        orc_accel_row(i, n, x, v, m, R, gam, G, eps, beta, a + 3 * i);
+}
+
+/* the same sum for the listed rows only: a[3*k..] is element rows[k] */
+void orc_forces_rows(int64_t n, const double *x, const double *v, const double *m,
+                     const double *R, const double *gam, double G, double eps,
+                     double beta, int64_t nrows, const int64_t *rows, double *a)
+{
+    int64_t k;
+#pragma omp parallel for schedule(static)
+    for (k = 0; k < nrows; ++k)
+        orc_accel_row(rows[k], n, x, v, m, R, gam, G, eps, beta, a + 3 * k);
 }
 
 /* Gravitational and repulsive potential energy shared out per element:

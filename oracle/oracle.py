@@ -77,6 +77,8 @@ def _load():
         lib.orc_donor_scale.argtypes = [_I64, _D, _D, _I64]
         lib.orc_forces.restype = None
         lib.orc_forces.argtypes = [_I64, _P, _P, _P, _P, _P, _D, _D, _D, _P]
+        lib.orc_forces_rows.restype = None
+        lib.orc_forces_rows.argtypes = [_I64, _P, _P, _P, _P, _P, _D, _D, _D, _I64, _P, _P]
         lib.orc_potential.restype = None
         lib.orc_potential.argtypes = [_I64, _P, _P, _P, _P, _D, _D, _P, _P]
         lib.orc_run.restype = None
@@ -159,6 +161,23 @@ def forces(x, v, m, R, gam, G=1.0, eps=0.0, beta=1.0):
     a = np.zeros((n, 3), dtype=np.float64)
     _load().orc_forces(n, _ptr(x), _ptr(v), _ptr(m), _ptr(R), _ptr(gam),
                        float(G), float(eps), float(beta), _ptr(a))
+    return a
+
+
+def forces_rows(rows, x, v, m, R, gam, G=1.0, eps=0.0, beta=1.0):
+    """Eqs. 4-6 for the listed elements only: (len(rows), 3)."""
+    x = _f64(x, (-1, 3))
+    n = x.shape[0]
+    v = _f64(v, (n, 3))
+    m = _f64(m, (n,))
+    R = _f64(R, (n,))
+    gam = _f64(gam, (n,))
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    if rows.size and (rows.min() < 0 or rows.max() >= n):
+        raise IndexError("row out of range")
+    a = np.zeros((rows.size, 3), dtype=np.float64)
+    _load().orc_forces_rows(n, _ptr(x), _ptr(v), _ptr(m), _ptr(R), _ptr(gam), float(G),
+                            float(eps), float(beta), rows.size, _ptr(rows), _ptr(a))
     return a
 
 

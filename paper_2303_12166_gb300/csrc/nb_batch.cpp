@@ -1,0 +1,924 @@
+// nb_batch.cpp -- host runtime of a batch of binary systems.
+#include "nb_batch.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+namespace nb {
+
+// ------------------------------------------------------------------ errors
+namespace {
+thread_local std::string t_err;
+}
+
+nb_status set_error(nb_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return s;
+}
+
+const char* last_error() { return t_err.c_str(); }
+
+#define NB_CU(call)                                                                          \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return set_error(e_ == cudaErrorMemoryAllocation ? NB_ENOMEM : NB_ECUDA,         \
+                             "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                             __LINE__);                                                      \
+    } while (0)
+
+#define NB_TRY(call)                     \
+    do {                                 \
+        nb_status s_ = (call);           \
+        if (s_ != NB_OK) return s_;      \
+    } while (0)
+
+// ------------------------------------------------------------------ model setup
+namespace {
+
+// SplitMix64 (Steele, Lea & Flood 2014) with the stream selection of nbody.h.
+struct SplitMix {
+    uint64_t state;
+    SplitMix(uint64_t seed, uint64_t stream) : state(seed ^ (stream * 0xD1B54A32D192ED03ULL)) {}
+    uint64_t next() {
+        state += 0x9E3779B97F4A7C15ULL;
+        uint64_t z = state;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        return z ^ (z >> 31);
+    }
+    double uniform() { return (double)(next() >> 11) * 0x1.0p-53; }
+};
+
+// Standard normals by Box-Muller, handed out one at a time.
+struct Normals {
+    SplitMix& g;
+    bool have = false;
+    double spare = 0.0;
+    explicit Normals(SplitMix& gen) : g(gen) {}
+    double next() {
+        if (have) {
+            have = false;
+            return spare;
+        }
+        const double u1 = g.uniform(), u2 = g.uniform();
+        const double rad = std::sqrt(-2.0 * std::log(1.0 - u1));
+        const double ang = 2.0 * M_PI * u2;
+        spare = rad * std::sin(ang);
+        have = true;
+        return rad * std::cos(ang);
+    }
+};
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+}  // namespace
+
+double model_roche_rL(double q, double coeff) {
+    // Eq. 3
+    const double a = std::cbrt(q);
+    return 0.49 * a * a / (coeff * a * a + std::log1p(a));
+}
+
+double model_roche_L1(double q) {
+    // Force balance on the line between the stars in the corotating frame
+    // (derivative of the Roche potential of Eq. 2 along x, times (1+q)/2):
+    // g(x) = -1/x^2 + q/(1-x)^2 + (1+q) x - q, increasing on (0,1).
+    auto g = [q](double x) { return -1.0 / (x * x) + q / ((1 - x) * (1 - x)) + (1 + q) * x - q; };
+    double lo = 1e-12, hi = 1.0 - 1e-12;
+    for (int it = 0; it < 128 && hi - lo > 1e-16; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (g(mid) < 0) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+nb_status check_params(const nb_params& p) {
+    if (!(std::isfinite(p.G) && p.G >= 0)) return set_error(NB_EINVAL, "G must be finite and >= 0");
+    if (!(std::isfinite(p.eps) && p.eps >= 0)) return set_error(NB_EINVAL, "eps must be >= 0");
+    if (!finite_pos(p.dt)) return set_error(NB_EINVAL, "dt must be > 0");
+    if (!(std::isfinite(p.beta) && p.beta >= 0 && p.beta <= 1))
+        return set_error(NB_EINVAL, "beta must be in [0, 1]");
+    if (!(std::isfinite(p.kappa_gamma) && p.kappa_gamma >= 0))
+        return set_error(NB_EINVAL, "kappa_gamma must be >= 0");
+    if (!finite_pos(p.rl_coeff)) return set_error(NB_EINVAL, "rl_coeff must be > 0");
+    if (p.force_prec != 32 && p.force_prec != 64)
+        return set_error(NB_EINVAL, "force_prec must be 32 or 64");
+    return NB_OK;
+}
+
+nb_status build_system(const nb_desc& d, const nb_params& p, SystemInit& out) {
+    NB_TRY(check_params(p));
+    if (d.n_donor < 0 || d.n_accretor < 0 || d.n_donor + d.n_accretor < 1)
+        return set_error(NB_EINVAL, "need n_donor, n_accretor >= 0 and at least one element");
+    if (d.n_donor + d.n_accretor > (int64_t)1 << 30)
+        return set_error(NB_EINVAL, "at most 2^30 elements per system");
+    if (!finite_pos(d.q)) return set_error(NB_EINVAL, "q must be > 0");
+    if (!finite_pos(d.sep)) return set_error(NB_EINVAL, "sep must be > 0");
+    if (!finite_pos(d.f_donor) || !finite_pos(d.f_accretor))
+        return set_error(NB_EINVAL, "f_donor and f_accretor must be > 0");
+    if (!(std::isfinite(d.expand_rate) && std::isfinite(d.sigma_v) && d.sigma_v >= 0))
+        return set_error(NB_EINVAL, "expand_rate and sigma_v must be finite, sigma_v >= 0");
+    if (d.expand_rate < 0) {
+        if (d.expand_steps < 0 || d.f_donor + d.expand_rate * (double)d.expand_steps <= 0)
+            return set_error(NB_EINVAL, "a shrinking donor needs a cap that keeps its radius > 0");
+    }
+
+    const int64_t nd = d.n_donor, na = d.n_accretor, n = nd + na;
+    out.n = n;
+    out.n_donor = nd;
+    out.x.assign(3 * n, 0.0);
+    out.v.assign(3 * n, 0.0);
+    out.m.assign(n, 0.0);
+    out.R0.assign(n, 0.0);
+    out.gam.assign(n, 0.0);
+
+    const double q = d.q, a = d.sep;
+    const double mass_acc = 1.0 / (1.0 + q), mass_don = q / (1.0 + q);
+    const double rl_d = model_roche_rL(q, p.rl_coeff);
+    const double rl_a = model_roche_rL(1.0 / q, p.rl_coeff);
+    const double star_rd = d.f_donor * rl_d * a;
+    const double star_ra = d.f_accretor * rl_a * a;
+    const double cen_d = a / (1.0 + q), cen_a = -a * q / (1.0 + q);
+    const double omega = std::sqrt(p.G / (a * a * a));
+
+    // element mass = star mass / count; radius = star radius count^(-1/3);
+    // repulsion strength kappa G m^2 N^(2/3) / R^5
+    struct Star { double mass, radius, gamma; };
+    auto star = [&](int64_t cnt, double M, double Rs) {
+        Star s{0, 0, 0};
+        if (cnt > 0) {
+            s.mass = M / (double)cnt;
+            s.radius = Rs / std::cbrt((double)cnt);
+            s.gamma = p.kappa_gamma * p.G * s.mass * s.mass * std::pow((double)cnt, 2.0 / 3.0) /
+                      std::pow(s.radius, 5.0);
+        }
+        return s;
+    };
+    const Star sd = star(nd, mass_don, star_rd), sa = star(na, mass_acc, star_ra);
+    for (int64_t i = 0; i < n; ++i) {
+        const Star& s = i < nd ? sd : sa;
+        out.m[i] = s.mass;
+        out.R0[i] = s.radius;
+        out.gam[i] = s.gamma;
+    }
+    if (d.mrg_in) {
+        for (int64_t i = 0; i < n; ++i) {
+            out.m[i] = d.mrg_in[3 * i + 0];
+            out.R0[i] = d.mrg_in[3 * i + 1];
+            out.gam[i] = d.mrg_in[3 * i + 2];
+            if (!(std::isfinite(out.m[i]) && out.m[i] > 0 && std::isfinite(out.R0[i]) &&
+                  out.R0[i] >= 0 && std::isfinite(out.gam[i]) && out.gam[i] >= 0))
+                return set_error(NB_EINVAL, "mrg_in[%lld]: need m > 0, R >= 0, gamma >= 0",
+                                 (long long)i);
+        }
+    }
+
+    if (d.xv_in) {
+        for (int64_t i = 0; i < n; ++i) {
+            for (int c = 0; c < 3; ++c) {
+                out.x[3 * i + c] = d.xv_in[6 * i + c];
+                out.v[3 * i + c] = d.xv_in[6 * i + 3 + c];
+                if (!std::isfinite(out.x[3 * i + c]) || !std::isfinite(out.v[3 * i + c]))
+                    return set_error(NB_EINVAL, "xv_in[%lld] is not finite", (long long)i);
+            }
+        }
+    } else {
+        SplitMix g(d.seed, d.stream);
+        for (int64_t i = 0; i < n; ++i) {
+            double u[3];
+            do {
+                for (int c = 0; c < 3; ++c) u[c] = 2.0 * g.uniform() - 1.0;
+            } while (u[0] * u[0] + u[1] * u[1] + u[2] * u[2] > 1.0);
+            const bool don = i < nd;
+            const double Rs = don ? star_rd : star_ra;
+            out.x[3 * i + 0] = (don ? cen_d : cen_a) + Rs * u[0];
+            out.x[3 * i + 1] = Rs * u[1];
+            out.x[3 * i + 2] = Rs * u[2];
+        }
+        Normals nrm(g);
+        const bool no_spin = (p.flags & NB_NO_SPIN) != 0;
+        for (int64_t i = 0; i < n; ++i) {
+            const double j0 = nrm.next(), j1 = nrm.next(), j2 = nrm.next();
+            const double px = no_spin ? (i < nd ? cen_d : cen_a) : out.x[3 * i + 0];
+            const double py = no_spin ? 0.0 : out.x[3 * i + 1];
+            out.v[3 * i + 0] = -omega * py + d.sigma_v * j0;
+            out.v[3 * i + 1] = omega * px + d.sigma_v * j1;
+            out.v[3 * i + 2] = d.sigma_v * j2;
+        }
+        double pm[3] = {0, 0, 0}, mt = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            for (int c = 0; c < 3; ++c) pm[c] += out.m[i] * out.v[3 * i + c];
+            mt += out.m[i];
+        }
+        for (int64_t i = 0; i < n; ++i)
+            for (int c = 0; c < 3; ++c) out.v[3 * i + c] -= pm[c] / mt;
+    }
+
+    out.G = p.G;
+    out.eps = p.eps;
+    out.dt = p.dt;
+    out.beta = p.beta;
+    out.contacts = (p.flags & NB_GRAVITY_ONLY) ? 0 : 1;
+    out.grow_f0 = d.f_donor;
+    out.grow_rate = d.expand_rate;
+    out.grow_cap = d.expand_steps;
+    out.xl1 = model_roche_L1(q);
+    // reference point of the FP32 copy: the initial centre of mass
+    double c[3] = {0, 0, 0}, mt = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int k = 0; k < 3; ++k) c[k] += out.m[i] * out.x[3 * i + k];
+        mt += out.m[i];
+    }
+    for (int k = 0; k < 3; ++k) out.origin[k] = c[k] / mt;
+
+    nb_info& f = out.info;
+    std::memset(&f, 0, sizeof f);
+    f.n = n;
+    f.n_donor = nd;
+    f.n_accretor = na;
+    f.m_donor = nd ? out.m[0] : 0;
+    f.m_accretor = na ? out.m[nd] : 0;
+    f.r_donor0 = nd ? out.R0[0] : 0;
+    f.r_accretor = na ? out.R0[nd] : 0;
+    f.gamma_donor = nd ? out.gam[0] : 0;
+    f.gamma_accretor = na ? out.gam[nd] : 0;
+    f.rl_donor = rl_d;
+    f.rl_accretor = rl_a;
+    f.x_L1 = out.xl1;
+    return NB_OK;
+}
+
+// ------------------------------------------------------------------ batch
+extern size_t diag_scratch_doubles();
+
+Batch::~Batch() { release_(); }
+
+void Batch::release_() {
+    if (!prof_marks_.empty() || !event_pool_.empty()) {
+        cudaStreamSynchronize(stream_);
+        for (auto& m : prof_marks_) {
+            cudaEventDestroy(m.a);
+            cudaEventDestroy(m.b);
+        }
+        for (auto e : event_pool_) cudaEventDestroy(e);
+        prof_marks_.clear();
+        event_pool_.clear();
+    }
+    if (graph_exec_) {
+        cudaGraphExecDestroy(graph_exec_);
+        graph_exec_ = nullptr;
+    }
+    if (!allocs_.empty()) {
+        cudaStreamSynchronize(stream_);
+        for (void* p : allocs_) cudaFreeAsync(p, stream_);
+        cudaStreamSynchronize(stream_);
+        allocs_.clear();
+    }
+    bytes_ = 0;
+}
+
+nb_status Batch::alloc_(void** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    NB_CU(cudaMallocAsync(p, bytes, stream_));
+    NB_CU(cudaMemsetAsync(*p, 0, bytes, stream_));
+    allocs_.push_back(*p);
+    bytes_ += (int64_t)bytes;
+    return NB_OK;
+}
+
+static uint32_t next_pow2(uint64_t v) {
+    uint64_t p = 1;
+    while (p < v) p <<= 1;
+    return (uint32_t)p;
+}
+
+nb_status Batch::init(const std::vector<int64_t>& n_per_slot, int prec, cudaStream_t stream) {
+    if (n_per_slot.empty()) return set_error(NB_EINVAL, "a batch needs at least one slot");
+    if (prec != 32 && prec != 64) return set_error(NB_EINVAL, "prec must be 32 or 64");
+    stream_ = stream;
+    prec_ = prec;
+    NB_CU(cudaGetDevice(&device_));
+    NB_CU(cudaDeviceGetAttribute(&sm_count_, cudaDevAttrMultiProcessorCount, device_));
+    const int nsys = (int)n_per_slot.size();
+    sc_.assign(nsys, SysConst{});
+    k_.assign(nsys, 0);
+    mass_.assign(nsys, {});
+    rmax_d0_.assign(nsys, 0.0);
+    rmax_a_.assign(nsys, 0.0);
+    int64_t off = 0;
+    for (int s = 0; s < nsys; ++s) {
+        const int64_t n = n_per_slot[s];
+        if (n < 1) return set_error(NB_EINVAL, "slot %d: size must be >= 1", s);
+        const int64_t npad = (n + NB_PAD - 1) / NB_PAD * NB_PAD;
+        sc_[s].off = off;
+        sc_[s].n = n;
+        sc_[s].npad = npad;
+        sc_[s].active = 0;
+        sc_[s].nchunks = 1;
+        off += npad;
+    }
+    if (off >= ((int64_t)1 << 31)) return set_error(NB_EINVAL, "batch too large (>= 2^31 elements)");
+    d_.ntot = off;
+    d_.nsys = nsys;
+    const size_t nt = (size_t)off;
+    NB_TRY(alloc_((void**)&d_.X, nt * sizeof(double4_32a)));
+    NB_TRY(alloc_((void**)&d_.V, nt * sizeof(double4_32a)));
+    NB_TRY(alloc_((void**)&d_.A, nt * sizeof(double4_32a)));
+    NB_TRY(alloc_((void**)&d_.E, nt * sizeof(double2)));
+    NB_TRY(alloc_((void**)&d_.pos4, (nt + NB_PAD) * sizeof(float4)));
+    NB_TRY(alloc_((void**)&d_.sys_of, nt * sizeof(int32_t)));
+    NB_TRY(alloc_((void**)&d_.cont, nt * sizeof(double4_32a)));
+    d_.nchunk_alloc = 0;
+    d_.part = nullptr;
+    uint64_t nb = std::max<uint64_t>(4096, 2 * (uint64_t)off);
+    nb = std::min<uint64_t>(nb, contact_max_buckets());
+    d_.nbucket = next_pow2(nb);
+    if (d_.nbucket > contact_max_buckets()) d_.nbucket >>= 1;
+    NB_TRY(alloc_((void**)&d_.key, nt * sizeof(uint32_t)));
+    NB_TRY(alloc_((void**)&d_.cellid, nt * sizeof(uint64_t)));
+    NB_TRY(alloc_((void**)&d_.cnt, d_.nbucket * sizeof(uint32_t)));
+    NB_TRY(alloc_((void**)&d_.fill, d_.nbucket * sizeof(uint32_t)));
+    NB_TRY(alloc_((void**)&d_.start, d_.nbucket * sizeof(uint32_t)));
+    NB_TRY(alloc_((void**)&d_.blocksum, (d_.nbucket / 4096 + 2) * sizeof(uint32_t)));
+    NB_TRY(alloc_((void**)&d_.sorted, nt * sizeof(uint32_t)));
+    NB_TRY(alloc_((void**)&d_.red, diag_scratch_doubles() * sizeof(double)));
+    NB_TRY(alloc_((void**)&d_.diag_out, NB_DIAG_OUT * sizeof(double)));
+    SysConst* scd = nullptr;
+    NB_TRY(alloc_((void**)&scd, nsys * sizeof(SysConst)));
+    d_.sc = scd;
+    NB_TRY(alloc_((void**)&d_.sm, nsys * sizeof(SysMut)));
+    NB_TRY(alloc_((void**)&counter_d_, 64));
+    // sys_of = -1 everywhere until a system is loaded
+    NB_CU(cudaMemsetAsync(d_.sys_of, 0xff, nt * sizeof(int32_t), stream_));
+    consts_dirty_ = true;
+    planned_ = false;
+    return NB_OK;
+}
+
+nb_status Batch::push_consts_() {
+    if (!consts_dirty_) return NB_OK;
+    NB_CU(cudaMemcpyAsync((void*)d_.sc, sc_.data(), sc_.size() * sizeof(SysConst),
+                          cudaMemcpyHostToDevice, stream_));
+    // pageable source: the copy has been staged when cudaMemcpyAsync returns
+    consts_dirty_ = false;
+    return NB_OK;
+}
+
+nb_status Batch::load(int s, const SystemInit& si, bool defer_forces) {
+    if (s < 0 || s >= nslots()) return set_error(NB_ENOTFOUND, "no slot %d", s);
+    SysConst& c = sc_[s];
+    if (si.n > c.npad) return set_error(NB_EINVAL, "system of %lld elements does not fit slot %d",
+                                        (long long)si.n, s);
+    c.n = si.n;
+    c.n_donor = si.n_donor;
+    c.dt = si.dt;
+    c.G = si.G;
+    c.eps = si.eps;
+    c.eps_f = (float)si.eps;
+    c.beta = si.beta;
+    for (int k = 0; k < 3; ++k) c.origin[k] = si.origin[k];
+    c.grow_f0 = si.grow_f0;
+    c.grow_rate = si.grow_rate;
+    c.grow_cap = si.grow_cap;
+    c.xl1 = si.xl1;
+    c.active = 1;
+    c.contacts = si.contacts;
+    double rd = 0, ra = 0;
+    for (int64_t i = 0; i < si.n; ++i) {
+        if (i < si.n_donor) rd = std::max(rd, si.R0[i]);
+        else ra = std::max(ra, si.R0[i]);
+    }
+    rmax_d0_[s] = rd;
+    rmax_a_[s] = ra;
+    c.rmax_donor0 = rd;
+    c.rmax_acc = ra;
+    if (!(rd > 0 || ra > 0)) c.contacts = 0;  // no element has a radius
+    k_[s] = 0;
+    mass_[s] = si.m;
+
+    // host staging (pageable: cudaMemcpyAsync returns after the copy-out)
+    const int64_t n = si.n, npad = c.npad;
+    std::vector<double4_32a> X(npad), V(npad);
+    std::vector<double2> E(npad);
+    std::vector<int32_t> owner(npad, -1);
+    for (int64_t i = 0; i < npad; ++i) {
+        if (i < n) {
+            X[i] = make_double4_32a(si.x[3 * i], si.x[3 * i + 1], si.x[3 * i + 2], si.m[i]);
+            V[i] = make_double4_32a(si.v[3 * i], si.v[3 * i + 1], si.v[3 * i + 2], 0.0);
+            E[i] = make_double2(si.R0[i], si.gam[i]);
+            owner[i] = s;
+        } else {
+            X[i] = make_double4_32a(0, 0, 0, 0);
+            V[i] = make_double4_32a(0, 0, 0, 0);
+            E[i] = make_double2(0, 0);
+        }
+    }
+    NB_CU(cudaMemcpyAsync(d_.X + c.off, X.data(), npad * sizeof(double4_32a),
+                          cudaMemcpyHostToDevice, stream_));
+    NB_CU(cudaMemcpyAsync(d_.V + c.off, V.data(), npad * sizeof(double4_32a),
+                          cudaMemcpyHostToDevice, stream_));
+    NB_CU(cudaMemsetAsync(d_.A + c.off, 0, npad * sizeof(double4_32a), stream_));
+    NB_CU(cudaMemcpyAsync(d_.E + c.off, E.data(), npad * sizeof(double2), cudaMemcpyHostToDevice,
+                          stream_));
+    NB_CU(cudaMemcpyAsync(d_.sys_of + c.off, owner.data(), npad * sizeof(int32_t),
+                          cudaMemcpyHostToDevice, stream_));
+    NB_CU(cudaMemsetAsync(d_.pos4 + c.off, 0, npad * sizeof(float4), stream_));
+    SysMut m0{};
+    NB_CU(cudaMemcpyAsync(d_.sm + s, &m0, sizeof m0, cudaMemcpyHostToDevice, stream_));
+    consts_dirty_ = true;
+    planned_ = false;
+    NB_TRY(push_consts_());
+    NB_CU(launch_shadow(d_, stream_));
+    if (!defer_forces) NB_TRY(init_acc(s));
+    // the staging vectors go out of scope: make sure pageable copies are done
+    NB_CU(cudaStreamSynchronize(stream_));
+    return NB_OK;
+}
+
+nb_status Batch::unload(int s) {
+    if (s < 0 || s >= nslots()) return set_error(NB_ENOTFOUND, "no slot %d", s);
+    sc_[s].active = 0;
+    consts_dirty_ = true;
+    planned_ = false;
+    return push_consts_();
+}
+
+nb_status Batch::set_pair_cfg(const PairCfg& c) {
+    if (!pair_cfg_supported(c))
+        return set_error(NB_EINVAL, "pair configuration tile=%d bi=%d threads=%d not built",
+                         c.tile, c.bi, c.threads);
+    cfg_ = c;
+    planned_ = false;
+    return NB_OK;
+}
+
+double Batch::pairs_per_step() const {
+    double p = 0;
+    for (const SysConst& c : sc_)
+        if (c.active) p += (double)c.n * (double)c.n;
+    return p;
+}
+
+nb_status Batch::plan_pairs_() {
+    if (planned_) return NB_OK;
+    const bool f32 = prec_ == 32;
+    const int I = f32 ? cfg_.threads * cfg_.bi : kF64Block;
+    const int tile = f32 ? cfg_.tile : kF64Tile;
+    const int occ = std::max(1, f32 ? pair_occupancy(cfg_) : pair_f64_occupancy());
+    const int64_t slots = (int64_t)sm_count_ * occ;
+
+    std::vector<int> act;
+    double total = 0;
+    for (int s = 0; s < nslots(); ++s)
+        if (sc_[s].active) {
+            act.push_back(s);
+            total += (double)sc_[s].n * (double)sc_[s].n;
+        }
+    items_.clear();
+    int maxchunks = 1;
+    dynamic_ = act.size() > 1;
+    for (int s : act) {
+        SysConst& c = sc_[s];
+        const int64_t nib = (c.n + I - 1) / I;
+        const int64_t ntiles = (c.n + tile - 1) / tile;
+        const int64_t smax = std::min<int64_t>(NB_MAX_CHUNKS, ntiles);
+        int64_t S = 1;
+        if (act.size() == 1) {
+            // fill the persistent grid evenly: smallest chunk count whose item
+            // count wastes at most 4 % of the last wave
+            double best = -1;
+            int64_t bestS = 1;
+            for (int64_t cand = 1; cand <= smax; ++cand) {
+                const int64_t items = nib * cand;
+                const int64_t waves = (items + slots - 1) / slots;
+                const double eff = (double)items / (double)(waves * slots);
+                if (eff > best + 1e-12) {
+                    best = eff;
+                    bestS = cand;
+                }
+                if (eff >= 0.96) {
+                    bestS = cand;
+                    break;
+                }
+            }
+            S = bestS;
+        } else {
+            // batched: items of roughly equal cost, about six per CTA slot
+            const double target =
+                std::max((double)I * tile * 8.0, total / ((double)slots * 6.0));
+            const double cost_full = (double)I * (double)(ntiles * tile);
+            S = (int64_t)std::llround(cost_full / target);
+            S = std::max<int64_t>(1, std::min(S, smax));
+        }
+        const int64_t tpc = (ntiles + S - 1) / S;  // tiles per chunk
+        S = (ntiles + tpc - 1) / tpc;
+        c.nchunks = (int32_t)S;
+        maxchunks = std::max<int>(maxchunks, (int)S);
+        for (int64_t ib = 0; ib < nib; ++ib) {
+            for (int64_t ch = 0; ch < S; ++ch) {
+                PairItem it{};
+                it.i0 = c.off + ib * I;
+                it.iend_rel = (int32_t)std::min<int64_t>(I, c.n - ib * I);
+                it.j0 = c.off + ch * tpc * tile;
+                it.nj = (int32_t)(std::min<int64_t>(tpc, ntiles - ch * tpc) * tile);
+                it.sys = s;
+                it.chunk = (int32_t)ch;
+                items_.push_back(it);
+            }
+        }
+    }
+    if (dynamic_) {
+        // longest first (LPT); the persistent CTAs claim items in this order
+        std::stable_sort(items_.begin(), items_.end(), [](const PairItem& a, const PairItem& b) {
+            return (int64_t)a.iend_rel * a.nj > (int64_t)b.iend_rel * b.nj;
+        });
+    }
+    if (maxchunks > d_.nchunk_alloc) {
+        // grow the partial-sum buffer (chunk-major)
+        if (d_.part) {
+            NB_CU(cudaStreamSynchronize(stream_));
+            auto itp = std::find(allocs_.begin(), allocs_.end(), (void*)d_.part);
+            if (itp != allocs_.end()) allocs_.erase(itp);
+            NB_CU(cudaFreeAsync(d_.part, stream_));
+            bytes_ -= (int64_t)d_.nchunk_alloc * d_.ntot * (int64_t)sizeof(double4_32a);
+        }
+        NB_TRY(alloc_((void**)&d_.part, (size_t)maxchunks * d_.ntot * sizeof(double4_32a)));
+        d_.nchunk_alloc = maxchunks;
+    }
+    if ((int)items_.size() > items_cap_) {
+        if (items_d_) {
+            NB_CU(cudaStreamSynchronize(stream_));
+            auto itp = std::find(allocs_.begin(), allocs_.end(), (void*)items_d_);
+            if (itp != allocs_.end()) allocs_.erase(itp);
+            NB_CU(cudaFreeAsync(items_d_, stream_));
+        }
+        items_cap_ = std::max<int>(64, (int)items_.size());
+        NB_TRY(alloc_((void**)&items_d_, (size_t)items_cap_ * sizeof(PairItem)));
+    }
+    if (!items_.empty())
+        NB_CU(cudaMemcpyAsync(items_d_, items_.data(), items_.size() * sizeof(PairItem),
+                              cudaMemcpyHostToDevice, stream_));
+    cfg_.grid = (int)std::min<int64_t>((int64_t)items_.size(), slots);
+    consts_dirty_ = true;
+    NB_TRY(push_consts_());
+    NB_CU(cudaStreamSynchronize(stream_));  // items_ host buffer is pageable
+    planned_ = true;
+    if (graph_exec_) {
+        cudaGraphExecDestroy(graph_exec_);
+        graph_exec_ = nullptr;
+        graph_n_ = -1;
+    }
+    return NB_OK;
+}
+
+nb_status Batch::launch_pairs_(bool pot) {
+    const int n = (int)items_.size();
+    if (n == 0) return NB_OK;
+    int* ctr = nullptr;
+    if (dynamic_) {
+        NB_CU(cudaMemsetAsync(counter_d_, 0, sizeof(int), stream_));
+        ctr = counter_d_;
+    }
+    cudaEvent_t ev = prof_begin_();
+    if (prec_ == 32) {
+        NB_CU(launch_pair_f32(d_, items_d_, n, cfg_, pot, ctr, stream_));
+    } else {
+        NB_CU(launch_pair_f64(d_, items_d_, n, cfg_.grid, pot, ctr, stream_));
+    }
+    kernels_ += 1;
+    pairs_done_ += pairs_per_step();
+    return prof_end_(ev, PH_PAIR);
+}
+
+bool Batch::any_contacts_() const {
+    for (const SysConst& c : sc_)
+        if (c.active && c.contacts && (c.rmax_donor0 > 0 || c.rmax_acc > 0)) return true;
+    return false;
+}
+
+// kernels of one contact pass: scan (3), scatter, bucket sort, repulsion
+static constexpr int kContactKernels = 6;
+
+nb_status Batch::contact_pass_(int kofs, bool energy, bool with_keys) {
+    cudaEvent_t ev = prof_begin_();
+    if (with_keys) {
+        NB_CU(cudaMemsetAsync(d_.cnt, 0, sizeof(uint32_t) * d_.nbucket, stream_));
+        NB_CU(launch_cell_keys(d_, kofs, stream_));
+        kernels_ += 1;
+    }
+    NB_CU(launch_contact(d_, kofs, energy, stream_));
+    kernels_ += kContactKernels;
+    return prof_end_(ev, PH_CONTACT);
+}
+
+cudaEvent_t Batch::prof_begin_() {
+    if (!prof_on_) return nullptr;
+    cudaEvent_t e = nullptr;
+    if (!event_pool_.empty()) {
+        e = event_pool_.back();
+        event_pool_.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        return nullptr;
+    }
+    cudaEventRecord(e, stream_);
+    return e;
+}
+
+nb_status Batch::prof_end_(cudaEvent_t a, int phase) {
+    if (!a) return NB_OK;
+    cudaEvent_t b = nullptr;
+    if (!event_pool_.empty()) {
+        b = event_pool_.back();
+        event_pool_.pop_back();
+    } else {
+        NB_CU(cudaEventCreate(&b));
+    }
+    NB_CU(cudaEventRecord(b, stream_));
+    prof_marks_.push_back({a, b, phase});
+    if (prof_marks_.size() > 4096) return prof_collect_();
+    return NB_OK;
+}
+
+nb_status Batch::prof_collect_() {
+    if (prof_marks_.empty()) return NB_OK;
+    NB_CU(cudaStreamSynchronize(stream_));
+    for (auto& m : prof_marks_) {
+        float ms = 0.f;
+        NB_CU(cudaEventElapsedTime(&ms, m.a, m.b));
+        prof_ms_[m.phase] += ms;
+        prof_n_[m.phase] += 1;
+        event_pool_.push_back(m.a);
+        event_pool_.push_back(m.b);
+    }
+    prof_marks_.clear();
+    return NB_OK;
+}
+
+nb_status Batch::set_profile(bool on) {
+    prof_on_ = on;
+    return NB_OK;
+}
+
+nb_status Batch::read_profile(nb_prof* out, bool reset) {
+    if (!out) return set_error(NB_EINVAL, "null output");
+    NB_TRY(prof_collect_());
+    NB_CU(cudaStreamSynchronize(stream_));
+    out->pair_launches = prof_n_[PH_PAIR];
+    out->pair_ms = prof_ms_[PH_PAIR];
+    out->contact_launches = prof_n_[PH_CONTACT];
+    out->contact_ms = prof_ms_[PH_CONTACT];
+    out->update_launches = prof_n_[PH_UPDATE];
+    out->update_ms = prof_ms_[PH_UPDATE];
+    out->kernels = kernels_;
+    out->pairs = pairs_done_;
+    if (reset) {
+        for (int k = 0; k < 3; ++k) {
+            prof_ms_[k] = 0;
+            prof_n_[k] = 0;
+        }
+        kernels_ = 0;
+        pairs_done_ = 0;
+    }
+    return NB_OK;
+}
+
+nb_status Batch::eval_forces(int kofs, bool pot, bool energy) {
+    NB_TRY(plan_pairs_());
+    NB_TRY(push_consts_());
+    if (any_contacts_()) NB_TRY(contact_pass_(kofs, energy, true));
+    return launch_pairs_(pot);
+}
+
+nb_status Batch::init_acc(int only) {
+    NB_TRY(eval_forces(0, false, false));
+    NB_CU(launch_store_acc(d_, only, stream_));
+    kernels_ += 1;
+    return NB_OK;
+}
+
+nb_status Batch::step_body_(int64_t n) {
+    const bool contacts = any_contacts_();
+    for (int64_t st = 0; st < n; ++st) {
+        if (contacts) NB_CU(cudaMemsetAsync(d_.cnt, 0, sizeof(uint32_t) * d_.nbucket, stream_));
+        cudaEvent_t ev = prof_begin_();
+        // the drift kernel also bins the new positions into the contact grid
+        NB_CU(launch_kick(d_, st == 0 ? KICK_START : KICK_FINISH_START, contacts, stream_));
+        kernels_ += 1;
+        NB_TRY(prof_end_(ev, PH_UPDATE));
+        NB_TRY(launch_pairs_(false));
+        if (contacts) NB_TRY(contact_pass_(1, false, false));
+        NB_CU(launch_advance(d_, stream_));
+        kernels_ += 1;
+    }
+    cudaEvent_t ev = prof_begin_();
+    NB_CU(launch_kick(d_, KICK_FINISH, false, stream_));
+    kernels_ += 1;
+    return prof_end_(ev, PH_UPDATE);
+}
+
+nb_status Batch::step(int64_t n) {
+    if (n < 0) return set_error(NB_EINVAL, "nsteps must be >= 0");
+    if (n == 0) return NB_OK;
+    NB_TRY(plan_pairs_());
+    NB_TRY(push_consts_());
+    if (use_graph_ && !prof_on_ && n > 1 && stream_ != nullptr) {
+        if (graph_n_ != n || !graph_exec_) {
+            if (graph_exec_) {
+                cudaGraphExecDestroy(graph_exec_);
+                graph_exec_ = nullptr;
+            }
+            cudaGraph_t g = nullptr;
+            NB_CU(cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal));
+            nb_status st = step_body_(n);
+            cudaError_t e = cudaStreamEndCapture(stream_, &g);
+            if (st != NB_OK) {
+                if (g) cudaGraphDestroy(g);
+                return st;
+            }
+            NB_CU(e);
+            e = cudaGraphInstantiate(&graph_exec_, g, 0);
+            cudaGraphDestroy(g);
+            NB_CU(e);
+            graph_n_ = n;
+        }
+        NB_CU(cudaGraphLaunch(graph_exec_, stream_));
+    } else {
+        NB_TRY(step_body_(n));
+    }
+    for (int s = 0; s < nslots(); ++s)
+        if (sc_[s].active) k_[s] += n;
+    return NB_OK;
+}
+
+nb_status Batch::sync() {
+    NB_CU(cudaStreamSynchronize(stream_));
+    std::vector<SysMut> m(nslots());
+    NB_CU(cudaMemcpy(m.data(), d_.sm, m.size() * sizeof(SysMut), cudaMemcpyDeviceToHost));
+    nb_status res = NB_OK;
+    bool reset = false;
+    for (int s = 0; s < nslots(); ++s) {
+        if (m[s].timeout) {
+            res = set_error(NB_ETIMEOUT, "system %d: a device wait gave up", s);
+            reset = true;
+        } else if (m[s].nonfinite && res == NB_OK) {
+            res = set_error(NB_ENONFINITE, "system %d: %llu non-finite element updates", s,
+                            (unsigned long long)m[s].nonfinite);
+            reset = true;
+        }
+        m[s].timeout = 0;
+        m[s].nonfinite = 0;
+    }
+    if (reset) NB_CU(cudaMemcpy(d_.sm, m.data(), m.size() * sizeof(SysMut), cudaMemcpyHostToDevice));
+    return res;
+}
+
+nb_status Batch::forces_out(int s, double* out, bool out_on_device) {
+    if (s < 0 || s >= nslots() || !sc_[s].active) return set_error(NB_ENOTFOUND, "no system %d", s);
+    if (!out) return set_error(NB_EINVAL, "null output");
+    NB_TRY(eval_forces(0, false, false));
+    const int64_t n = sc_[s].n;
+    if (out_on_device) {
+        NB_CU(launch_sum_forces(d_, s, n, out, stream_));
+        return sync();
+    }
+    if (fout_cap_ < n) {
+        if (fout_d_) {
+            NB_CU(cudaStreamSynchronize(stream_));
+            auto itp = std::find(allocs_.begin(), allocs_.end(), (void*)fout_d_);
+            if (itp != allocs_.end()) allocs_.erase(itp);
+            NB_CU(cudaFreeAsync(fout_d_, stream_));
+        }
+        NB_TRY(alloc_((void**)&fout_d_, (size_t)n * 3 * sizeof(double)));
+        fout_cap_ = n;
+    }
+    NB_CU(launch_sum_forces(d_, s, n, fout_d_, stream_));
+    NB_CU(cudaMemcpyAsync(out, fout_d_, (size_t)n * 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                          stream_));
+    return sync();
+}
+
+nb_status Batch::diagnostics(int s, nb_diag* out) {
+    if (s < 0 || s >= nslots() || !sc_[s].active) return set_error(NB_ENOTFOUND, "no system %d", s);
+    if (!out) return set_error(NB_EINVAL, "null output");
+    NB_TRY(eval_forces(0, true, true));
+    NB_CU(launch_diag(d_, s, stream_));
+    double v[NB_DIAG_OUT];
+    SysMut m{};
+    NB_CU(cudaMemcpyAsync(v, d_.diag_out, sizeof v, cudaMemcpyDeviceToHost, stream_));
+    NB_CU(cudaMemcpyAsync(&m, d_.sm + s, sizeof m, cudaMemcpyDeviceToHost, stream_));
+    NB_CU(cudaStreamSynchronize(stream_));
+    const SysConst& c = sc_[s];
+    std::memset(out, 0, sizeof *out);
+    out->step = m.k;
+    out->time = (double)m.k * c.dt;
+    out->e_kin = v[1];
+    out->e_grav = v[19];
+    out->e_rep = v[20];
+    out->e_tot = v[1] + v[19] + v[20];
+    for (int d = 0; d < 3; ++d) {
+        out->p[d] = v[2 + d];
+        out->l[d] = v[5 + d];
+        out->com[d] = v[0] > 0 ? v[8 + d] / v[0] : 0.0;
+        out->com_donor[d] = v[22 + d];
+        out->com_accretor[d] = v[25 + d];
+    }
+    out->separation = v[28];
+    const int64_t kk = (c.grow_cap >= 0 && m.k > c.grow_cap) ? c.grow_cap : m.k;
+    out->r_donor = (c.grow_f0 + c.grow_rate * (double)kk) / c.grow_f0;
+    out->n_past_L1 = (int64_t)std::llround(v[32]);
+    out->m_past_L1 = v[33];
+    out->n_nonfinite = (int64_t)std::llround(v[21]);
+    return NB_OK;
+}
+
+nb_status Batch::get_state(int s, double* xv, double* a, nb_ckpt_meta* meta) {
+    if (s < 0 || s >= nslots() || !sc_[s].active) return set_error(NB_ENOTFOUND, "no system %d", s);
+    const SysConst& c = sc_[s];
+    const int64_t n = c.n;
+    std::vector<double4_32a> X(n), V(n), A(n);
+    SysMut m{};
+    NB_CU(cudaMemcpyAsync(X.data(), d_.X + c.off, n * sizeof(double4_32a), cudaMemcpyDeviceToHost,
+                          stream_));
+    NB_CU(cudaMemcpyAsync(V.data(), d_.V + c.off, n * sizeof(double4_32a), cudaMemcpyDeviceToHost,
+                          stream_));
+    if (a)
+        NB_CU(cudaMemcpyAsync(A.data(), d_.A + c.off, n * sizeof(double4_32a),
+                              cudaMemcpyDeviceToHost, stream_));
+    NB_CU(cudaMemcpyAsync(&m, d_.sm + s, sizeof m, cudaMemcpyDeviceToHost, stream_));
+    NB_CU(cudaStreamSynchronize(stream_));
+    if (xv) {
+        for (int64_t i = 0; i < n; ++i) {
+            xv[6 * i + 0] = X[i].x;
+            xv[6 * i + 1] = X[i].y;
+            xv[6 * i + 2] = X[i].z;
+            xv[6 * i + 3] = V[i].x;
+            xv[6 * i + 4] = V[i].y;
+            xv[6 * i + 5] = V[i].z;
+        }
+    }
+    if (a) {
+        for (int64_t i = 0; i < n; ++i) {
+            a[3 * i + 0] = A[i].x;
+            a[3 * i + 1] = A[i].y;
+            a[3 * i + 2] = A[i].z;
+        }
+    }
+    if (meta) {
+        meta->n = n;
+        meta->step = m.k;
+        for (int d = 0; d < 3; ++d) meta->origin[d] = c.origin[d];
+    }
+    return NB_OK;
+}
+
+nb_status Batch::set_state(int s, const double* xv, const double* a, const nb_ckpt_meta* meta) {
+    if (s < 0 || s >= nslots() || !sc_[s].active) return set_error(NB_ENOTFOUND, "no system %d", s);
+    if (!xv || !meta) return set_error(NB_EINVAL, "xv_in and meta are required");
+    SysConst& c = sc_[s];
+    const int64_t n = c.n;
+    if (meta->n != n) return set_error(NB_EINVAL, "checkpoint has %lld elements, system %lld",
+                                       (long long)meta->n, (long long)n);
+    if (meta->step < 0) return set_error(NB_EINVAL, "checkpoint step must be >= 0");
+    std::vector<double4_32a> X(n), V(n), A(a ? n : 0);
+    for (int64_t i = 0; i < n; ++i) {
+        for (int d = 0; d < 6; ++d)
+            if (!std::isfinite(xv[6 * i + d]))
+                return set_error(NB_EINVAL, "xv_in[%lld] is not finite", (long long)i);
+        X[i] = make_double4_32a(xv[6 * i], xv[6 * i + 1], xv[6 * i + 2], mass_[s][i]);
+        V[i] = make_double4_32a(xv[6 * i + 3], xv[6 * i + 4], xv[6 * i + 5], 0.0);
+        if (a) A[i] = make_double4_32a(a[3 * i], a[3 * i + 1], a[3 * i + 2], 0.0);
+    }
+    NB_CU(cudaStreamSynchronize(stream_));
+    NB_CU(cudaMemcpyAsync(d_.X + c.off, X.data(), n * sizeof(double4_32a), cudaMemcpyHostToDevice,
+                          stream_));
+    NB_CU(cudaMemcpyAsync(d_.V + c.off, V.data(), n * sizeof(double4_32a), cudaMemcpyHostToDevice,
+                          stream_));
+    SysMut m{};
+    m.k = meta->step;
+    NB_CU(cudaMemcpyAsync(d_.sm + s, &m, sizeof m, cudaMemcpyHostToDevice, stream_));
+    k_[s] = meta->step;
+    for (int d = 0; d < 3; ++d) c.origin[d] = meta->origin[d];
+    consts_dirty_ = true;
+    NB_TRY(push_consts_());
+    NB_CU(launch_shadow(d_, stream_));
+    if (a) {
+        NB_CU(cudaMemcpyAsync(d_.A + c.off, A.data(), n * sizeof(double4_32a),
+                              cudaMemcpyHostToDevice, stream_));
+    } else {
+        NB_TRY(init_acc(s));
+    }
+    NB_CU(cudaStreamSynchronize(stream_));
+    return NB_OK;
+}
+
+}  // namespace nb

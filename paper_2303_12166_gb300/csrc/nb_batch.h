@@ -1,0 +1,140 @@
+// nb_batch.h -- host runtime of a batch of binary systems (C++).
+//
+// A Batch owns the device arrays of nb_internal.h for a fixed set of system
+// slots, the pair-kernel work list, and the step sequencing.  The single
+// system C API, the batched API and the server are all thin layers over it.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "nb_internal.h"
+#include "nbody.h"
+
+namespace nb {
+
+// Thread-local error text behind nb_last_error().
+nb_status set_error(nb_status s, const char* fmt, ...);
+const char* last_error();
+
+// Host description of one system, ready for upload.
+struct SystemInit {
+    int64_t n = 0, n_donor = 0;
+    std::vector<double> x, v;         // n*3
+    std::vector<double> m, R0, gam;   // n
+    double G = 1, eps = 0, dt = 1e-3, beta = 1;
+    int contacts = 1;
+    double grow_f0 = 1, grow_rate = 0;
+    int64_t grow_cap = -1;
+    double xl1 = 0.5;
+    double origin[3] = {0, 0, 0};
+    nb_info info{};
+};
+
+// Library-side model setup (the initial-condition recipe of nbody.h).
+double model_roche_rL(double q, double coeff);
+double model_roche_L1(double q);
+nb_status build_system(const nb_desc& d, const nb_params& p, SystemInit& out);
+nb_status check_params(const nb_params& p);
+
+class Batch {
+public:
+    Batch() = default;
+    ~Batch();
+    Batch(const Batch&) = delete;
+    Batch& operator=(const Batch&) = delete;
+
+    // Allocate room for systems of the given padded sizes on `stream`.
+    // prec: 32 or 64 (pair term precision for every system of the batch).
+    nb_status init(const std::vector<int64_t>& n_per_slot, int prec, cudaStream_t stream);
+    // Load a system into slot s (host -> device), make it active and
+    // evaluate its initial acceleration unless `defer_forces`.
+    nb_status load(int s, const SystemInit& si, bool defer_forces = false);
+    // Deactivate a slot (its elements are skipped by every kernel).
+    nb_status unload(int s);
+
+    // Pair-kernel configuration (tile, i-blocking, threads).
+    nb_status set_pair_cfg(const PairCfg& c);
+    const PairCfg& pair_cfg() const { return cfg_; }
+
+    // Enqueue n leap-frog steps of every active system.
+    nb_status step(int64_t n);
+    // Enqueue one force evaluation at the current state (radii of step k+kofs).
+    nb_status eval_forces(int kofs, bool pot, bool energy);
+    // Evaluate forces at the current state and store them as the integrator's
+    // a^k of system `only` (-1: every active system).
+    nb_status init_acc(int only = -1);
+
+    nb_status sync();                 // wait + report device-side flags
+    nb_status forces_out(int s, double* out, bool out_on_device);
+    nb_status diagnostics(int s, nb_diag* out);
+    nb_status get_state(int s, double* xv, double* a, nb_ckpt_meta* meta);
+    nb_status set_state(int s, const double* xv, const double* a, const nb_ckpt_meta* meta);
+
+    int nslots() const { return (int)sc_.size(); }
+    int64_t n_of(int s) const { return sc_[s].n; }
+    int64_t steps_of(int s) const { return k_[s]; }
+    bool active(int s) const { return sc_[s].active != 0; }
+    int64_t device_bytes() const { return bytes_; }
+    cudaStream_t stream() const { return stream_; }
+    int prec() const { return prec_; }
+    const BatchDev& dev() const { return d_; }
+    int nitems() const { return (int)items_.size(); }
+    // pair interactions evaluated per step (sum of n^2 over active systems)
+    double pairs_per_step() const;
+    // capture subsequent multi-step calls in a CUDA graph (per step count)
+    void set_use_graph(bool g) { use_graph_ = g; }
+    // per-phase event timing
+    nb_status set_profile(bool on);
+    nb_status read_profile(nb_prof* out, bool reset);
+
+private:
+    nb_status alloc_(void** p, size_t bytes);
+    nb_status push_consts_();
+    nb_status plan_pairs_();
+    nb_status launch_pairs_(bool pot);
+    nb_status step_body_(int64_t n);
+    void release_();
+
+    int device_ = 0;
+    int sm_count_ = 0;
+    int prec_ = 32;
+    cudaStream_t stream_ = nullptr;
+    BatchDev d_{};
+    std::vector<SysConst> sc_;
+    std::vector<int64_t> k_;
+    std::vector<std::vector<double>> mass_;  // host copy of element masses
+    std::vector<double> rmax_d0_, rmax_a_;
+    PairCfg cfg_{128, 4, 256, 0};
+    std::vector<PairItem> items_;
+    PairItem* items_d_ = nullptr;
+    int items_cap_ = 0;
+    int* counter_d_ = nullptr;
+    bool dynamic_ = false;
+    bool planned_ = false;
+    bool consts_dirty_ = true;
+    int64_t bytes_ = 0;
+    std::vector<void*> allocs_;
+    bool use_graph_ = false;
+    cudaGraphExec_t graph_exec_ = nullptr;
+    int64_t graph_n_ = -1;
+    double* fout_d_ = nullptr;  // staging for forces_out to host
+    int64_t fout_cap_ = 0;
+    // profiling
+    enum Phase { PH_PAIR = 0, PH_CONTACT = 1, PH_UPDATE = 2 };
+    struct ProfMark { cudaEvent_t a, b; int phase; };
+    bool prof_on_ = false;
+    std::vector<ProfMark> prof_marks_;
+    std::vector<cudaEvent_t> event_pool_;
+    double prof_ms_[3] = {0, 0, 0};
+    int64_t prof_n_[3] = {0, 0, 0};
+    int64_t kernels_ = 0;
+    double pairs_done_ = 0;
+    cudaEvent_t prof_begin_();
+    nb_status prof_end_(cudaEvent_t a, int phase);
+    nb_status prof_collect_();
+    bool any_contacts_() const;
+    nb_status contact_pass_(int kofs, bool energy, bool with_keys);
+};
+
+}  // namespace nb

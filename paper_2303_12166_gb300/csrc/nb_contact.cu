@@ -1,0 +1,268 @@
+// nb_contact.cu -- the contact repulsion of Eqs. 5/6 in FP64.
+//
+// Two elements i, j repel only while they overlap, r < R_i + R_j.  With the
+// pair radius R = (R_i + R_j)/2 the bracket of Eqs. 5/6 (read with r^3/12)
+// is pi (4/3 R^3 - R^2 r + r^3/12), the overlap volume of two radius-R
+// spheres; the force is gamma_ij times that volume while the pair closes,
+// (x_j - x_i).(v_j - v_i) < 0, and beta times it otherwise (zero counts as
+// separating), gamma_ij = (gamma_i + gamma_j)/2.  It pushes i away from j.
+//
+// Neighbours are found exactly with a hashed uniform grid whose cell edge h
+// (nb_device.cuh: cell_edge) is at least the largest contact distance, so
+// every overlapping pair lies in the same or an adjacent cell:
+//   1. bin: cellid[i] = packed floor(x_i / h), key[i] = hash(system, cellid),
+//      cnt[key]++   (fused into the drift kernel, or cell_keys_kernel)
+//   2. exclusive scan of cnt -> start (and the number of binned elements)
+//   3. scatter element indices into their bucket, then sort every bucket by
+//      element index, so the summation order below depends only on the
+//      positions and the step index
+//   4. one thread per binned element, in bucket order (spatial neighbours
+//      share warps and cache lines): visit the 27 surrounding cells in a
+//      fixed order; a candidate must carry the visited cell's id (hash
+//      collisions are skipped), pass an FP32 distance pre-test on the FP32
+//      copy with a margin that covers its rounding, and then the exact FP64
+//      test r < R_i + R_j.
+// The force itself is FP64 from the FP64 state, so the stiff overlap term
+// carries no FP32 rounding of the positions.
+#include "nb_device.cuh"
+
+namespace nb {
+namespace {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanPerThread = 4;
+constexpr int kScanBlock = kScanThreads * kScanPerThread;  // 4096 buckets per block
+
+__global__ void cell_keys_kernel(BatchDev b, int kofs) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.ntot) return;
+    const int s = b.sys_of[i];
+    if (s >= 0) {
+        const SysConst& c = b.sc[s];
+        const double h = cell_edge(c, b.sm[s].k + kofs);
+        if (c.active && c.contacts && h > 0.0) {
+            const double4_32a x = b.X[i];
+            bin_element(b, s, i, x.x, x.y, x.z, h);
+            return;
+        }
+    }
+    b.key[i] = 0xffffffffu;
+}
+
+// Block-wide exclusive scan of kScanPerThread values per thread; `total`
+// receives the block total (meaningful in thread kScanThreads-1).
+__device__ __forceinline__ void block_scan(uint32_t (&v)[kScanPerThread], uint32_t& total) {
+    __shared__ uint32_t warp_tot[kScanThreads / 32];
+    uint32_t run = 0;
+#pragma unroll
+    for (int u = 0; u < kScanPerThread; ++u) {
+        const uint32_t c = v[u];
+        v[u] = run;
+        run += c;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < kScanThreads / 32 ? warp_tot[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        warp_tot[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t excl = x - run + (warp > 0 ? warp_tot[warp - 1] : 0u);
+#pragma unroll
+    for (int u = 0; u < kScanPerThread; ++u) v[u] += excl;
+    total = excl + run;
+}
+
+// Phase 1: every block scans kScanBlock counts.
+__global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(const uint32_t* __restrict__ cnt,
+                                                                   uint32_t* __restrict__ start,
+                                                                   uint32_t* __restrict__ blocksum,
+                                                                   uint32_t n) {
+    const uint32_t base = blockIdx.x * kScanBlock + threadIdx.x * kScanPerThread;
+    uint32_t v[kScanPerThread];
+#pragma unroll
+    for (int u = 0; u < kScanPerThread; ++u) v[u] = base + u < n ? cnt[base + u] : 0u;
+    uint32_t total;
+    block_scan(v, total);
+#pragma unroll
+    for (int u = 0; u < kScanPerThread; ++u)
+        if (base + u < n) start[base + u] = v[u];
+    if (threadIdx.x == kScanThreads - 1) blocksum[blockIdx.x] = total;
+}
+
+// Phase 2: one block scans the block totals (at most kScanBlock of them) and
+// stores the grand total (the number of binned elements) after them.
+__global__ void __launch_bounds__(kScanThreads) scan_top_kernel(uint32_t* __restrict__ blocksum,
+                                                                uint32_t nblocks) {
+    const uint32_t base = threadIdx.x * kScanPerThread;
+    uint32_t v[kScanPerThread];
+#pragma unroll
+    for (int u = 0; u < kScanPerThread; ++u) v[u] = base + u < nblocks ? blocksum[base + u] : 0u;
+    uint32_t total;
+    block_scan(v, total);
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kScanPerThread; ++u)
+        if (base + u < nblocks) blocksum[base + u] = v[u];
+    if (threadIdx.x == kScanThreads - 1) blocksum[nblocks] = total;
+}
+
+// Phase 3: add the block offsets.
+__global__ void scan_add_kernel(uint32_t* __restrict__ start, const uint32_t* __restrict__ blocksum,
+                                uint32_t n) {
+    const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < n) start[idx] += blocksum[idx / kScanBlock];
+}
+
+__global__ void scatter_kernel(BatchDev b) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.ntot) return;
+    const uint32_t key = b.key[i];
+    if (key == 0xffffffffu) return;
+    const uint32_t slot = b.start[key] + atomicAdd(&b.fill[key], 1u);
+    b.sorted[slot] = (uint32_t)i;
+}
+
+// Insertion sort of every bucket by element index (buckets hold a few elements).
+__global__ void bucket_sort_kernel(BatchDev b) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= b.nbucket) return;
+    const uint32_t c = b.cnt[k];
+    if (c < 2) return;
+    uint32_t* s = b.sorted + b.start[k];
+    for (uint32_t u = 1; u < c; ++u) {
+        const uint32_t v = s[u];
+        uint32_t w = u;
+        while (w > 0 && s[w - 1] > v) {
+            s[w] = s[w - 1];
+            --w;
+        }
+        s[w] = v;
+    }
+}
+
+__device__ __forceinline__ float max_abs3(float4 p) {
+    return fmaxf(fabsf(p.x), fmaxf(fabsf(p.y), fabsf(p.z)));
+}
+
+template <bool ENERGY>
+__global__ void __launch_bounds__(128) contact_kernel(BatchDev b, int kofs, uint32_t total_idx) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= b.blocksum[total_idx]) return;
+    const uint32_t i = b.sorted[t];
+    const int s = b.sys_of[i];
+    const SysConst& c = b.sc[s];
+    const int64_t k = b.sm[s].k + kofs;
+    const double h = cell_edge(c, k);
+    const double scale = donor_scale(c, k);
+    const int64_t dend = c.off + c.n_donor;
+    const double4_32a xi = b.X[i];
+    const double4_32a vi = b.V[i];
+    const double2 ei = b.E[i];
+    const double Ri = ei.x * ((int64_t)i < dend ? scale : 1.0);
+    const float4 pi4 = b.pos4[i];
+    // FP32 pre-test: |d| < R_i + R_max (R_max = h/2) plus a margin covering
+    // the rounding of both FP32 coordinates (2^-24 relative each, per axis)
+    const float cut = (float)(Ri + 0.5 * h) * 1.0001f;
+    const float mi = max_abs3(pi4);
+    long long cx, cy, cz;
+    unpack_cell(b.cellid[i], cx, cy, cz);
+    const uint32_t mask = b.nbucket - 1;
+    const double beta = c.beta;
+    const double pi = 3.14159265358979323846;
+
+    double ax = 0.0, ay = 0.0, az = 0.0, er = 0.0;
+    for (int oz = -1; oz <= 1; ++oz)
+        for (int oy = -1; oy <= 1; ++oy)
+            for (int ox = -1; ox <= 1; ++ox) {
+                const long long nx = cx + ox, ny = cy + oy, nz = cz + oz;
+                if (nx < -kCellLim || ny < -kCellLim || nz < -kCellLim || nx >= kCellLim ||
+                    ny >= kCellLim || nz >= kCellLim)
+                    continue;
+                const uint64_t cell = pack_cell(nx, ny, nz);
+                const uint32_t key = bucket_of(s, cell, mask);
+                const uint32_t beg = b.start[key];
+                const uint32_t end = beg + b.cnt[key];
+                for (uint32_t slot = beg; slot < end; ++slot) {
+                    const uint32_t j = b.sorted[slot];
+                    if (j == i || b.cellid[j] != cell) continue;
+                    const float4 pj = b.pos4[j];
+                    const float dxf = pj.x - pi4.x, dyf = pj.y - pi4.y, dzf = pj.z - pi4.z;
+                    const float tol = cut + 2.5e-7f * (mi + max_abs3(pj));
+                    if (dxf * dxf + dyf * dyf + dzf * dzf > tol * tol) continue;
+                    if (b.sys_of[j] != s) continue;
+                    const double4_32a xj = b.X[j];
+                    const double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+                    const double d2 = dx * dx + dy * dy + dz * dz;
+                    const double2 ej = b.E[j];
+                    const double Rj = ej.x * ((int64_t)j < dend ? scale : 1.0);
+                    const double Rs = Ri + Rj;
+                    if (!(d2 > 0.0) || d2 >= Rs * Rs * (1.0 + 1e-12)) continue;
+                    const double r = sqrt(d2);
+                    if (!(r < Rs)) continue;
+                    const double R = 0.5 * Rs;
+                    const double g = 0.5 * (ei.y + ej.y);
+                    const double vol = pi * (4.0 / 3.0 * R * R * R - R * R * r + r * r * r / 12.0);
+                    const double4_32a vj = b.V[j];
+                    const double closing =
+                        dx * (vj.x - vi.x) + dy * (vj.y - vi.y) + dz * (vj.z - vi.z);
+                    const double cf = closing < 0.0 ? 1.0 : beta;
+                    // repulsion: acceleration of i along -d/r
+                    const double f = -cf * g * vol / (xi.w * r);
+                    ax += f * dx;
+                    ay += f * dy;
+                    az += f * dz;
+                    if (ENERGY) {
+                        const double U = pi * (R * R * R * R - 4.0 / 3.0 * R * R * R * r +
+                                               0.5 * R * R * r * r - r * r * r * r / 48.0);
+                        er += 0.5 * g * U;
+                    }
+                }
+            }
+    b.cont[i] = make_double4_32a(ax, ay, az, er);
+}
+
+}  // namespace
+
+cudaError_t launch_cell_keys(const BatchDev& b, int kofs, cudaStream_t s) {
+    const int nt = 256;
+    const int64_t nb = (b.ntot + nt - 1) / nt;
+    if (nb > 0) cell_keys_kernel<<<(unsigned)nb, nt, 0, s>>>(b, kofs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_contact(const BatchDev& b, int kofs, bool with_energy, cudaStream_t s) {
+    if (b.ntot == 0) return cudaSuccess;
+    const uint32_t nblk = (b.nbucket + kScanBlock - 1) / kScanBlock;
+    scan_blocks_kernel<<<nblk, kScanThreads, 0, s>>>(b.cnt, b.start, b.blocksum, b.nbucket);
+    scan_top_kernel<<<1, kScanThreads, 0, s>>>(b.blocksum, nblk);
+    scan_add_kernel<<<(b.nbucket + 255) / 256, 256, 0, s>>>(b.start, b.blocksum, b.nbucket);
+    cudaError_t e = cudaMemsetAsync(b.fill, 0, sizeof(uint32_t) * b.nbucket, s);
+    if (e != cudaSuccess) return e;
+    const unsigned ng = (unsigned)((b.ntot + 255) / 256);
+    scatter_kernel<<<ng, 256, 0, s>>>(b);
+    bucket_sort_kernel<<<(b.nbucket + 255) / 256, 256, 0, s>>>(b);
+    const unsigned ngc = (unsigned)((b.ntot + 127) / 128);
+    if (with_energy)
+        contact_kernel<true><<<ngc, 128, 0, s>>>(b, kofs, nblk);
+    else
+        contact_kernel<false><<<ngc, 128, 0, s>>>(b, kofs, nblk);
+    return cudaGetLastError();
+}
+
+// Largest number of buckets one scan handles: kScanBlock blocks of kScanBlock.
+uint64_t contact_max_buckets() { return (uint64_t)kScanBlock * kScanBlock; }
+
+}  // namespace nb

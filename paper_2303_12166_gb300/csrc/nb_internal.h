@@ -1,0 +1,148 @@
+// nb_internal.h -- device data layout and kernel launchers of the library.
+//
+// The unit of work is a *batch*: one or more independent binary systems whose
+// elements live side by side in the same device arrays.  A single system is
+// a batch of one; the batched and served forms use the same kernels.
+//
+// Per element (index i over the whole batch, systems padded to NB_PAD):
+//   X    double4_32a  (x, y, z, m)          FP64 position and mass
+//   V    double4_32a  (vx, vy, vz, 0)       FP64 velocity
+//   A    double4_32a  (ax, ay, az, 0)       FP64 acceleration a^k of the state
+//   E    double2  (R0, gamma)           initial radius and repulsion strength
+//   pos4 float4   (x-o, y-o, z-o, G m)  FP32 copy relative to the system's
+//                                       reference point o (the j-stream of
+//                                       the pair kernel)
+//   sys_of int32                        owning system (-1 for padding)
+// Pair sums land in `part` (double4_32a per element and j-chunk); the contact
+// term in `cont` (double4_32a: a, e_rep).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace nb {
+
+constexpr int NB_PAD = 256;          // system ranges are padded to this many elements
+constexpr int NB_MAX_CHUNKS = 64;    // j-chunks per system (partial sums per element)
+
+// Read-only per-system record (host writes it before launches).
+struct SysConst {
+    int64_t off;        // first element of the system in the batch arrays
+    int64_t n;          // real elements
+    int64_t npad;       // padded range length (multiple of NB_PAD)
+    int64_t n_donor;    // donor elements are [off, off + n_donor)
+    double dt, G, eps, beta;
+    double origin[3];   // reference point of pos4
+    double grow_f0, grow_rate;
+    int64_t grow_cap;   // < 0: no cap
+    double rmax_donor0; // largest initial donor radius
+    double rmax_acc;    // largest accretor radius
+    double xl1;         // L1 distance from the accretor (units of separation)
+    int32_t active;     // 0: skipped by every kernel
+    int32_t contacts;   // 0: gravity only
+    int32_t nchunks;    // j-chunks whose partial sums form the pair term
+    float eps_f;        // eps in FP32
+};
+
+// Device-written per-system record.
+struct SysMut {
+    int64_t k;            // completed steps
+    unsigned long long nonfinite;  // elements found non-finite by the update kernels
+    unsigned int timeout; // a bounded device wait gave up
+    unsigned int pad_;
+};
+
+// One unit of the pair kernel: the i-block [i0, i0 + I) (clipped to the
+// system) against the j-range [j0, j0 + nj) of the same system; the sum is
+// written to partial slot `chunk`.
+struct PairItem {
+    int64_t i0;
+    int64_t j0;
+    int32_t nj;         // multiple of the tile length
+    int32_t sys;
+    int32_t chunk;
+    int32_t iend_rel;   // i-block end relative to i0 (clip), <= I
+};
+
+// Device arrays of a batch (all pointers are device memory).
+struct BatchDev {
+    int64_t ntot;          // total padded elements
+    int32_t nsys;
+    double4_32a* X;
+    double4_32a* V;
+    double4_32a* A;
+    double2* E;
+    float4* pos4;          // ntot + NB_PAD slack
+    int32_t* sys_of;
+    double4_32a* part;         // NB chunks * ntot
+    int32_t nchunk_alloc;  // chunks allocated in part
+    double4_32a* cont;         // ntot
+    const SysConst* sc;
+    SysMut* sm;
+    // contact grid
+    uint32_t nbucket;      // power of two
+    uint32_t* key;         // ntot: bucket of each element (0xffffffff: none)
+    uint64_t* cellid;      // ntot: packed cell coordinates of each element
+    uint32_t* cnt;         // nbucket
+    uint32_t* fill;        // nbucket
+    uint32_t* start;       // nbucket
+    uint32_t* blocksum;    // nbucket / 4096 + 2; [nblocks] = number of binned elements
+    uint32_t* sorted;      // ntot
+    // diagnostics scratch
+    double* red;           // per-block partial sums
+    double* diag_out;      // final diagnostic values
+};
+
+// Kernel launchers (defined in the .cu files).  All return cudaGetLastError().
+// Pair term, FP32 (tile length and i-blocking chosen by the tuner).
+struct PairCfg {
+    int tile;      // j-tile length (64, 128, 256)
+    int bi;        // i-elements per thread (1, 2, 4, 8)
+    int threads;   // threads per block (128 or 256)
+    int grid;      // persistent grid size
+};
+// counter: nullptr -> items are dealt round-robin over the grid; otherwise a
+// zeroed device int that CTAs increment to claim items (dynamic order).
+cudaError_t launch_pair_f32(const BatchDev& b, const PairItem* items, int nitems,
+                            const PairCfg& cfg, bool with_pot, int* counter, cudaStream_t s);
+bool pair_cfg_supported(const PairCfg& cfg);
+int pair_occupancy(const PairCfg& cfg);  // resident CTAs per SM
+// FP64 comparison path: i-blocks of kF64Block elements, j-tiles of 128.
+constexpr int kF64Block = 128;
+constexpr int kF64Tile = 128;
+cudaError_t launch_pair_f64(const BatchDev& b, const PairItem* items, int nitems, int grid,
+                            bool with_pot, int* counter, cudaStream_t s);
+int pair_f64_occupancy();
+
+// Update kernels.  With build_keys the drift kernel also bins the new
+// positions into the contact grid of step k+1 (b.cnt must be zeroed).
+enum KickMode { KICK_START = 0, KICK_FINISH = 1, KICK_FINISH_START = 2 };
+cudaError_t launch_shadow(const BatchDev& b, cudaStream_t s);
+cudaError_t launch_kick(const BatchDev& b, KickMode mode, bool build_keys, cudaStream_t s);
+// k += 1 for every active system (the last kernel of a step)
+cudaError_t launch_advance(const BatchDev& b, cudaStream_t s);
+// out3: n x 3 doubles, the summed acceleration of system `sys` (n real elements)
+cudaError_t launch_sum_forces(const BatchDev& b, int sys, int64_t n, double* out3, cudaStream_t s);
+// A = pair term + contact term for system `only` (-1: all), velocities untouched
+cudaError_t launch_store_acc(const BatchDev& b, int only, cudaStream_t s);
+
+// Contact grid and repulsion (FP64).
+// launch_cell_keys (grid of step k + kofs) needs b.cnt zeroed; launch_contact
+// runs the scan, the scatter, the bucket sort and the repulsion with the
+// radii of step k + kofs.
+cudaError_t launch_cell_keys(const BatchDev& b, int kofs, cudaStream_t s);
+cudaError_t launch_contact(const BatchDev& b, int kofs, bool with_energy, cudaStream_t s);
+uint64_t contact_max_buckets();
+
+// Diagnostics of one system (needs part.w and cont.w from a force pass with
+// the potential): writes NB_DIAG_OUT doubles to b.diag_out:
+//   [0] sum m  [1] E_kin  [2..4] P  [5..7] L  [8..10] sum m x
+//   [11] m donor  [12..14] sum m x donor  [15] m accretor  [16..18] sum m x accretor
+//   [19] E_grav  [20] E_rep  [21] non-finite count
+//   [22..24] com donor  [25..27] com accretor  [28] separation  [29..31] axis
+//   [32] donor elements past L1  [33] their mass
+constexpr int NB_DIAG_NV = 22;
+constexpr int NB_DIAG_OUT = 40;
+cudaError_t launch_diag(const BatchDev& b, int sys, cudaStream_t s);
+size_t diag_scratch_doubles();
+
+}  // namespace nb

@@ -1,0 +1,319 @@
+// nb_update.cu -- the leap-frog update (kick-drift-kick) and the FP64
+// diagnostics.  All state arithmetic is FP64; each update rounds exactly as
+// written (v + (dt/2) a, then x + dt v: no fused multiply-add), so given the
+// same acceleration the state matches a plain double-precision integrator
+// bit for bit.
+//
+// A step k -> k+1 is
+//   v^{k+1/2} = v^k + (dt/2) a^k
+//   x^{k+1}   = x^k + dt v^{k+1/2}                  (then the FP32 copy pos4)
+//   a^{k+1}   = pair term + contact term at (x^{k+1}, v^{k+1/2}, radii(k+1))
+//   v^{k+1}   = v^{k+1/2} + (dt/2) a^{k+1}
+// Between consecutive steps of one nb_step call the closing kick of step k
+// and the opening kick and drift of step k+1 run in one kernel
+// (KICK_FINISH_START) with the same two roundings.  The device step counter
+// k of a system counts drifts: a separate one-thread-per-system kernel
+// advances it after the force evaluation of each step, so no kernel both
+// reads and writes it.
+#include "nb_device.cuh"
+
+namespace nb {
+namespace {
+
+enum { KICK_STORE = 3 };
+
+__device__ __forceinline__ double kick1(double v, double hdt, double a) {
+    return __dadd_rn(v, __dmul_rn(hdt, a));
+}
+
+__device__ __forceinline__ double3 total_acc(const BatchDev& b, const SysConst& c, int64_t i) {
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    for (int ch = 0; ch < c.nchunks; ++ch) {
+        const double4_32a p = b.part[(int64_t)ch * b.ntot + i];
+        ax += p.x;
+        ay += p.y;
+        az += p.z;
+    }
+    if (c.contacts) {
+        const double4_32a q = b.cont[i];
+        ax += q.x;
+        ay += q.y;
+        az += q.z;
+    }
+    return make_double3(ax, ay, az);
+}
+
+__device__ __forceinline__ void write_shadow(const BatchDev& b, const SysConst& c, int64_t i,
+                                             const double4_32a& x) {
+    b.pos4[i] = make_float4((float)(x.x - c.origin[0]), (float)(x.y - c.origin[1]),
+                            (float)(x.z - c.origin[2]), (float)(c.G * x.w));
+}
+
+template <int MODE, bool KEYS>
+__global__ void kick_kernel(BatchDev b, int only) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.ntot) return;
+    const int s = b.sys_of[i];
+    // every element gets a fresh grid key (none for padding / idle systems)
+    if (s < 0 || !b.sc[s].active) {
+        if (KEYS) b.key[i] = 0xffffffffu;
+        return;
+    }
+    if (only >= 0 && s != only) return;
+    const SysConst& c = b.sc[s];
+
+    double4_32a x = b.X[i];
+    double4_32a v = b.V[i];
+    double3 a;
+    if (MODE == KICK_START) {
+        const double4_32a a4 = b.A[i];
+        a = make_double3(a4.x, a4.y, a4.z);
+    } else {
+        a = total_acc(b, c, i);
+        b.A[i] = make_double4_32a(a.x, a.y, a.z, 0.0);
+    }
+    if (MODE == KICK_STORE) return;
+    const double hdt = 0.5 * c.dt;
+    v.x = kick1(v.x, hdt, a.x);
+    v.y = kick1(v.y, hdt, a.y);
+    v.z = kick1(v.z, hdt, a.z);
+    if (MODE == KICK_FINISH) {
+        if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z)))
+            atomicAdd(&b.sm[s].nonfinite, 1ull);
+        b.V[i] = v;
+        return;
+    }
+    if (MODE == KICK_FINISH_START) {
+        v.x = kick1(v.x, hdt, a.x);
+        v.y = kick1(v.y, hdt, a.y);
+        v.z = kick1(v.z, hdt, a.z);
+    }
+    x.x = __dadd_rn(x.x, __dmul_rn(c.dt, v.x));
+    x.y = __dadd_rn(x.y, __dmul_rn(c.dt, v.y));
+    x.z = __dadd_rn(x.z, __dmul_rn(c.dt, v.z));
+    if (!(isfinite(x.x) && isfinite(x.y) && isfinite(x.z) && isfinite(v.x) && isfinite(v.y) &&
+          isfinite(v.z)))
+        atomicAdd(&b.sm[s].nonfinite, 1ull);
+    b.X[i] = x;
+    b.V[i] = v;
+    write_shadow(b, c, i, x);
+    if (KEYS) {
+        const double h = cell_edge(c, b.sm[s].k + 1);
+        if (c.contacts && h > 0.0) bin_element(b, s, i, x.x, x.y, x.z, h);
+        else b.key[i] = 0xffffffffu;
+    }
+}
+
+__global__ void advance_kernel(BatchDev b) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < b.nsys && b.sc[s].active) b.sm[s].k += 1;
+}
+
+__global__ void shadow_kernel(BatchDev b) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.ntot) return;
+    const int s = b.sys_of[i];
+    if (s < 0) return;
+    const SysConst& c = b.sc[s];
+    if (!c.active) return;
+    write_shadow(b, c, i, b.X[i]);
+}
+
+__global__ void sum_forces_kernel(BatchDev b, int s, double* __restrict__ out) {
+    const SysConst& c = b.sc[s];
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= c.n) return;
+    const double3 a = total_acc(b, c, c.off + r);
+    out[3 * r + 0] = a.x;
+    out[3 * r + 1] = a.y;
+    out[3 * r + 2] = a.z;
+}
+
+// ---------------------------------------------------------------- diagnostics
+constexpr int kDiagThreads = 256;
+constexpr int kDiagBlocks = 296;  // fixed: the reduction order depends on n only
+constexpr int NV = NB_DIAG_NV;     // first-pass sums
+constexpr int NV2 = 2;            // second-pass sums
+
+template <int NVAL>
+__device__ void block_reduce_store(double (&v)[NVAL], double* dst) {
+    __shared__ double sh[kDiagThreads / 32][NVAL];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NVAL; ++k) {
+        double x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[warp][k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < NVAL) {
+        double x = 0.0;
+        for (int w = 0; w < kDiagThreads / 32; ++w) x += sh[w][threadIdx.x];
+        dst[blockIdx.x * NVAL + threadIdx.x] = x;
+    }
+}
+
+__global__ void __launch_bounds__(kDiagThreads) diag_pass1_kernel(BatchDev b, int s) {
+    const SysConst& c = b.sc[s];
+    double v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = 0.0;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < c.n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = c.off + r;
+        const double4_32a x = b.X[i];
+        const double4_32a u = b.V[i];
+        const double m = x.w;
+        v[0] += m;
+        v[1] += 0.5 * m * (u.x * u.x + u.y * u.y + u.z * u.z);
+        v[2] += m * u.x;
+        v[3] += m * u.y;
+        v[4] += m * u.z;
+        v[5] += m * (x.y * u.z - x.z * u.y);
+        v[6] += m * (x.z * u.x - x.x * u.z);
+        v[7] += m * (x.x * u.y - x.y * u.x);
+        v[8] += m * x.x;
+        v[9] += m * x.y;
+        v[10] += m * x.z;
+        if (r < c.n_donor) {
+            v[11] += m;
+            v[12] += m * x.x;
+            v[13] += m * x.y;
+            v[14] += m * x.z;
+        } else {
+            v[15] += m;
+            v[16] += m * x.x;
+            v[17] += m * x.y;
+            v[18] += m * x.z;
+        }
+        // pair potential: sum_j G m_j/(r+eps) was accumulated in part.w
+        double pot = 0.0;
+        for (int ch = 0; ch < c.nchunks; ++ch) pot += b.part[(int64_t)ch * b.ntot + i].w;
+        v[19] += -0.5 * m * pot;
+        if (c.contacts) v[20] += b.cont[i].w;
+        if (!(isfinite(x.x) && isfinite(x.y) && isfinite(x.z) && isfinite(u.x) &&
+              isfinite(u.y) && isfinite(u.z)))
+            v[21] += 1.0;
+    }
+    block_reduce_store<NV>(v, b.red);
+}
+
+// Sums the block partials in a fixed order and derives the L1 plane.
+// diag_out: [0, NV) sums, [NV .. NV+6) com_donor, com_accretor,
+// NV+6 separation, NV+7 .. NV+9 axis unit vector.
+__global__ void diag_final1_kernel(BatchDev b, int s, int nblk) {
+    __shared__ double tot[NV];
+    if (threadIdx.x < NV) {
+        double x = 0.0;
+        for (int k = 0; k < nblk; ++k) x += b.red[k * NV + threadIdx.x];
+        tot[threadIdx.x] = x;
+        b.diag_out[threadIdx.x] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double cd[3] = {0, 0, 0}, ca[3] = {0, 0, 0};
+        for (int d = 0; d < 3; ++d) {
+            cd[d] = tot[11] > 0 ? tot[12 + d] / tot[11] : 0.0;
+            ca[d] = tot[15] > 0 ? tot[16 + d] / tot[15] : 0.0;
+            b.diag_out[NV + d] = cd[d];
+            b.diag_out[NV + 3 + d] = ca[d];
+        }
+        const double dx = cd[0] - ca[0], dy = cd[1] - ca[1], dz = cd[2] - ca[2];
+        const double sep = sqrt(dx * dx + dy * dy + dz * dz);
+        b.diag_out[NV + 6] = sep;
+        b.diag_out[NV + 7] = sep > 0 ? dx / sep : 0.0;
+        b.diag_out[NV + 8] = sep > 0 ? dy / sep : 0.0;
+        b.diag_out[NV + 9] = sep > 0 ? dz / sep : 0.0;
+    }
+}
+
+__global__ void __launch_bounds__(kDiagThreads) diag_pass2_kernel(BatchDev b, int s) {
+    const SysConst& c = b.sc[s];
+    const double* d = b.diag_out;
+    const double ca[3] = {d[NV + 3], d[NV + 4], d[NV + 5]};
+    const double sep = d[NV + 6];
+    const double ux = d[NV + 7], uy = d[NV + 8], uz = d[NV + 9];
+    const double plane = c.xl1 * sep;
+    double v[NV2] = {0.0, 0.0};
+    if (c.n_donor > 0 && c.n_donor < c.n && sep > 0) {
+        for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < c.n_donor;
+             r += (int64_t)gridDim.x * blockDim.x) {
+            const double4_32a x = b.X[c.off + r];
+            const double proj = (x.x - ca[0]) * ux + (x.y - ca[1]) * uy + (x.z - ca[2]) * uz;
+            if (proj < plane) {
+                v[0] += 1.0;
+                v[1] += x.w;
+            }
+        }
+    }
+    block_reduce_store<NV2>(v, b.red);
+}
+
+__global__ void diag_final2_kernel(BatchDev b, int nblk) {
+    if (threadIdx.x < NV2) {
+        double x = 0.0;
+        for (int k = 0; k < nblk; ++k) x += b.red[k * NV2 + threadIdx.x];
+        b.diag_out[NV + 10 + threadIdx.x] = x;
+    }
+}
+
+template <int MODE, bool KEYS>
+cudaError_t kick_t(const BatchDev& b, cudaStream_t s, int only = -1) {
+    const int nt = 256;
+    int64_t n = b.ntot > b.nsys ? b.ntot : b.nsys;
+    const unsigned ng = (unsigned)((n + nt - 1) / nt);
+    if (ng) kick_kernel<MODE, KEYS><<<ng, nt, 0, s>>>(b, only);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_shadow(const BatchDev& b, cudaStream_t s) {
+    const int nt = 256;
+    const unsigned ng = (unsigned)((b.ntot + nt - 1) / nt);
+    if (ng) shadow_kernel<<<ng, nt, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kick(const BatchDev& b, KickMode mode, bool keys, cudaStream_t s) {
+    switch (mode) {
+        case KICK_START:
+            return keys ? kick_t<KICK_START, true>(b, s) : kick_t<KICK_START, false>(b, s);
+        case KICK_FINISH:
+            return kick_t<KICK_FINISH, false>(b, s);
+        case KICK_FINISH_START:
+            return keys ? kick_t<KICK_FINISH_START, true>(b, s)
+                        : kick_t<KICK_FINISH_START, false>(b, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_advance(const BatchDev& b, cudaStream_t s) {
+    advance_kernel<<<(b.nsys + 127) / 128, 128, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_store_acc(const BatchDev& b, int only, cudaStream_t s) {
+    return kick_t<KICK_STORE, false>(b, s, only);
+}
+
+cudaError_t launch_sum_forces(const BatchDev& b, int sys, int64_t n, double* out3,
+                              cudaStream_t s) {
+    const int nt = 256;
+    const unsigned ng = (unsigned)((n + nt - 1) / nt);
+    if (ng) sum_forces_kernel<<<ng, nt, 0, s>>>(b, sys, out3);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diag(const BatchDev& b, int sys, cudaStream_t s) {
+    diag_pass1_kernel<<<kDiagBlocks, kDiagThreads, 0, s>>>(b, sys);
+    diag_final1_kernel<<<1, 64, 0, s>>>(b, sys, kDiagBlocks);
+    diag_pass2_kernel<<<kDiagBlocks, kDiagThreads, 0, s>>>(b, sys);
+    diag_final2_kernel<<<1, 32, 0, s>>>(b, kDiagBlocks);
+    return cudaGetLastError();
+}
+
+size_t diag_scratch_doubles() { return (size_t)kDiagBlocks * NV; }
+
+}  // namespace nb

@@ -1,0 +1,321 @@
+"""ctypes binding of include/nbody.h -- argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of its own: all work runs in libnbody.so (CUDA kernels for
+sm_103a).  Importing this module fails loudly if the library has not been
+built; there is no fallback.
+
+Non-OK statuses raise :class:`NbError` (status code + nb_last_error text),
+except ``nb_poll``'s NB_PENDING, which is returned.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libnbody.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"libnbody.so not found at {LIB_PATH}; build it with "
+        "`python -m paper_2303_12166_gb300.build` (needs nvcc, CUDA 13)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+_D = ctypes.c_double
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_U32 = ctypes.c_uint32
+_U64 = ctypes.c_uint64
+_P = ctypes.c_void_p
+
+NB_OK, NB_EINVAL, NB_ENOMEM, NB_EBUDGET, NB_ECUDA = 0, 1, 2, 3, 4
+NB_ENONFINITE, NB_ETIMEOUT, NB_PENDING, NB_ENOTFOUND = 5, 6, 7, 8
+NB_GRAVITY_ONLY, NB_NO_SPIN = 1, 2
+
+
+class nb_params(ctypes.Structure):
+    _fields_ = [("G", _D), ("eps", _D), ("dt", _D), ("beta", _D), ("kappa_gamma", _D),
+                ("rl_coeff", _D), ("force_prec", _I32), ("flags", _U32)]
+
+
+class nb_desc(ctypes.Structure):
+    _fields_ = [("n_donor", _I64), ("n_accretor", _I64), ("q", _D), ("sep", _D),
+                ("f_donor", _D), ("f_accretor", _D), ("expand_rate", _D),
+                ("expand_steps", _I64), ("sigma_v", _D), ("seed", _U64), ("stream", _U64),
+                ("xv_in", ctypes.POINTER(_D)), ("mrg_in", ctypes.POINTER(_D))]
+
+
+class nb_diag(ctypes.Structure):
+    _fields_ = [("step", _I64), ("time", _D), ("e_kin", _D), ("e_grav", _D), ("e_rep", _D),
+                ("e_tot", _D), ("p", _D * 3), ("l", _D * 3), ("com", _D * 3),
+                ("com_donor", _D * 3), ("com_accretor", _D * 3), ("separation", _D),
+                ("r_donor", _D), ("n_past_L1", _I64), ("m_past_L1", _D),
+                ("n_nonfinite", _I64)]
+
+
+class nb_ckpt_meta(ctypes.Structure):
+    _fields_ = [("n", _I64), ("step", _I64), ("origin", _D * 3)]
+
+
+class nb_prof(ctypes.Structure):
+    _fields_ = [("pair_launches", _I64), ("pair_ms", _D), ("contact_launches", _I64),
+                ("contact_ms", _D), ("update_launches", _I64), ("update_ms", _D),
+                ("kernels", _I64), ("pairs", _D)]
+
+
+class nb_info(ctypes.Structure):
+    _fields_ = [("n", _I64), ("n_donor", _I64), ("n_accretor", _I64), ("m_donor", _D),
+                ("m_accretor", _D), ("r_donor0", _D), ("r_accretor", _D),
+                ("gamma_donor", _D), ("gamma_accretor", _D), ("rl_donor", _D),
+                ("rl_accretor", _D), ("x_L1", _D), ("device_bytes", _I64)]
+
+
+def _sig(name, res, args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_sig("nb_abi_version", ctypes.c_int, [])
+_sig("nb_status_str", ctypes.c_char_p, [ctypes.c_int])
+_sig("nb_last_error", ctypes.c_char_p, [])
+_sig("nb_params_default", ctypes.c_int, [ctypes.POINTER(nb_params)])
+_sig("nb_desc_default", ctypes.c_int, [ctypes.POINTER(nb_desc)])
+_sig("nb_roche_rL", _D, [_D, _D])
+_sig("nb_roche_L1", _D, [_D])
+_sig("nb_create_system", ctypes.c_int,
+     [ctypes.POINTER(nb_desc), ctypes.POINTER(nb_params), _P, ctypes.POINTER(_P)])
+_sig("nb_destroy", None, [_P])
+_sig("nb_get_info", ctypes.c_int, [_P, ctypes.POINTER(nb_info)])
+_sig("nb_forces", ctypes.c_int, [_P, _P, ctypes.c_int])
+_sig("nb_step", ctypes.c_int, [_P, _I64])
+_sig("nb_sync", ctypes.c_int, [_P])
+_sig("nb_diagnostics", ctypes.c_int, [_P, ctypes.POINTER(nb_diag)])
+_sig("nb_get_state", ctypes.c_int, [_P, _P, _P, ctypes.POINTER(nb_ckpt_meta)])
+_sig("nb_set_state", ctypes.c_int, [_P, _P, _P, ctypes.POINTER(nb_ckpt_meta)])
+_sig("nb_profile", ctypes.c_int, [_P, ctypes.c_int])
+_sig("nb_profile_read", ctypes.c_int, [_P, ctypes.POINTER(nb_prof), ctypes.c_int])
+
+
+class NbError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = int(status)
+        msg = _lib.nb_last_error().decode(errors="replace")
+        name = _lib.nb_status_str(self.status).decode()
+        super().__init__(f"{where}: {name} ({self.status}): {msg}")
+
+
+def _check(status: int, where: str) -> int:
+    if status != NB_OK:
+        raise NbError(status, where)
+    return status
+
+
+def _stream_ptr(stream) -> int:
+    """Accept None (default stream), an int handle or a torch.cuda.Stream."""
+    if stream is None:
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(_D))
+
+
+# ------------------------------------------------------------------ library
+def nb_abi_version() -> int:
+    return int(_lib.nb_abi_version())
+
+
+def nb_status_str(status: int) -> str:
+    return _lib.nb_status_str(int(status)).decode()
+
+
+def nb_last_error() -> str:
+    return _lib.nb_last_error().decode(errors="replace")
+
+
+def nb_params_default(**overrides) -> nb_params:
+    p = nb_params()
+    _check(_lib.nb_params_default(ctypes.byref(p)), "nb_params_default")
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def nb_desc_default(**overrides) -> nb_desc:
+    d = nb_desc()
+    _check(_lib.nb_desc_default(ctypes.byref(d)), "nb_desc_default")
+    for k, v in overrides.items():
+        setattr(d, k, v)
+    return d
+
+
+def nb_roche_rL(q: float, coeff: float = 0.69) -> float:
+    return float(_lib.nb_roche_rL(float(q), float(coeff)))
+
+
+def nb_roche_L1(q: float) -> float:
+    return float(_lib.nb_roche_L1(float(q)))
+
+
+# ------------------------------------------------------------------ single system
+def nb_create_system(desc: nb_desc, params: nb_params, stream=None, xv_in=None, mrg_in=None):
+    """Returns an opaque handle (int).  xv_in (n,6) / mrg_in (n,3) are optional
+    host arrays copied during the call."""
+    keep = []
+    if xv_in is not None:
+        a = np.ascontiguousarray(xv_in, dtype=np.float64).reshape(-1)
+        keep.append(a)
+        desc.xv_in = _dptr(a)
+    if mrg_in is not None:
+        a = np.ascontiguousarray(mrg_in, dtype=np.float64).reshape(-1)
+        keep.append(a)
+        desc.mrg_in = _dptr(a)
+    h = _P()
+    try:
+        _check(_lib.nb_create_system(ctypes.byref(desc), ctypes.byref(params),
+                                     _P(_stream_ptr(stream)), ctypes.byref(h)),
+               "nb_create_system")
+    finally:
+        desc.xv_in = None
+        desc.mrg_in = None
+    return h.value
+
+
+def nb_destroy(h) -> None:
+    _lib.nb_destroy(_P(h))
+
+
+def nb_get_info(h) -> nb_info:
+    info = nb_info()
+    _check(_lib.nb_get_info(_P(h), ctypes.byref(info)), "nb_get_info")
+    return info
+
+
+def nb_forces(h, out=None):
+    """Accelerations (n,3) FP64 at the current state.  With ``out`` a CUDA
+    tensor of n*3 float64 the result is written there (device pointer);
+    otherwise a new numpy array is returned."""
+    if out is not None and hasattr(out, "data_ptr"):
+        _check(_lib.nb_forces(_P(h), _P(out.data_ptr()), 1), "nb_forces")
+        return out
+    n = nb_get_info(h).n
+    a = np.empty((n, 3), dtype=np.float64) if out is None else out
+    _check(_lib.nb_forces(_P(h), a.ctypes.data_as(_P), 0), "nb_forces")
+    return a
+
+
+def nb_step(h, nsteps: int) -> None:
+    _check(_lib.nb_step(_P(h), int(nsteps)), "nb_step")
+
+
+def nb_sync(h) -> None:
+    _check(_lib.nb_sync(_P(h)), "nb_sync")
+
+
+def _diag_dict(d: nb_diag) -> dict:
+    out = {}
+    for name, _ in nb_diag._fields_:
+        v = getattr(d, name)
+        out[name] = np.array(v[:]) if isinstance(v, ctypes.Array) else v
+    return out
+
+
+def nb_diagnostics(h) -> dict:
+    d = nb_diag()
+    _check(_lib.nb_diagnostics(_P(h), ctypes.byref(d)), "nb_diagnostics")
+    return _diag_dict(d)
+
+
+def nb_get_state(h, with_acc: bool = True):
+    """Returns (xv (n,6), a (n,3) or None, meta)."""
+    n = nb_get_info(h).n
+    xv = np.empty((n, 6), dtype=np.float64)
+    a = np.empty((n, 3), dtype=np.float64) if with_acc else None
+    meta = nb_ckpt_meta()
+    _check(_lib.nb_get_state(_P(h), xv.ctypes.data_as(_P),
+                             a.ctypes.data_as(_P) if a is not None else None,
+                             ctypes.byref(meta)), "nb_get_state")
+    return xv, a, meta
+
+
+def nb_set_state(h, xv, a, meta: nb_ckpt_meta) -> None:
+    xv = np.ascontiguousarray(xv, dtype=np.float64)
+    a = None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+    _check(_lib.nb_set_state(_P(h), xv.ctypes.data_as(_P),
+                             a.ctypes.data_as(_P) if a is not None else None,
+                             ctypes.byref(meta)), "nb_set_state")
+
+
+def nb_profile(h, enable: bool) -> None:
+    _check(_lib.nb_profile(_P(h), 1 if enable else 0), "nb_profile")
+
+
+def nb_profile_read(h, reset: bool = False) -> dict:
+    p = nb_prof()
+    _check(_lib.nb_profile_read(_P(h), ctypes.byref(p), 1 if reset else 0), "nb_profile_read")
+    return {name: getattr(p, name) for name, _ in nb_prof._fields_}
+
+
+class System:
+    """Owning wrapper of an nb_system_t handle."""
+
+    def __init__(self, desc: nb_desc | None = None, params: nb_params | None = None,
+                 stream=None, xv_in=None, mrg_in=None):
+        self.desc = desc if desc is not None else nb_desc_default()
+        self.params = params if params is not None else nb_params_default()
+        self.h = nb_create_system(self.desc, self.params, stream, xv_in=xv_in, mrg_in=mrg_in)
+        self.info = nb_get_info(self.h)
+
+    @property
+    def n(self) -> int:
+        return int(self.info.n)
+
+    def forces(self, out=None):
+        return nb_forces(self.h, out)
+
+    def step(self, nsteps: int):
+        nb_step(self.h, nsteps)
+
+    def sync(self):
+        nb_sync(self.h)
+
+    def diagnostics(self) -> dict:
+        return nb_diagnostics(self.h)
+
+    def get_state(self, with_acc: bool = True):
+        return nb_get_state(self.h, with_acc)
+
+    def set_state(self, xv, a, meta):
+        nb_set_state(self.h, xv, a, meta)
+
+    def profile(self, enable: bool = True):
+        nb_profile(self.h, enable)
+
+    def profile_read(self, reset: bool = False) -> dict:
+        return nb_profile_read(self.h, reset)
+
+    def close(self):
+        if self.h:
+            nb_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,76 @@
+"""The C ABI library loads and exports every entry point include/nbody.h
+declares; host-only calls behave; without a GPU the compute calls fail
+loudly (no CPU fallback)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", h)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**\s*(nb_[A-Za-z0-9_]+)\s*\(",
+                             txt, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_2303_12166_gb300 import build
+    return build.build()
+
+
+def test_every_declared_symbol_is_exported(lib_path):
+    names = _declared()
+    assert {"nb_create_system", "nb_step", "nb_forces", "nb_diagnostics"} <= names
+    lib = ctypes.CDLL(lib_path)
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_calls(lib_path, orc):
+    from paper_2303_12166_gb300 import nbody as nbm
+    assert nbm.nb_abi_version() == 1
+    assert nbm.nb_status_str(nbm.NB_EINVAL) == "invalid argument"
+    p = nbm.nb_params_default()
+    assert (p.G, p.eps, p.dt, p.beta, p.kappa_gamma, p.rl_coeff, p.force_prec) == \
+        (1.0, 0.01, 1e-3, 0.5, 8.0, 0.69, 32)
+    d = nbm.nb_desc_default()
+    assert (d.n_donor, d.n_accretor, d.q) == (512, 512, 0.5)
+    # the library's Eq. 3 and L1 agree with the oracle's
+    for q in [0.1, 0.2, 0.3, 0.5, 1.0, 2.0, 5.0]:
+        assert nbm.nb_roche_rL(q) == pytest.approx(orc.roche_rL(q), rel=1e-14)
+        assert nbm.nb_roche_L1(q) == pytest.approx(orc.roche_L1(q), abs=1e-14)
+
+
+def test_invalid_parameters_rejected(lib_path):
+    from paper_2303_12166_gb300 import nbody as nbm
+    cases = [dict(dt=0.0), dict(beta=1.5), dict(eps=-1.0), dict(force_prec=16)]
+    for bad in cases:
+        with pytest.raises(nbm.NbError) as ei:
+            nbm.nb_create_system(nbm.nb_desc_default(), nbm.nb_params_default(**bad))
+        assert ei.value.status == nbm.NB_EINVAL
+    for bad in [dict(n_donor=0, n_accretor=0), dict(q=0.0), dict(f_donor=-1.0),
+                dict(expand_rate=-1e-3, expand_steps=-1)]:
+        with pytest.raises(nbm.NbError) as ei:
+            nbm.nb_create_system(nbm.nb_desc_default(**bad), nbm.nb_params_default())
+        assert ei.value.status == nbm.NB_EINVAL
+
+
+def test_no_gpu_fails_loudly(lib_path):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2303_12166_gb300 import nbody as nbm
+    with pytest.raises(nbm.NbError) as ei:
+        nbm.nb_create_system(nbm.nb_desc_default(n_donor=8, n_accretor=8), nbm.nb_params_default())
+    assert ei.value.status in (nbm.NB_ECUDA, nbm.NB_ENOMEM)

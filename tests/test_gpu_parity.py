@@ -1,0 +1,264 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (from the arithmetic):
+  * FP32 pair term: per-step accelerations within 1e-5 RMS-relative.
+  * FP64 pair term: within 1e-12 RMS-relative (summation order only).
+  * 100 steps of the 1,024-element binary: positions within 1e-4 (max abs).
+  * Initial conditions: both sides build them from the same recipe and the
+    same SplitMix64 draws; equal to 1e-14.
+"""
+import numpy as np
+import pytest
+
+import synth
+from nbtest import oracle_ic, rms_rel, workload_kwargs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nbm():
+    from paper_2303_12166_gb300 import build
+    build.build()
+    from paper_2303_12166_gb300 import nbody
+    return nbody
+
+
+def _make(nbm, desc, params, **kw):
+    d = nbm.nb_desc_default(**desc)
+    p = nbm.nb_params_default(**params)
+    return nbm.System(d, p, **kw)
+
+
+def _state(sys_):
+    xv, a, meta = sys_.get_state()
+    return xv[:, :3], xv[:, 3:], a, meta
+
+
+# ---------------------------------------------------------------- initial state
+def test_initial_conditions_match_oracle(nbm, orc):
+    desc, params = workload_kwargs("binary_1k")
+    with _make(nbm, desc, params) as s:
+        x, v, a, meta = _state(s)
+        ox, ov, om, oR, og = oracle_ic(orc, desc, params)
+        assert np.abs(x - ox).max() < 1e-14
+        assert np.abs(v - ov).max() < 1e-14
+        info = s.info
+        assert info.m_donor == pytest.approx(om[0], rel=1e-15)
+        assert info.r_donor0 == pytest.approx(oR[0], rel=1e-14)
+        assert info.gamma_accretor == pytest.approx(og[-1], rel=1e-13)
+        assert meta.step == 0
+
+
+# ---------------------------------------------------------------- one force evaluation
+@pytest.mark.parametrize("prec,tol", [(32, 1e-5), (64, 1e-12)])
+def test_forces_binary_1k(nbm, orc, prec, tol):
+    desc, params = workload_kwargs("binary_1k")
+    params = dict(params, force_prec=prec)
+    with _make(nbm, desc, params) as s:
+        a = s.forces()
+        x, v, a_stored, _ = _state(s)
+        ox, ov, om, oR, og = oracle_ic(orc, desc, params)
+        ref = orc.forces(ox, ov, om, oR, og, G=1.0, eps=params["eps"], beta=params["beta"])
+        assert rms_rel(a, ref) <= tol
+        # the stored a^0 equals the evaluation at the same state
+        assert np.array_equal(a, a_stored)
+
+
+def _random_system(nbm, n, seed, prec, spread=0.3):
+    """A cloud of n elements with per-element masses, radii and strengths
+    chosen so that many pairs overlap (both contact branches)."""
+    x, v = synth.cloud(n, seed, radius=spread, speed=0.2)
+    st = synth.Stream(seed, 11)
+    m = 0.5 + st.uniform(n)
+    R = (0.02 + 0.02 * st.uniform(n)) * (spread / 0.3) * max(1.0, (64.0 / max(n, 1)) ** (1 / 3))
+    gam = 1.0 + st.uniform(n)
+    nd = n // 2
+    desc = dict(n_donor=nd, n_accretor=n - nd, q=0.5, f_donor=0.8, f_accretor=0.5)
+    params = dict(eps=0.003, dt=1e-3, beta=0.35, force_prec=prec)
+    xv = np.concatenate([x, v], 1)
+    mrg = np.stack([m, R, gam], 1)
+    return _make(nbm, desc, params, xv_in=xv, mrg_in=mrg), (x, v, m, R, gam)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 32, 33, 63, 64, 65, 255, 256, 257, 1000, 2049])
+@pytest.mark.parametrize("prec,tol", [(32, 1e-5), (64, 1e-12)])
+def test_forces_ragged_sizes(nbm, orc, n, prec, tol):
+    s, (x, v, m, R, gam) = _random_system(nbm, n, 100 + n, prec)
+    with s:
+        a = s.forces()
+        ref = orc.forces(x, v, m, R, gam, G=1.0, eps=0.003, beta=0.35)
+        if n == 1:
+            assert np.all(a == 0.0)
+        else:
+            assert rms_rel(a, ref) <= tol
+            # and element by element against the largest acceleration
+            assert np.abs(a - ref).max() <= 50 * tol * np.abs(ref).max()
+
+
+def test_contact_branches_exercised(orc):
+    x, v = synth.cloud(257, 357, radius=0.3, speed=0.2)
+    st = synth.Stream(357, 11)
+    st.uniform(257)
+    R = (0.02 + 0.02 * st.uniform(257))
+    conv = div = 0
+    for i in range(257):
+        d = x - x[i]
+        r = np.sqrt((d * d).sum(1))
+        c = (r < R + R[i]) & (r > 0)
+        dv = ((v - v[i]) * d).sum(1)
+        conv += int((c & (dv < 0)).sum())
+        div += int((c & (dv >= 0)).sum())
+    assert conv > 50 and div > 50
+
+
+# ---------------------------------------------------------------- trajectories
+def test_trajectory_binary_1k_100_steps(nbm, orc):
+    desc, params = workload_kwargs("binary_1k")
+    with _make(nbm, desc, params) as s:
+        s.step(100)
+        s.sync()
+        x, v, a, meta = _state(s)
+        assert meta.step == 100
+    ox, ov, om, oR, og = oracle_ic(orc, desc, params)
+    rx, rv, ra = orc.run(ox, ov, om, oR, og, G=1.0, eps=params["eps"], beta=params["beta"],
+                         dt=params["dt"], nsteps=100, n_donor=desc["n_donor"])
+    assert np.abs(x - rx).max() <= 1e-4
+    assert np.sqrt(((x - rx) ** 2).mean()) <= 1e-5
+
+
+def test_trajectory_fp64_path(nbm, orc):
+    desc, params = workload_kwargs("binary_1k")
+    params = dict(params, force_prec=64)
+    with _make(nbm, desc, params) as s:
+        s.step(20)
+        s.sync()
+        x, v, a, _ = _state(s)
+    ox, ov, om, oR, og = oracle_ic(orc, desc, params)
+    rx, rv, ra = orc.run(ox, ov, om, oR, og, G=1.0, eps=params["eps"], beta=params["beta"],
+                         dt=params["dt"], nsteps=20, n_donor=desc["n_donor"])
+    assert np.abs(x - rx).max() <= 1e-9
+
+
+def test_donor_expansion_trajectory(nbm, orc):
+    """Donor radius grows each step (rate in r_L per step, capped)."""
+    desc = dict(n_donor=1536, n_accretor=512, q=0.3, f_donor=0.9, f_accretor=0.5,
+                expand_rate=5e-3, expand_steps=30, sigma_v=1e-3, seed=4, stream=0)
+    params = dict(eps=0.005, dt=5e-4, beta=0.5)
+    with _make(nbm, desc, params) as s:
+        s.step(40)
+        s.sync()
+        x, v, a, meta = _state(s)
+        d = s.diagnostics()
+    ox, ov, om, oR, og = oracle_ic(orc, desc, dict(params, G=1.0, kappa_gamma=8.0, rl_coeff=0.69))
+    rx, rv, ra = orc.run(ox, ov, om, oR, og, G=1.0, eps=0.005, beta=0.5, dt=5e-4, nsteps=40,
+                         n_donor=1536, grow_f0=0.9, grow_rate=5e-3, grow_cap=30)
+    assert np.abs(x - rx).max() <= 1e-4
+    assert d["r_donor"] == pytest.approx(orc.donor_scale(40, 0.9, 5e-3, 30), rel=1e-15)
+
+
+# ---------------------------------------------------------------- full sizes, sampled
+@pytest.mark.parametrize("name,nrows", [("binary_64k", 384), ("binary_1m", 192)])
+def test_forces_full_size_sampled(nbm, orc, name, nrows):
+    desc, params = workload_kwargs(name)
+    with _make(nbm, desc, params) as s:
+        a = s.forces()
+        x, v, _, _ = _state(s)
+        n = s.n
+    ox, ov, om, oR, og = oracle_ic(orc, desc, params)
+    assert np.abs(x - ox).max() < 1e-14
+    nd = desc["n_donor"]
+    rows = np.unique(np.concatenate([
+        [0, 1, nd - 1, nd, nd + 1, n - 1],
+        (synth.u01(5, 9, nrows) * n).astype(np.int64)]))
+    ref = orc.forces_rows(rows, ox, ov, om, oR, og, G=1.0, eps=params["eps"], beta=params["beta"])
+    assert rms_rel(a[rows], ref) <= 1e-5
+
+
+# ---------------------------------------------------------------- diagnostics
+def test_diagnostics_match_oracle(nbm, orc):
+    desc, params = workload_kwargs("binary_1k")
+    with _make(nbm, desc, params) as s:
+        s.step(10)
+        d = s.diagnostics()
+        x, v, _, _ = _state(s)
+    ox, ov, om, oR, og = oracle_ic(orc, desc, params)
+    ref = orc.diagnostics(x, v, om, oR, og, eps=params["eps"], n_donor=desc["n_donor"], q=desc["q"])
+    assert d["step"] == 10
+    assert d["e_kin"] == pytest.approx(ref["E_kin"], rel=1e-12)
+    assert d["e_rep"] == pytest.approx(ref["E_rep"], rel=1e-10)
+    assert d["e_grav"] == pytest.approx(ref["E_grav"], rel=1e-6)  # FP32 pair potential
+    assert np.allclose(d["p"], ref["P"], rtol=0, atol=1e-14)
+    assert np.allclose(d["l"], ref["L"], rtol=1e-12, atol=1e-15)
+    assert np.allclose(d["com"], ref["com"], rtol=0, atol=1e-14)
+    assert np.allclose(d["com_donor"], ref["com_donor"], rtol=0, atol=1e-14)
+    assert d["separation"] == pytest.approx(ref["separation"], rel=1e-13)
+    assert d["n_past_L1"] == ref["n_past_L1"]
+    assert d["n_nonfinite"] == 0
+
+
+# ---------------------------------------------------------------- determinism, checkpoints
+def test_runs_are_bitwise_reproducible(nbm):
+    desc, params = workload_kwargs("binary_1k")
+    out = []
+    for _ in range(2):
+        with _make(nbm, desc, params) as s:
+            s.step(25)
+            out.append(_state(s))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_checkpoint_resume_bitwise(nbm):
+    desc, params = workload_kwargs("binary_1k")
+    desc = dict(desc, expand_rate=1e-3, expand_steps=25)
+    with _make(nbm, desc, params) as s:
+        s.step(40)
+        x_ref, v_ref, a_ref, _ = _state(s)
+    with _make(nbm, desc, params) as s:
+        s.step(15)
+        xv, a, meta = s.get_state()
+    with _make(nbm, desc, params) as s2:
+        s2.set_state(xv, a, meta)
+        s2.step(25)
+        x2, v2, a2, meta2 = _state(s2)
+    assert meta2.step == 40
+    assert np.array_equal(x_ref, x2) and np.array_equal(v_ref, v2) and np.array_equal(a_ref, a2)
+
+
+def test_steps_split_across_calls_bitwise(nbm):
+    desc, params = workload_kwargs("binary_1k")
+    with _make(nbm, desc, params) as s:
+        s.step(12)
+        r1 = _state(s)
+    with _make(nbm, desc, params) as s:
+        for _ in range(3):
+            s.step(4)
+        r2 = _state(s)
+    assert np.array_equal(r1[0], r2[0]) and np.array_equal(r1[1], r2[1])
+
+
+# ---------------------------------------------------------------- failure detection
+def test_nonfinite_state_is_reported(nbm):
+    """An element whose drift overflows to infinity is flagged by the update
+    kernel and reported by nb_sync as NB_ENONFINITE (no GPU fault)."""
+    n = 8
+    x, v = synth.cloud(n, 3, radius=0.5)
+    v[3] = [1e308, 0.0, 0.0]
+    desc = dict(n_donor=4, n_accretor=4, q=1.0)
+    params = dict(eps=0.01, dt=10.0, flags=nbm.NB_GRAVITY_ONLY)
+    with _make(nbm, desc, params, xv_in=np.concatenate([x, v], 1)) as s:
+        s.step(1)
+        with pytest.raises(nbm.NbError) as ei:
+            s.sync()
+        assert ei.value.status == nbm.NB_ENONFINITE
+        assert s.diagnostics()["n_nonfinite"] >= 1
+
+
+def test_gravity_only_flag(nbm, orc):
+    desc, params = workload_kwargs("binary_1k")
+    params = dict(params, flags=nbm.NB_GRAVITY_ONLY)
+    with _make(nbm, desc, params) as s:
+        a = s.forces()
+    ox, ov, om, oR, og = oracle_ic(orc, desc, params)
+    ref = orc.forces(ox, ov, om, oR, np.zeros_like(og), G=1.0, eps=params["eps"])
+    assert rms_rel(a, ref) <= 1e-5
