@@ -237,6 +237,11 @@ def run_ours(args):
     params = nbm.nb_params_default(eps=w["eps"], dt=w["dt"], beta=0.5,
                                    force_prec=64 if args.fp64 else 32)
     sysm = nbm.System(desc, params, stream=stream)
+    if args.pair_cfg:
+        sysm.set_pair_cfg(*[int(v) for v in args.pair_cfg.split(",")])
+        tuned = sysm.pair_cfg()
+    else:
+        tuned = sysm.autotune(2) if not args.fp64 else sysm.pair_cfg()
 
     sysm.step(args.warmup)
     sysm.sync()
@@ -306,6 +311,8 @@ def run_ours(args):
     if rank == 0:
         cfg = _config(args.workload, w, {
             "force_prec": 64 if args.fp64 else 32,
+            "pair_cfg": {k: tuned[k] for k in ("tile", "i_per_thread", "threads", "min_blocks",
+                                                "nr_slots")},
             "l2": f"no flush: per-step working set {working_set / 1e6:.0f} MB > L2 129 MB"
             if working_set > L2_BYTES else f"working set {working_set / 1e6:.0f} MB",
             "parallelism": f"replicas x{ws}"})
@@ -345,6 +352,8 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--pair-cfg", default="",
+                    help="tile,i_per_thread,threads,min_blocks,nr_slots (skips the autotuner)")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

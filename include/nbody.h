@@ -154,6 +154,18 @@ typedef struct nb_prof {
     double pairs;              /* pair interactions evaluated by the pair kernel */
 } nb_prof;
 
+/* Launch shape of the FP32 pair kernel. */
+typedef struct nb_pair_cfg {
+    int32_t tile;          /* j-elements per shared-memory tile (64, 128, 256) */
+    int32_t i_per_thread;  /* i-elements held in registers per thread */
+    int32_t threads;       /* threads per block */
+    int32_t min_blocks;    /* resident blocks per SM the registers are sized for */
+    int32_t nr_slots;      /* i-elements per thread whose reciprocal is computed
+                              by Newton-Raphson on the FP32 pipe instead of MUFU */
+    int32_t reserved;
+    double ms;             /* measured time of one pair pass (autotune), else 0 */
+} nb_pair_cfg;
+
 typedef struct nb_system* nb_system_t;
 
 /* ---- library ---------------------------------------------------------- */
@@ -218,6 +230,14 @@ nb_status nb_get_state(nb_system_t sys, double* xv_out, double* a_out, nb_ckpt_m
  * one bit for bit when a_in is given. */
 nb_status nb_set_state(nb_system_t sys, const double* xv_in, const double* a_in,
                        const nb_ckpt_meta* meta);
+
+/* Time every built pair-kernel variant on this system's current state
+ * (reps launches each, CUDA events) and keep the fastest; best (may be
+ * NULL) receives it.  Results are cached per element count and precision
+ * for the life of the process.  The state is not changed. */
+nb_status nb_autotune(nb_system_t sys, int reps, nb_pair_cfg* best);
+nb_status nb_set_pair_cfg(nb_system_t sys, const nb_pair_cfg* cfg);
+nb_status nb_get_pair_cfg(nb_system_t sys, nb_pair_cfg* cfg);
 
 /* Enable (1) or disable (0) per-phase event timing of subsequent calls;
  * while enabled, multi-step calls are not captured in CUDA graphs. */

@@ -3,7 +3,10 @@
 // status; nothing throws across the ABI.
 #include <cstring>
 #include <exception>
+#include <map>
+#include <mutex>
 #include <new>
+#include <utility>
 
 #include "nb_batch.h"
 
@@ -28,6 +31,21 @@ nb_status guarded(F&& f) {
     } catch (...) {
         return set_error(NB_EINVAL, "internal error");
     }
+}
+
+// Process-wide tuning cache: (element count, precision) -> best variant.
+std::mutex g_tune_mu;
+std::map<std::pair<int64_t, int>, std::pair<nb::PairCfg, double>> g_tune_cache;
+
+nb_pair_cfg to_abi(const nb::PairCfg& c, double ms) {
+    nb_pair_cfg o{};
+    o.tile = c.tile;
+    o.i_per_thread = c.bi;
+    o.threads = c.threads;
+    o.min_blocks = c.minb;
+    o.nr_slots = c.nr;
+    o.ms = ms;
+    return o;
 }
 
 }  // namespace
@@ -94,6 +112,8 @@ nb_status nb_create_system(const nb_desc* desc, const nb_params* params, void* s
         nb_status st = nb::build_system(*desc, *params, si);
         if (st != NB_OK) return st;
         nb_system* sys = new nb_system();
+        // multi-step calls replay a captured CUDA graph (needs a non-default stream)
+        sys->batch.set_use_graph(true);
         st = sys->batch.init({si.n}, params->force_prec, static_cast<cudaStream_t>(stream));
         if (st == NB_OK) st = sys->batch.load(0, si);
         if (st == NB_OK) st = sys->batch.sync();
@@ -150,6 +170,47 @@ nb_status nb_set_state(nb_system_t sys, const double* xv_in, const double* a_in,
                        const nb_ckpt_meta* meta) {
     if (!sys) return set_error(NB_EINVAL, "null system");
     return guarded([&] { return sys->batch.set_state(0, xv_in, a_in, meta); });
+}
+
+nb_status nb_autotune(nb_system_t sys, int reps, nb_pair_cfg* best) {
+    if (!sys) return set_error(NB_EINVAL, "null system");
+    return guarded([&]() -> nb_status {
+        const auto key = std::make_pair(sys->info.n, sys->batch.prec());
+        {
+            std::lock_guard<std::mutex> g(g_tune_mu);
+            auto it = g_tune_cache.find(key);
+            if (it != g_tune_cache.end()) {
+                nb_status st = sys->batch.set_pair_cfg(it->second.first);
+                if (st == NB_OK && best) *best = to_abi(it->second.first, it->second.second);
+                return st;
+            }
+        }
+        nb::PairCfg c{};
+        double ms = 0;
+        nb_status st = sys->batch.autotune(reps, &c, &ms);
+        if (st != NB_OK) return st;
+        {
+            std::lock_guard<std::mutex> g(g_tune_mu);
+            g_tune_cache[key] = {c, ms};
+        }
+        if (best) *best = to_abi(c, ms);
+        return NB_OK;
+    });
+}
+
+nb_status nb_set_pair_cfg(nb_system_t sys, const nb_pair_cfg* cfg) {
+    if (!sys || !cfg) return set_error(NB_EINVAL, "null argument");
+    return guarded([&] {
+        nb::PairCfg c{cfg->tile, cfg->i_per_thread, cfg->threads, 0, cfg->min_blocks,
+                      cfg->nr_slots};
+        return sys->batch.set_pair_cfg(c);
+    });
+}
+
+nb_status nb_get_pair_cfg(nb_system_t sys, nb_pair_cfg* cfg) {
+    if (!sys || !cfg) return set_error(NB_EINVAL, "null argument");
+    *cfg = to_abi(sys->batch.pair_cfg(), 0.0);
+    return NB_OK;
 }
 
 nb_status nb_profile(nb_system_t sys, int enable) {

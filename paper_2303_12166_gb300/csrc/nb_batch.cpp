@@ -335,7 +335,13 @@ nb_status Batch::init(const std::vector<int64_t>& n_per_slot, int prec, cudaStre
     NB_TRY(alloc_((void**)&d_.V, nt * sizeof(double4_32a)));
     NB_TRY(alloc_((void**)&d_.A, nt * sizeof(double4_32a)));
     NB_TRY(alloc_((void**)&d_.E, nt * sizeof(double2)));
-    NB_TRY(alloc_((void**)&d_.pos4, (nt + NB_PAD) * sizeof(float4)));
+    {
+        // one allocation, four component arrays of ntot + NB_PAD floats each
+        const size_t stride = nt + NB_PAD;
+        float* base = nullptr;
+        NB_TRY(alloc_((void**)&base, 4 * stride * sizeof(float)));
+        d_.pj = PosSoA{base, base + stride, base + 2 * stride, base + 3 * stride};
+    }
     NB_TRY(alloc_((void**)&d_.sys_of, nt * sizeof(int32_t)));
     NB_TRY(alloc_((void**)&d_.cont, nt * sizeof(double4_32a)));
     d_.nchunk_alloc = 0;
@@ -351,6 +357,8 @@ nb_status Batch::init(const std::vector<int64_t>& n_per_slot, int prec, cudaStre
     NB_TRY(alloc_((void**)&d_.start, d_.nbucket * sizeof(uint32_t)));
     NB_TRY(alloc_((void**)&d_.blocksum, (d_.nbucket / 4096 + 2) * sizeof(uint32_t)));
     NB_TRY(alloc_((void**)&d_.sorted, nt * sizeof(uint32_t)));
+    NB_TRY(alloc_((void**)&d_.scell, nt * sizeof(uint64_t)));
+    NB_TRY(alloc_((void**)&d_.spos, nt * sizeof(float4)));
     NB_TRY(alloc_((void**)&d_.red, diag_scratch_doubles() * sizeof(double)));
     NB_TRY(alloc_((void**)&d_.diag_out, NB_DIAG_OUT * sizeof(double)));
     SysConst* scd = nullptr;
@@ -432,7 +440,10 @@ nb_status Batch::load(int s, const SystemInit& si, bool defer_forces) {
                           stream_));
     NB_CU(cudaMemcpyAsync(d_.sys_of + c.off, owner.data(), npad * sizeof(int32_t),
                           cudaMemcpyHostToDevice, stream_));
-    NB_CU(cudaMemsetAsync(d_.pos4 + c.off, 0, npad * sizeof(float4), stream_));
+    NB_CU(cudaMemsetAsync(d_.pj.x + c.off, 0, npad * sizeof(float), stream_));
+    NB_CU(cudaMemsetAsync(d_.pj.y + c.off, 0, npad * sizeof(float), stream_));
+    NB_CU(cudaMemsetAsync(d_.pj.z + c.off, 0, npad * sizeof(float), stream_));
+    NB_CU(cudaMemsetAsync(d_.pj.m + c.off, 0, npad * sizeof(float), stream_));
     SysMut m0{};
     NB_CU(cudaMemcpyAsync(d_.sm + s, &m0, sizeof m0, cudaMemcpyHostToDevice, stream_));
     consts_dirty_ = true;
@@ -455,8 +466,9 @@ nb_status Batch::unload(int s) {
 
 nb_status Batch::set_pair_cfg(const PairCfg& c) {
     if (!pair_cfg_supported(c))
-        return set_error(NB_EINVAL, "pair configuration tile=%d bi=%d threads=%d not built",
-                         c.tile, c.bi, c.threads);
+        return set_error(NB_EINVAL,
+                         "pair configuration tile=%d bi=%d threads=%d minb=%d nr=%d not built",
+                         c.tile, c.bi, c.threads, c.minb, c.nr);
     cfg_ = c;
     planned_ = false;
     return NB_OK;
@@ -537,6 +549,36 @@ nb_status Batch::plan_pairs_() {
             }
         }
     }
+    if (f32) {
+        // per j-tile common mass: tiles whose elements all carry the same
+        // G m (as the FP32 copy holds it) skip the per-pair mass product
+        const int64_t ntiles_all = d_.ntot / tile;
+        std::vector<float> tm(ntiles_all, -1.f);
+        for (int s : act) {
+            const SysConst& c = sc_[s];
+            const std::vector<double>& m = mass_[s];
+            for (int64_t t0 = 0; t0 < c.n; t0 += tile) {
+                if (t0 + tile > c.n) break;  // padded last tile
+                const float g0 = (float)(c.G * m[t0]);
+                bool same = g0 > 0.f;
+                for (int64_t j = t0 + 1; same && j < t0 + tile; ++j)
+                    same = (float)(c.G * m[j]) == g0;
+                if (same) tm[(c.off + t0) / tile] = g0;
+            }
+        }
+        if (ntiles_all > tmass_cap_) {
+            if (tmass_d_) {
+                NB_CU(cudaStreamSynchronize(stream_));
+                auto itp = std::find(allocs_.begin(), allocs_.end(), (void*)tmass_d_);
+                if (itp != allocs_.end()) allocs_.erase(itp);
+                NB_CU(cudaFreeAsync(tmass_d_, stream_));
+            }
+            NB_TRY(alloc_((void**)&tmass_d_, (size_t)ntiles_all * sizeof(float)));
+            tmass_cap_ = ntiles_all;
+        }
+        NB_CU(cudaMemcpyAsync(tmass_d_, tm.data(), tm.size() * sizeof(float),
+                              cudaMemcpyHostToDevice, stream_));
+    }
     if (dynamic_) {
         // longest first (LPT); the persistent CTAs claim items in this order
         std::stable_sort(items_.begin(), items_.end(), [](const PairItem& a, const PairItem& b) {
@@ -581,8 +623,9 @@ nb_status Batch::plan_pairs_() {
     return NB_OK;
 }
 
-nb_status Batch::launch_pairs_(bool pot) {
-    const int n = (int)items_.size();
+nb_status Batch::launch_pairs_(bool pot, int nitems_limit) {
+    int n = (int)items_.size();
+    if (nitems_limit >= 0 && nitems_limit < n) n = nitems_limit;
     if (n == 0) return NB_OK;
     int* ctr = nullptr;
     if (dynamic_) {
@@ -591,7 +634,7 @@ nb_status Batch::launch_pairs_(bool pot) {
     }
     cudaEvent_t ev = prof_begin_();
     if (prec_ == 32) {
-        NB_CU(launch_pair_f32(d_, items_d_, n, cfg_, pot, ctr, stream_));
+        NB_CU(launch_pair_f32(d_, tmass_d_, items_d_, n, cfg_, pot, ctr, stream_));
     } else {
         NB_CU(launch_pair_f64(d_, items_d_, n, cfg_.grid, pot, ctr, stream_));
     }
@@ -616,7 +659,7 @@ nb_status Batch::contact_pass_(int kofs, bool energy, bool with_keys) {
         NB_CU(launch_cell_keys(d_, kofs, stream_));
         kernels_ += 1;
     }
-    NB_CU(launch_contact(d_, kofs, energy, stream_));
+    NB_CU(launch_contact(d_, kofs, energy, prec_ == 64, stream_));
     kernels_ += kContactKernels;
     return prof_end_(ev, PH_CONTACT);
 }
@@ -661,6 +704,66 @@ nb_status Batch::prof_collect_() {
         event_pool_.push_back(m.b);
     }
     prof_marks_.clear();
+    return NB_OK;
+}
+
+nb_status Batch::autotune(int reps, PairCfg* best, double* best_ms) {
+    if (prec_ != 32) {
+        if (best) *best = cfg_;
+        if (best_ms) *best_ms = 0;
+        return NB_OK;
+    }
+    if (reps < 1) reps = 1;
+    NB_TRY(push_consts_());
+    cudaEvent_t e0, e1;
+    NB_CU(cudaEventCreate(&e0));
+    NB_CU(cudaEventCreate(&e1));
+    PairCfg keep = cfg_;
+    double best_t = 1e300;
+    PairCfg best_c = cfg_;
+    nb_status st = NB_OK;
+    for (const PairCfg& c0 : pair_cfgs()) {
+        PairCfg c = c0;
+        if (pair_occupancy(c) < 1) continue;
+        cfg_ = c;
+        planned_ = false;
+        if ((st = plan_pairs_()) != NB_OK) break;
+        // time about two waves of the persistent grid (items are equal-sized
+        // within a system), normalised per pair interaction
+        const int nlim = std::min<int>((int)items_.size(), 2 * std::max(cfg_.grid, 1));
+        double pairs = 0;
+        for (int q = 0; q < nlim; ++q) pairs += (double)items_[q].iend_rel * items_[q].nj;
+        if ((st = launch_pairs_(false, nlim)) != NB_OK) break;  // warm-up
+        cudaEventRecord(e0, stream_);
+        for (int r = 0; r < reps && st == NB_OK; ++r) st = launch_pairs_(false, nlim);
+        cudaEventRecord(e1, stream_);
+        if (st != NB_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            st = set_error(NB_ECUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double t = ms / reps / pairs;  // ms per pair
+        if (t < best_t) {
+            best_t = t;
+            best_c = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // the timed launches are not part of any step
+    kernels_ = 0;
+    pairs_done_ = 0;
+    cfg_ = st == NB_OK ? best_c : keep;
+    planned_ = false;
+    if (st != NB_OK) return st;
+    NB_TRY(plan_pairs_());
+    if (best) *best = cfg_;
+    // report the time of one full pair pass at the measured rate
+    double pairs_all = 0;
+    for (const PairItem& it : items_) pairs_all += (double)it.iend_rel * it.nj;
+    if (best_ms) *best_ms = best_t * pairs_all;
     return NB_OK;
 }
 

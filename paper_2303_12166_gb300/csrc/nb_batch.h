@@ -84,6 +84,8 @@ public:
     double pairs_per_step() const;
     // capture subsequent multi-step calls in a CUDA graph (per step count)
     void set_use_graph(bool g) { use_graph_ = g; }
+    // time every pair-kernel variant (reps launches each) and keep the best
+    nb_status autotune(int reps, PairCfg* best, double* best_ms);
     // per-phase event timing
     nb_status set_profile(bool on);
     nb_status read_profile(nb_prof* out, bool reset);
@@ -92,7 +94,7 @@ private:
     nb_status alloc_(void** p, size_t bytes);
     nb_status push_consts_();
     nb_status plan_pairs_();
-    nb_status launch_pairs_(bool pot);
+    nb_status launch_pairs_(bool pot, int nitems_limit = -1);
     nb_status step_body_(int64_t n);
     void release_();
 
@@ -105,7 +107,9 @@ private:
     std::vector<int64_t> k_;
     std::vector<std::vector<double>> mass_;  // host copy of element masses
     std::vector<double> rmax_d0_, rmax_a_;
-    PairCfg cfg_{128, 4, 256, 0};
+    PairCfg cfg_{128, 4, 256, 0, 2, 1};
+    float* tmass_d_ = nullptr;   // per j-tile common G m (see launch_pair_f32)
+    int64_t tmass_cap_ = 0;
     std::vector<PairItem> items_;
     PairItem* items_d_ = nullptr;
     int items_cap_ = 0;

@@ -19,11 +19,18 @@
 //   4. one thread per binned element, in bucket order (spatial neighbours
 //      share warps and cache lines): visit the 27 surrounding cells in a
 //      fixed order; a candidate must carry the visited cell's id (hash
-//      collisions are skipped), pass an FP32 distance pre-test on the FP32
-//      copy with a margin that covers its rounding, and then the exact FP64
-//      test r < R_i + R_j.
-// The force itself is FP64 from the FP64 state, so the stiff overlap term
-// carries no FP32 rounding of the positions.
+//      collisions are skipped) and pass an FP32 distance pre-test on the
+//      FP32 copy with a margin that covers its rounding.
+// Precision.  Every decision is taken in FP64 from the FP64 state, as in
+// the direct FP64 sum: the difference d = x_j - x_i, d^2, the contact test
+// (R_i + R_j)^2 - d^2 > 0 and the closing test d.(v_j - v_i) < 0.  The force
+// magnitude is then evaluated in FP32 from those FP64 quantities: the
+// overlap depth is (Rs^2 - d^2)/(Rs + r) with Rs^2 - d^2 formed by one FP64
+// fused multiply-add, so the volume pi (4R + r) depth^2 / 12 suffers no
+// cancellation and the FP32 relative error of the force stays ~1e-7.  FP64
+// throughput on this GPU is a small fraction of FP32, so this keeps the
+// FP64 work to ~16 operations per contact.  The energy variant (used by the
+// diagnostics) evaluates the whole term in FP64.
 #include "nb_device.cuh"
 
 namespace nb {
@@ -126,30 +133,51 @@ __global__ void scan_add_kernel(uint32_t* __restrict__ start, const uint32_t* __
     if (idx < n) start[idx] += blocksum[idx / kScanBlock];
 }
 
-__global__ void scatter_kernel(BatchDev b) {
+// current radius of element i (donor radii grow with the step index)
+__device__ __forceinline__ double radius_of(const BatchDev& b, const SysConst& c, int64_t i,
+                                            double scale) {
+    return b.E[i].x * (i < c.off + c.n_donor ? scale : 1.0);
+}
+
+__global__ void scatter_kernel(BatchDev b, int kofs) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= b.ntot) return;
     const uint32_t key = b.key[i];
     if (key == 0xffffffffu) return;
+    const int s = b.sys_of[i];
+    const SysConst& c = b.sc[s];
+    const double R = radius_of(b, c, i, donor_scale(c, b.sm[s].k + kofs));
     const uint32_t slot = b.start[key] + atomicAdd(&b.fill[key], 1u);
     b.sorted[slot] = (uint32_t)i;
+    b.scell[slot] = b.cellid[i];
+    b.spos[slot] = make_float4(b.pj.x[i], b.pj.y[i], b.pj.z[i], (float)R);
 }
 
-// Insertion sort of every bucket by element index (buckets hold a few elements).
+// Insertion sort of every bucket by element index (buckets hold a few
+// elements); the cell ids and FP32 positions move along.
 __global__ void bucket_sort_kernel(BatchDev b) {
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= b.nbucket) return;
     const uint32_t c = b.cnt[k];
     if (c < 2) return;
-    uint32_t* s = b.sorted + b.start[k];
+    const uint32_t base = b.start[k];
+    uint32_t* s = b.sorted + base;
+    uint64_t* sc = b.scell + base;
+    float4* sp = b.spos + base;
     for (uint32_t u = 1; u < c; ++u) {
         const uint32_t v = s[u];
+        const uint64_t vc = sc[u];
+        const float4 vp = sp[u];
         uint32_t w = u;
         while (w > 0 && s[w - 1] > v) {
             s[w] = s[w - 1];
+            sc[w] = sc[w - 1];
+            sp[w] = sp[w - 1];
             --w;
         }
         s[w] = v;
+        sc[w] = vc;
+        sp[w] = vp;
     }
 }
 
@@ -157,7 +185,9 @@ __device__ __forceinline__ float max_abs3(float4 p) {
     return fmaxf(fabsf(p.x), fmaxf(fabsf(p.y), fabsf(p.z)));
 }
 
-template <bool ENERGY>
+// FULL64: the whole term in FP64 (the FP64 force path and the diagnostics);
+// ENERGY: also the repulsion energy (implies FULL64).
+template <bool FULL64, bool ENERGY>
 __global__ void __launch_bounds__(128) contact_kernel(BatchDev b, int kofs, uint32_t total_idx) {
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= b.blocksum[total_idx]) return;
@@ -165,25 +195,26 @@ __global__ void __launch_bounds__(128) contact_kernel(BatchDev b, int kofs, uint
     const int s = b.sys_of[i];
     const SysConst& c = b.sc[s];
     const int64_t k = b.sm[s].k + kofs;
-    const double h = cell_edge(c, k);
     const double scale = donor_scale(c, k);
     const int64_t dend = c.off + c.n_donor;
     const double4_32a xi = b.X[i];
     const double4_32a vi = b.V[i];
     const double2 ei = b.E[i];
     const double Ri = ei.x * ((int64_t)i < dend ? scale : 1.0);
-    const float4 pi4 = b.pos4[i];
-    // FP32 pre-test: |d| < R_i + R_max (R_max = h/2) plus a margin covering
-    // the rounding of both FP32 coordinates (2^-24 relative each, per axis)
-    const float cut = (float)(Ri + 0.5 * h) * 1.0001f;
+    const float4 pi4 = b.spos[t];
+    // FP32 pre-test |d| < R_i + R_j with a margin covering the rounding of
+    // both FP32 coordinates (2^-24 relative each, per axis) and of R_j
+    const float Rif = (float)Ri;
     const float mi = max_abs3(pi4);
+    const float inv_m = (float)(1.0 / xi.w);
     long long cx, cy, cz;
-    unpack_cell(b.cellid[i], cx, cy, cz);
+    unpack_cell(b.scell[t], cx, cy, cz);
     const uint32_t mask = b.nbucket - 1;
-    const double beta = c.beta;
-    const double pi = 3.14159265358979323846;
+    const float beta = (float)c.beta;
+    const float pif = 3.14159265358979f;
 
-    double ax = 0.0, ay = 0.0, az = 0.0, er = 0.0;
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    double eax = 0.0, eay = 0.0, eaz = 0.0, er = 0.0;
     for (int oz = -1; oz <= 1; ++oz)
         for (int oy = -1; oy <= 1; ++oy)
             for (int ox = -1; ox <= 1; ++ox) {
@@ -196,42 +227,68 @@ __global__ void __launch_bounds__(128) contact_kernel(BatchDev b, int kofs, uint
                 const uint32_t beg = b.start[key];
                 const uint32_t end = beg + b.cnt[key];
                 for (uint32_t slot = beg; slot < end; ++slot) {
-                    const uint32_t j = b.sorted[slot];
-                    if (j == i || b.cellid[j] != cell) continue;
-                    const float4 pj = b.pos4[j];
+                    if (b.scell[slot] != cell) continue;  // hash collision
+                    const float4 pj = b.spos[slot];
                     const float dxf = pj.x - pi4.x, dyf = pj.y - pi4.y, dzf = pj.z - pi4.z;
-                    const float tol = cut + 2.5e-7f * (mi + max_abs3(pj));
+                    const float tol =
+                        (Rif + pj.w) * 1.0001f + 2.5e-7f * (mi + max_abs3(pj));
                     if (dxf * dxf + dyf * dyf + dzf * dzf > tol * tol) continue;
-                    if (b.sys_of[j] != s) continue;
+                    const uint32_t j = b.sorted[slot];
+                    if (j == i || b.sys_of[j] != s) continue;
+                    // FP64 decisions
                     const double4_32a xj = b.X[j];
                     const double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
-                    const double d2 = dx * dx + dy * dy + dz * dz;
-                    const double2 ej = b.E[j];
-                    const double Rj = ej.x * ((int64_t)j < dend ? scale : 1.0);
-                    const double Rs = Ri + Rj;
-                    if (!(d2 > 0.0) || d2 >= Rs * Rs * (1.0 + 1e-12)) continue;
-                    const double r = sqrt(d2);
-                    if (!(r < Rs)) continue;
-                    const double R = 0.5 * Rs;
-                    const double g = 0.5 * (ei.y + ej.y);
-                    const double vol = pi * (4.0 / 3.0 * R * R * R - R * R * r + r * r * r / 12.0);
+                    const double d2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                    const double Rs = Ri + b.E[j].x * ((int64_t)j < dend ? scale : 1.0);
+                    const double gap2 = fma(Rs, Rs, -d2);  // Rs^2 - d^2
+                    if (!(d2 > 0.0) || !(gap2 > -1e-12 * d2)) continue;
+                    if (!(gap2 > 1e-12 * d2)) {
+                        // within rounding of the contact distance: decide as
+                        // sqrt(d^2) < Rs, exactly as the direct sum does
+                        if (!(sqrt(d2) < Rs)) continue;
+                    }
                     const double4_32a vj = b.V[j];
                     const double closing =
-                        dx * (vj.x - vi.x) + dy * (vj.y - vi.y) + dz * (vj.z - vi.z);
-                    const double cf = closing < 0.0 ? 1.0 : beta;
-                    // repulsion: acceleration of i along -d/r
-                    const double f = -cf * g * vol / (xi.w * r);
-                    ax += f * dx;
-                    ay += f * dy;
-                    az += f * dz;
-                    if (ENERGY) {
-                        const double U = pi * (R * R * R * R - 4.0 / 3.0 * R * R * R * r +
-                                               0.5 * R * R * r * r - r * r * r * r / 48.0);
-                        er += 0.5 * g * U;
+                        fma(dx, vj.x - vi.x, fma(dy, vj.y - vi.y, dz * (vj.z - vi.z)));
+                    const double2 ej = b.E[j];
+                    if (FULL64) {
+                        // full FP64 evaluation
+                        const double r = sqrt(d2);
+                        const double R = 0.5 * Rs;
+                        const double g = 0.5 * (ei.y + ej.y);
+                        const double pi = 3.14159265358979323846;
+                        const double vol =
+                            pi * (4.0 / 3.0 * R * R * R - R * R * r + r * r * r / 12.0);
+                        const double cf = closing < 0.0 ? 1.0 : c.beta;
+                        const double f = -cf * g * vol / (xi.w * r);
+                        eax += f * dx;
+                        eay += f * dy;
+                        eaz += f * dz;
+                        if (ENERGY) {
+                            const double U = pi * (R * R * R * R - 4.0 / 3.0 * R * R * R * r +
+                                                   0.5 * R * R * r * r - r * r * r * r / 48.0);
+                            er += 0.5 * g * U;
+                        }
+                    } else {
+                        // FP32 magnitude from the FP64 geometry
+                        const float d2f = (float)d2;
+                        const float r = sqrtf(d2f);
+                        const float Rsf = (float)Rs;
+                        const float depth = fmaxf((float)gap2, 0.f) / (Rsf + r);
+                        const float vol = pif / 12.f * (2.f * Rsf + r) * depth * depth;
+                        const float g = 0.5f * (float)(ei.y + ej.y);
+                        const float cf = closing < 0.0 ? 1.f : beta;
+                        const float f = -cf * g * vol * inv_m / r;
+                        ax = fmaf(f, (float)dx, ax);
+                        ay = fmaf(f, (float)dy, ay);
+                        az = fmaf(f, (float)dz, az);
                     }
                 }
             }
-    b.cont[i] = make_double4_32a(ax, ay, az, er);
+    if (FULL64)
+        b.cont[i] = make_double4_32a(eax, eay, eaz, er);
+    else
+        b.cont[i] = make_double4_32a(ax, ay, az, 0.0);
 }
 
 }  // namespace
@@ -243,7 +300,8 @@ cudaError_t launch_cell_keys(const BatchDev& b, int kofs, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_contact(const BatchDev& b, int kofs, bool with_energy, cudaStream_t s) {
+cudaError_t launch_contact(const BatchDev& b, int kofs, bool with_energy, bool full64,
+                           cudaStream_t s) {
     if (b.ntot == 0) return cudaSuccess;
     const uint32_t nblk = (b.nbucket + kScanBlock - 1) / kScanBlock;
     scan_blocks_kernel<<<nblk, kScanThreads, 0, s>>>(b.cnt, b.start, b.blocksum, b.nbucket);
@@ -252,13 +310,15 @@ cudaError_t launch_contact(const BatchDev& b, int kofs, bool with_energy, cudaSt
     cudaError_t e = cudaMemsetAsync(b.fill, 0, sizeof(uint32_t) * b.nbucket, s);
     if (e != cudaSuccess) return e;
     const unsigned ng = (unsigned)((b.ntot + 255) / 256);
-    scatter_kernel<<<ng, 256, 0, s>>>(b);
+    scatter_kernel<<<ng, 256, 0, s>>>(b, kofs);
     bucket_sort_kernel<<<(b.nbucket + 255) / 256, 256, 0, s>>>(b);
     const unsigned ngc = (unsigned)((b.ntot + 127) / 128);
     if (with_energy)
-        contact_kernel<true><<<ngc, 128, 0, s>>>(b, kofs, nblk);
+        contact_kernel<true, true><<<ngc, 128, 0, s>>>(b, kofs, nblk);
+    else if (full64)
+        contact_kernel<true, false><<<ngc, 128, 0, s>>>(b, kofs, nblk);
     else
-        contact_kernel<false><<<ngc, 128, 0, s>>>(b, kofs, nblk);
+        contact_kernel<false, false><<<ngc, 128, 0, s>>>(b, kofs, nblk);
     return cudaGetLastError();
 }
 

@@ -9,14 +9,16 @@
 //   V    double4_32a  (vx, vy, vz, 0)       FP64 velocity
 //   A    double4_32a  (ax, ay, az, 0)       FP64 acceleration a^k of the state
 //   E    double2  (R0, gamma)           initial radius and repulsion strength
-//   pos4 float4   (x-o, y-o, z-o, G m)  FP32 copy relative to the system's
-//                                       reference point o (the j-stream of
-//                                       the pair kernel)
+//   pj   4 x float (x-o, y-o, z-o, G m)  FP32 copy relative to the system's
+//                                       reference point o, one array per
+//                                       component (the j-stream of the pair
+//                                       kernel)
 //   sys_of int32                        owning system (-1 for padding)
 // Pair sums land in `part` (double4_32a per element and j-chunk); the contact
 // term in `cont` (double4_32a: a, e_rep).
 #pragma once
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 namespace nb {
@@ -31,7 +33,7 @@ struct SysConst {
     int64_t npad;       // padded range length (multiple of NB_PAD)
     int64_t n_donor;    // donor elements are [off, off + n_donor)
     double dt, G, eps, beta;
-    double origin[3];   // reference point of pos4
+    double origin[3];   // reference point of the FP32 copy pj
     double grow_f0, grow_rate;
     int64_t grow_cap;   // < 0: no cap
     double rmax_donor0; // largest initial donor radius
@@ -63,6 +65,14 @@ struct PairItem {
     int32_t iend_rel;   // i-block end relative to i0 (clip), <= I
 };
 
+// FP32 copy of the positions and G m, one array per component.
+struct PosSoA {
+    float* x;
+    float* y;
+    float* z;
+    float* m;
+};
+
 // Device arrays of a batch (all pointers are device memory).
 struct BatchDev {
     int64_t ntot;          // total padded elements
@@ -71,7 +81,7 @@ struct BatchDev {
     double4_32a* V;
     double4_32a* A;
     double2* E;
-    float4* pos4;          // ntot + NB_PAD slack
+    PosSoA pj;             // each ntot + NB_PAD (slack)
     int32_t* sys_of;
     double4_32a* part;         // NB chunks * ntot
     int32_t nchunk_alloc;  // chunks allocated in part
@@ -86,7 +96,9 @@ struct BatchDev {
     uint32_t* fill;        // nbucket
     uint32_t* start;       // nbucket
     uint32_t* blocksum;    // nbucket / 4096 + 2; [nblocks] = number of binned elements
-    uint32_t* sorted;      // ntot
+    uint32_t* sorted;      // ntot: element indices, bucket by bucket
+    uint64_t* scell;       // ntot: cell id of sorted[slot]
+    float4* spos;          // ntot: FP32 position and current radius of sorted[slot]
     // diagnostics scratch
     double* red;           // per-block partial sums
     double* diag_out;      // final diagnostic values
@@ -99,12 +111,18 @@ struct PairCfg {
     int bi;        // i-elements per thread (1, 2, 4, 8)
     int threads;   // threads per block (128 or 256)
     int grid;      // persistent grid size
+    int minb;      // resident blocks per SM the register budget is sized for
+    int nr;        // i-slots per thread whose reciprocal runs on the FP32 pipe
 };
+// tmass: per global j-tile (index j / tile) the common G m of its elements,
+// or <= 0 if they differ (nullptr: always per pair).
 // counter: nullptr -> items are dealt round-robin over the grid; otherwise a
 // zeroed device int that CTAs increment to claim items (dynamic order).
-cudaError_t launch_pair_f32(const BatchDev& b, const PairItem* items, int nitems,
-                            const PairCfg& cfg, bool with_pot, int* counter, cudaStream_t s);
+cudaError_t launch_pair_f32(const BatchDev& b, const float* tmass, const PairItem* items,
+                            int nitems, const PairCfg& cfg, bool with_pot, int* counter,
+                            cudaStream_t s);
 bool pair_cfg_supported(const PairCfg& cfg);
+std::vector<PairCfg> pair_cfgs();         // every built variant
 int pair_occupancy(const PairCfg& cfg);  // resident CTAs per SM
 // FP64 comparison path: i-blocks of kF64Block elements, j-tiles of 128.
 constexpr int kF64Block = 128;
@@ -130,7 +148,9 @@ cudaError_t launch_store_acc(const BatchDev& b, int only, cudaStream_t s);
 // runs the scan, the scatter, the bucket sort and the repulsion with the
 // radii of step k + kofs.
 cudaError_t launch_cell_keys(const BatchDev& b, int kofs, cudaStream_t s);
-cudaError_t launch_contact(const BatchDev& b, int kofs, bool with_energy, cudaStream_t s);
+// full64: evaluate the force magnitude in FP64 too (the FP64 force path)
+cudaError_t launch_contact(const BatchDev& b, int kofs, bool with_energy, bool full64,
+                           cudaStream_t s);
 uint64_t contact_max_buckets();
 
 // Diagnostics of one system (needs part.w and cont.w from a force pass with

@@ -45,8 +45,10 @@ __device__ __forceinline__ double3 total_acc(const BatchDev& b, const SysConst& 
 
 __device__ __forceinline__ void write_shadow(const BatchDev& b, const SysConst& c, int64_t i,
                                              const double4_32a& x) {
-    b.pos4[i] = make_float4((float)(x.x - c.origin[0]), (float)(x.y - c.origin[1]),
-                            (float)(x.z - c.origin[2]), (float)(c.G * x.w));
+    b.pj.x[i] = (float)(x.x - c.origin[0]);
+    b.pj.y[i] = (float)(x.y - c.origin[1]);
+    b.pj.z[i] = (float)(x.z - c.origin[2]);
+    b.pj.m[i] = (float)(c.G * x.w);
 }
 
 template <int MODE, bool KEYS>

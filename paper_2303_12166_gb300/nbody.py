@@ -67,6 +67,11 @@ class nb_prof(ctypes.Structure):
                 ("kernels", _I64), ("pairs", _D)]
 
 
+class nb_pair_cfg(ctypes.Structure):
+    _fields_ = [("tile", _I32), ("i_per_thread", _I32), ("threads", _I32),
+                ("min_blocks", _I32), ("nr_slots", _I32), ("reserved", _I32), ("ms", _D)]
+
+
 class nb_info(ctypes.Structure):
     _fields_ = [("n", _I64), ("n_donor", _I64), ("n_accretor", _I64), ("m_donor", _D),
                 ("m_accretor", _D), ("r_donor0", _D), ("r_accretor", _D),
@@ -99,6 +104,9 @@ _sig("nb_diagnostics", ctypes.c_int, [_P, ctypes.POINTER(nb_diag)])
 _sig("nb_get_state", ctypes.c_int, [_P, _P, _P, ctypes.POINTER(nb_ckpt_meta)])
 _sig("nb_set_state", ctypes.c_int, [_P, _P, _P, ctypes.POINTER(nb_ckpt_meta)])
 _sig("nb_profile", ctypes.c_int, [_P, ctypes.c_int])
+_sig("nb_autotune", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(nb_pair_cfg)])
+_sig("nb_set_pair_cfg", ctypes.c_int, [_P, ctypes.POINTER(nb_pair_cfg)])
+_sig("nb_get_pair_cfg", ctypes.c_int, [_P, ctypes.POINTER(nb_pair_cfg)])
 _sig("nb_profile_read", ctypes.c_int, [_P, ctypes.POINTER(nb_prof), ctypes.c_int])
 
 
@@ -255,6 +263,28 @@ def nb_set_state(h, xv, a, meta: nb_ckpt_meta) -> None:
                              ctypes.byref(meta)), "nb_set_state")
 
 
+def _cfg_dict(c: nb_pair_cfg) -> dict:
+    return {name: getattr(c, name) for name, _ in nb_pair_cfg._fields_}
+
+
+def nb_autotune(h, reps: int = 3) -> dict:
+    c = nb_pair_cfg()
+    _check(_lib.nb_autotune(_P(h), int(reps), ctypes.byref(c)), "nb_autotune")
+    return _cfg_dict(c)
+
+
+def nb_set_pair_cfg(h, tile: int, i_per_thread: int, threads: int, min_blocks: int,
+                    nr_slots: int = 0) -> None:
+    c = nb_pair_cfg(tile, i_per_thread, threads, min_blocks, nr_slots, 0, 0.0)
+    _check(_lib.nb_set_pair_cfg(_P(h), ctypes.byref(c)), "nb_set_pair_cfg")
+
+
+def nb_get_pair_cfg(h) -> dict:
+    c = nb_pair_cfg()
+    _check(_lib.nb_get_pair_cfg(_P(h), ctypes.byref(c)), "nb_get_pair_cfg")
+    return _cfg_dict(c)
+
+
 def nb_profile(h, enable: bool) -> None:
     _check(_lib.nb_profile(_P(h), 1 if enable else 0), "nb_profile")
 
@@ -296,6 +326,15 @@ class System:
 
     def set_state(self, xv, a, meta):
         nb_set_state(self.h, xv, a, meta)
+
+    def autotune(self, reps: int = 3) -> dict:
+        return nb_autotune(self.h, reps)
+
+    def set_pair_cfg(self, tile, i_per_thread, threads, min_blocks, nr_slots=0):
+        nb_set_pair_cfg(self.h, tile, i_per_thread, threads, min_blocks, nr_slots)
+
+    def pair_cfg(self) -> dict:
+        return nb_get_pair_cfg(self.h)
 
     def profile(self, enable: bool = True):
         nb_profile(self.h, enable)

@@ -262,3 +262,66 @@ def test_gravity_only_flag(nbm, orc):
     ox, ov, om, oR, og = oracle_ic(orc, desc, params)
     ref = orc.forces(ox, ov, om, oR, np.zeros_like(og), G=1.0, eps=params["eps"])
     assert rms_rel(a, ref) <= 1e-5
+
+
+# ---------------------------------------------------------------- launch variants
+def _variants():
+    return [(128, 4, 256, 2, 0), (128, 4, 256, 2, 1), (256, 4, 256, 2, 1), (64, 4, 256, 2, 1),
+            (128, 8, 128, 2, 0), (128, 8, 128, 2, 1), (128, 8, 128, 2, 2), (256, 8, 128, 2, 2),
+            (128, 2, 256, 3, 0), (128, 4, 128, 4, 1)]
+
+
+@pytest.mark.parametrize("cfg", _variants())
+def test_every_pair_variant_matches_oracle(nbm, orc, cfg):
+    """Each built (tile, i per thread, threads, blocks) variant, on a ragged
+    size with per-element masses (per-pair mass path) and on the binary
+    (uniform-mass tiles)."""
+    s, (x, v, m, R, gam) = _random_system(nbm, 2049, 77, 32)
+    with s:
+        s.set_pair_cfg(*cfg)
+        a = s.forces()
+    ref = orc.forces(x, v, m, R, gam, G=1.0, eps=0.003, beta=0.35)
+    assert rms_rel(a, ref) <= 1e-5
+    desc, params = workload_kwargs("binary_1k")
+    with _make(nbm, desc, params) as s:
+        s.set_pair_cfg(*cfg)
+        a = s.forces()
+    ox, ov, om, oR, og = oracle_ic(orc, desc, params)
+    ref = orc.forces(ox, ov, om, oR, og, G=1.0, eps=params["eps"], beta=params["beta"])
+    assert rms_rel(a, ref) <= 1e-5
+
+
+def test_autotune_keeps_parity(nbm, orc):
+    desc, params = workload_kwargs("binary_1k")
+    with _make(nbm, desc, params) as s:
+        best = s.autotune(2)
+        assert (best["tile"], best["i_per_thread"], best["threads"], best["min_blocks"],
+                best["nr_slots"]) in _variants()
+        assert best["ms"] > 0
+        cfg = s.pair_cfg()
+        assert cfg["tile"] == best["tile"]
+        a = s.forces()
+    ox, ov, om, oR, og = oracle_ic(orc, desc, params)
+    ref = orc.forces(ox, ov, om, oR, og, G=1.0, eps=params["eps"], beta=params["beta"])
+    assert rms_rel(a, ref) <= 1e-5
+
+
+def test_graph_replay_equals_direct_launches(nbm):
+    """Multi-step calls on a non-default stream replay a captured CUDA graph;
+    the result is bitwise that of direct launches on the default stream."""
+    import torch
+    desc, params = workload_kwargs("binary_1k")
+    desc = dict(desc, expand_rate=1e-3, expand_steps=-1)
+    with _make(nbm, desc, params) as s:
+        s.step(7)
+        s.step(7)
+        r_direct = _state(s)
+    stream = torch.cuda.Stream()
+    with _make(nbm, desc, params, stream=stream) as s:
+        s.step(7)
+        s.step(7)
+        s.sync()
+        r_graph = _state(s)
+    for a, b in zip(r_direct[:3], r_graph[:3]):
+        assert np.array_equal(a, b)
+    assert r_graph[3].step == 14
