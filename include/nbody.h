@@ -247,6 +247,34 @@ nb_status nb_profile(nb_system_t sys, int enable);
  * them afterwards.  Counts kernels and pairs even when timing is off. */
 nb_status nb_profile_read(nb_system_t sys, nb_prof* out, int reset);
 
+/* ---- allocation-free pair term ----------------------------------------- */
+
+/* No counterpart in the paper: an entry point for callers that may not
+ * allocate device memory -- for example code running inside a host
+ * framework that owns all device memory through its own pool (a cudaMalloc
+ * from this library would bypass and fragment the pool, and cudaFree
+ * synchronises the whole device), or a latency-critical thread that may not
+ * block on that synchronisation.
+ *
+ * Evaluates the pair term of Eq. 4 (no contact term): for each element i,
+ *   acc_out[i] = sum_{j != i} G m_j (x_j - x_i) / (r_ij (r_ij + eps)^2),
+ * with the library's FP32 pair kernel, into caller-owned memory.
+ *   xyzm:    device pointer, n x 4 doubles (x, y, z, m) per element
+ *   n:       1 .. NB_NOALLOC_MAX_N; larger n returns NB_EINVAL
+ *   acc_out: device pointer, n x 3 doubles
+ *   stream:  cudaStream_t (as void*) the work is ordered on
+ * Its scratch is one fixed array of about 2.4 MB in the library's device
+ * image, held by every GPU that loads the library until the process exits;
+ * the call allocates nothing (no cudaMalloc, cudaFree or allocating library
+ * routine).  The first call on a device looks up the array's device address
+ * with that device current; make it before any stream capture.  Calls share
+ * the array: calls whose work overlaps on the GPU race and must be
+ * serialised.  Blocks until acc_out is written; NB_ETIMEOUT if a device
+ * wait gave up. */
+#define NB_NOALLOC_MAX_N 16384
+nb_status nb_pair_forces_noalloc(const double* xyzm, int64_t n, double G, double eps,
+                                 double* acc_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

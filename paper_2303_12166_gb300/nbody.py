@@ -105,6 +105,7 @@ _sig("nb_get_state", ctypes.c_int, [_P, _P, _P, ctypes.POINTER(nb_ckpt_meta)])
 _sig("nb_set_state", ctypes.c_int, [_P, _P, _P, ctypes.POINTER(nb_ckpt_meta)])
 _sig("nb_profile", ctypes.c_int, [_P, ctypes.c_int])
 _sig("nb_autotune", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(nb_pair_cfg)])
+_sig("nb_pair_forces_noalloc", ctypes.c_int, [_P, _I64, _D, _D, _P, _P])
 _sig("nb_set_pair_cfg", ctypes.c_int, [_P, ctypes.POINTER(nb_pair_cfg)])
 _sig("nb_get_pair_cfg", ctypes.c_int, [_P, ctypes.POINTER(nb_pair_cfg)])
 _sig("nb_profile_read", ctypes.c_int, [_P, ctypes.POINTER(nb_prof), ctypes.c_int])
@@ -283,6 +284,19 @@ def nb_get_pair_cfg(h) -> dict:
     c = nb_pair_cfg()
     _check(_lib.nb_get_pair_cfg(_P(h), ctypes.byref(c)), "nb_get_pair_cfg")
     return _cfg_dict(c)
+
+
+NB_NOALLOC_MAX_N = 16384
+
+
+def nb_pair_forces_noalloc(xyzm_ptr: int, n: int, G: float, eps: float, acc_ptr: int,
+                           stream=None) -> None:
+    """Pair term of Eq. 4 into caller-owned device memory, without any
+    allocation by the library (see include/nbody.h).  Pointers are device
+    addresses (e.g. tensor.data_ptr()): xyzm n x 4 doubles, acc n x 3."""
+    _check(_lib.nb_pair_forces_noalloc(_P(xyzm_ptr), int(n), float(G), float(eps),
+                                       _P(acc_ptr), _P(_stream_ptr(stream))),
+           "nb_pair_forces_noalloc")
 
 
 def nb_profile(h, enable: bool) -> None:
