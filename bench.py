@@ -212,6 +212,128 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ batched / served
+SWEEP_PARAMS = dict(eps=0.005, dt=5e-4, beta=0.5)
+
+
+def measure_batched(nbm, torch, dev, stream, args, ws, rank):
+    """Parameter sweep of independent binaries (element counts log-uniform in
+    [2,048, 65,536]) advanced in one batch: one persistent pair-kernel launch
+    per step for all systems.  Systems are dealt to ranks (no exchange).
+    Compared with the same systems advanced one at a time through the
+    single-system API, with and without FP64 diagnostics every step."""
+    import synth
+    from paper_2303_12166_gb300.dist import max_over_ranks, shard, sum_over_ranks
+    systems = synth.sweep_systems(args.sweep_systems, seed=0)
+    mine = shard(len(systems), ws, rank)
+    descs = [nbm.nb_desc_default(**systems[s]) for s in mine]
+    params = [nbm.nb_params_default(**SWEEP_PARAMS) for _ in mine]
+    b = nbm.Batch(descs, params, stream=stream)
+    tuned = b.autotune(1)
+    b.step(3)
+    b.sync()
+    b.profile(True)
+    b.profile_read(reset=True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    b.step(args.batched_steps)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    b.sync()
+    prof = b.profile_read(reset=True)
+    b.close()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dev)
+    pairs_mine = float(sum((d.n_donor + d.n_accretor) ** 2 for d in descs))
+    pairs = sum_over_ranks(pairs_mine, dev)
+    el = ms * 1e-3
+    out = {"workload": f"sweep_{len(systems)}", "systems": len(systems),
+           "n_range": [2048, 65536], "steps": args.batched_steps,
+           "value": len(systems) * args.batched_steps / el, "unit": "system-steps/s",
+           "pairs_per_s": pairs * args.batched_steps / el,
+           "ms_per_step": ms / args.batched_steps,
+           "pair_cfg": {k: tuned[k] for k in ("tile", "i_per_thread", "threads", "min_blocks",
+                                               "nr_slots")},
+           "phase_ms": {"pair": prof["pair_ms"], "contact": prof["contact_ms"],
+                        "update": prof["update_ms"]},
+           "gpu_launches": int(prof["kernels"])}
+    if rank == 0 and args.per_system_sample > 0:
+        # the same kind of systems one at a time (a sample, extrapolated per
+        # system-step): plain stepping, and stepping with FP64 diagnostics
+        sample = [systems[s] for s in range(0, len(systems), len(systems) // args.per_system_sample)]
+        sample = sample[:args.per_system_sample]
+        sysms = [nbm.System(nbm.nb_desc_default(**d), nbm.nb_params_default(**SWEEP_PARAMS),
+                            stream=stream) for d in sample]
+        k = 3
+        for sy in sysms:
+            sy.step(1)
+            sy.sync()
+        t0 = time.perf_counter()
+        for sy in sysms:
+            sy.step(k)
+            sy.sync()
+        plain = len(sysms) * k / (time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        for sy in sysms:
+            for _ in range(k):
+                sy.step(1)
+                sy.diagnostics()
+        diag = len(sysms) * k / (time.perf_counter() - t0)
+        for sy in sysms:
+            sy.close()
+        # the sample's size mix differs from the sweep's; normalise per pair
+        pairs_sample = float(sum((d["n_donor"] + d["n_accretor"]) ** 2 for d in sample))
+        per_sys_pairs = pairs / len(systems)
+        out["per_system_path"] = {
+            "systems_sampled": len(sample), "steps": k,
+            "plain_system_steps_per_s": plain * (pairs_sample / len(sample)) / per_sys_pairs,
+            "fp64_diag_system_steps_per_s": diag * (pairs_sample / len(sample)) / per_sys_pairs,
+            "note": "one system at a time through nb_step / nb_diagnostics, rescaled to the "
+                    "sweep's mean pairs per system"}
+        out["speedup_vs_per_system_fp64_diag"] = out["value"] / \
+            out["per_system_path"]["fp64_diag_system_steps_per_s"]
+        out["speedup_vs_per_system_plain"] = out["value"] / \
+            out["per_system_path"]["plain_system_steps_per_s"]
+    return out
+
+
+def measure_served(nbm, stream, args):
+    """Poisson arrivals (20/s) of sweep runs: element count log-uniform in
+    [4,096, 262,144], steps uniform in [1,000, 20,000] divided by
+    --served-steps-div; served by continuous batching (nb_server)."""
+    import synth
+    trace = synth.served_trace(args.served_requests, seed=0, steps_div=args.served_steps_div)
+    srv = nbm.nb_server_create(int(150e9), 64, 262144, 32, stream)
+    try:
+        info = nbm.nb_server_info(srv)
+        t0 = time.perf_counter()
+        tickets = []
+        for r in trace:
+            wait = r["t_arrival"] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            tickets.append(nbm.nb_submit(srv, nbm.nb_desc_default(**r["desc"]),
+                                         nbm.nb_params_default(**SWEEP_PARAMS), r["nsteps"]))
+        nbm.nb_server_drain(srv, 1800.0)
+        res = [nbm.nb_poll(srv, t) for t in tickets]
+    finally:
+        nbm.nb_server_destroy(srv)
+    bad = [r for r in res if r["status"] != 0]
+    lat = np.array([r["t_finish"] - r["t_submit"] for r in res])
+    span = max(r["t_finish"] for r in res) - min(r["t_submit"] for r in res)
+    pairs = float(sum(r["n"] ** 2 * r["steps"] for r in res))
+    steps = float(sum(r["steps"] for r in res))
+    return {"workload": f"served_{len(trace)}", "requests": len(trace), "arrival_hz": 20.0,
+            "n_range": [4096, 262144],
+            "steps_range": [1000 // args.served_steps_div, 20000 // args.served_steps_div],
+            "slots": info["nslots"], "failed": len(bad),
+            "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)),
+            "makespan_s": span, "value": pairs / span, "unit": "pairs/s",
+            "system_steps_per_s": steps / span}
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(args):
     import torch
@@ -308,6 +430,11 @@ def run_ours(args):
 
     working_set = sysm.info.device_bytes
     sysm.close()
+    batched = served = None
+    if not args.no_extras:
+        batched = measure_batched(nbm, torch, dev, stream, args, ws, rank)
+        if rank == 0 and ws == 1:
+            served = measure_served(nbm, stream, args)
     if rank == 0:
         cfg = _config(args.workload, w, {
             "force_prec": 64 if args.fp64 else 32,
@@ -334,6 +461,8 @@ def run_ours(args):
             "phase_ms": {"pair": prof["pair_ms"], "contact": prof["contact_ms"],
                          "update": prof["update_ms"]},
             "clocks": clk.summary(),
+            "batched": batched,
+            "served": served,
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -352,6 +481,13 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-sweep and served measurements")
+    ap.add_argument("--sweep-systems", type=int, default=256)
+    ap.add_argument("--batched-steps", type=int, default=10)
+    ap.add_argument("--per-system-sample", type=int, default=8)
+    ap.add_argument("--served-requests", type=int, default=32)
+    ap.add_argument("--served-steps-div", type=int, default=100)
     ap.add_argument("--pair-cfg", default="",
                     help="tile,i_per_thread,threads,min_blocks,nr_slots (skips the autotuner)")
     args = ap.parse_args(argv)

@@ -247,6 +247,80 @@ nb_status nb_profile(nb_system_t sys, int enable);
  * them afterwards.  Counts kernels and pairs even when timing is off. */
 nb_status nb_profile_read(nb_system_t sys, nb_prof* out, int reset);
 
+/* ---- batches of independent systems ------------------------------------ */
+
+/* A batch advances many independent binary systems (parameter sweeps) in the
+ * same kernel launches: one persistent pair-kernel launch covers every
+ * system's pair term (work items longest first), one contact pass and one
+ * update kernel cover all elements.  Each system is built exactly as
+ * nb_create_system builds it, and its result is bitwise the same as alone
+ * (the work split of a system depends only on its own size and the launch
+ * shape). */
+typedef struct nb_batch* nb_batch_t;
+
+/* descs[s], params[s] for s < nsys; every params[s].force_prec must be equal.
+ * Enqueued on `stream`; *out is valid on return. */
+nb_status nb_batch_create(const nb_desc* descs, const nb_params* params, int32_t nsys,
+                          void* stream, nb_batch_t* out);
+void nb_batch_destroy(nb_batch_t b);
+nb_status nb_batch_info(nb_batch_t b, int32_t sys, nb_info* out);
+/* nsteps leap-frog steps of every system (asynchronous, like nb_step) */
+nb_status nb_batch_step(nb_batch_t b, int64_t nsteps);
+nb_status nb_batch_sync(nb_batch_t b);
+nb_status nb_batch_forces(nb_batch_t b, int32_t sys, double* acc_out, int out_on_device);
+nb_status nb_batch_diagnostics(nb_batch_t b, int32_t sys, nb_diag* out);
+nb_status nb_batch_get_state(nb_batch_t b, int32_t sys, double* xv_out, double* a_out,
+                             nb_ckpt_meta* meta);
+nb_status nb_batch_set_pair_cfg(nb_batch_t b, const nb_pair_cfg* cfg);
+nb_status nb_batch_autotune(nb_batch_t b, int reps, nb_pair_cfg* best);
+nb_status nb_batch_profile(nb_batch_t b, int enable);
+nb_status nb_batch_profile_read(nb_batch_t b, nb_prof* out, int reset);
+
+/* ---- serving: continuous batching of parameter-sweep runs --------------- */
+
+/* A server owns one batch of fixed-size slots on the device (as many slots of
+ * max_n elements as hbm_budget_bytes allows, at most max_slots) and a host
+ * thread that serves submitted runs: queued runs are admitted in arrival
+ * order as slots free up, all admitted runs advance together (one pair
+ * kernel launch per step for all of them), and each run is retired the moment
+ * it completes its steps, freeing its slot for the next.  State stays on the
+ * device for the whole run.  A run's result equals the result of running the
+ * same request alone. */
+typedef struct nb_server* nb_server_t;
+
+typedef struct nb_result {
+    nb_status status;     /* NB_OK, or what ended the run (NB_ENONFINITE, ...) */
+    int32_t reserved;
+    int64_t n;            /* element count */
+    int64_t steps;        /* steps completed */
+    double t_submit;      /* seconds on the server clock (nb_server_clock) */
+    double t_start;       /* admission */
+    double t_finish;      /* retirement */
+    nb_diag diag;         /* diagnostics of the final state; e_grav, e_rep and
+                             e_tot are NaN (the O(N^2) energy pass is skipped) */
+} nb_result;
+
+/* prec: 32 or 64 (the force precision of every run).  NB_EBUDGET if not even
+ * one slot of max_n elements fits the budget. */
+nb_status nb_server_create(size_t hbm_budget_bytes, int32_t max_slots, int64_t max_n,
+                           int32_t prec, void* stream, nb_server_t* out);
+nb_status nb_server_info(nb_server_t srv, int32_t* nslots, int64_t* slot_n,
+                         int64_t* device_bytes);
+/* Queue a run of nsteps steps; *ticket identifies it.  The arrays of desc are
+ * copied.  NB_EBUDGET if the system is larger than a slot. */
+nb_status nb_submit(nb_server_t srv, const nb_desc* desc, const nb_params* params,
+                    int64_t nsteps, uint64_t* ticket);
+/* NB_OK with *out filled once the run has finished, NB_PENDING before,
+ * NB_ENOTFOUND for an unknown ticket. */
+nb_status nb_poll(nb_server_t srv, uint64_t ticket, nb_result* out);
+/* Wait until every submitted run has finished (NB_ETIMEOUT after timeout_s). */
+nb_status nb_server_drain(nb_server_t srv, double timeout_s);
+/* Seconds since the server was created (the clock of nb_result's times). */
+double nb_server_clock(nb_server_t srv);
+/* Stop the serving thread (runs still queued or active are abandoned) and
+ * free the device memory. */
+void nb_server_destroy(nb_server_t srv);
+
 /* ---- allocation-free pair term ----------------------------------------- */
 
 /* No counterpart in the paper: an entry point for callers that may not

@@ -7,6 +7,7 @@
 #include <mutex>
 #include <new>
 #include <utility>
+#include <vector>
 
 #include "nb_batch.h"
 
@@ -16,6 +17,11 @@ using nb::set_error;
 struct nb_system {
     Batch batch;
     nb_info info{};
+};
+
+struct nb_batch {
+    Batch batch;
+    std::vector<nb_info> info;
 };
 
 namespace {
@@ -221,6 +227,120 @@ nb_status nb_profile(nb_system_t sys, int enable) {
 nb_status nb_profile_read(nb_system_t sys, nb_prof* out, int reset) {
     if (!sys) return set_error(NB_EINVAL, "null system");
     return guarded([&] { return sys->batch.read_profile(out, reset != 0); });
+}
+
+// ------------------------------------------------------------------ batches
+nb_status nb_batch_create(const nb_desc* descs, const nb_params* params, int32_t nsys,
+                          void* stream, nb_batch_t* out) {
+    return guarded([&]() -> nb_status {
+        if (!descs || !params || !out || nsys < 1)
+            return set_error(NB_EINVAL, "nb_batch_create: need nsys >= 1 and non-null arrays");
+        *out = nullptr;
+        std::vector<nb::SystemInit> si(nsys);
+        std::vector<int64_t> sizes(nsys);
+        for (int32_t s = 0; s < nsys; ++s) {
+            if (params[s].force_prec != params[0].force_prec)
+                return set_error(NB_EINVAL, "nb_batch_create: systems differ in force_prec");
+            nb_status st = nb::build_system(descs[s], params[s], si[s]);
+            if (st != NB_OK) return st;
+            sizes[s] = si[s].n;
+        }
+        nb_batch* b = new nb_batch();
+        b->batch.set_use_graph(true);
+        nb_status st = b->batch.init(sizes, params[0].force_prec, static_cast<cudaStream_t>(stream));
+        for (int32_t s = 0; st == NB_OK && s < nsys; ++s) st = b->batch.load(s, si[s], true);
+        if (st == NB_OK) st = b->batch.init_acc(-1);
+        if (st == NB_OK) st = b->batch.sync();
+        if (st != NB_OK) {
+            delete b;
+            return st;
+        }
+        for (auto& x : si) b->info.push_back(x.info);
+        *out = b;
+        return NB_OK;
+    });
+}
+
+void nb_batch_destroy(nb_batch_t b) {
+    try {
+        delete b;
+    } catch (...) {
+    }
+}
+
+static nb_status check_sys(nb_batch_t b, int32_t sys) {
+    if (!b) return set_error(NB_EINVAL, "null batch");
+    if (sys < 0 || sys >= (int32_t)b->info.size())
+        return set_error(NB_ENOTFOUND, "no system %d in the batch", (int)sys);
+    return NB_OK;
+}
+
+nb_status nb_batch_info(nb_batch_t b, int32_t sys, nb_info* out) {
+    nb_status st = check_sys(b, sys);
+    if (st != NB_OK) return st;
+    if (!out) return set_error(NB_EINVAL, "null output");
+    *out = b->info[sys];
+    out->device_bytes = b->batch.device_bytes();
+    return NB_OK;
+}
+
+nb_status nb_batch_step(nb_batch_t b, int64_t nsteps) {
+    if (!b) return set_error(NB_EINVAL, "null batch");
+    return guarded([&] { return b->batch.step(nsteps); });
+}
+
+nb_status nb_batch_sync(nb_batch_t b) {
+    if (!b) return set_error(NB_EINVAL, "null batch");
+    return guarded([&] { return b->batch.sync(); });
+}
+
+nb_status nb_batch_forces(nb_batch_t b, int32_t sys, double* acc_out, int out_on_device) {
+    nb_status st = check_sys(b, sys);
+    if (st != NB_OK) return st;
+    return guarded([&] { return b->batch.forces_out(sys, acc_out, out_on_device != 0); });
+}
+
+nb_status nb_batch_diagnostics(nb_batch_t b, int32_t sys, nb_diag* out) {
+    nb_status st = check_sys(b, sys);
+    if (st != NB_OK) return st;
+    return guarded([&] { return b->batch.diagnostics(sys, out); });
+}
+
+nb_status nb_batch_get_state(nb_batch_t b, int32_t sys, double* xv_out, double* a_out,
+                             nb_ckpt_meta* meta) {
+    nb_status st = check_sys(b, sys);
+    if (st != NB_OK) return st;
+    return guarded([&] { return b->batch.get_state(sys, xv_out, a_out, meta); });
+}
+
+nb_status nb_batch_set_pair_cfg(nb_batch_t b, const nb_pair_cfg* cfg) {
+    if (!b || !cfg) return set_error(NB_EINVAL, "null argument");
+    return guarded([&] {
+        nb::PairCfg c{cfg->tile, cfg->i_per_thread, cfg->threads, 0, cfg->min_blocks,
+                      cfg->nr_slots};
+        return b->batch.set_pair_cfg(c);
+    });
+}
+
+nb_status nb_batch_autotune(nb_batch_t b, int reps, nb_pair_cfg* best) {
+    if (!b) return set_error(NB_EINVAL, "null batch");
+    return guarded([&]() -> nb_status {
+        nb::PairCfg c{};
+        double ms = 0;
+        nb_status st = b->batch.autotune(reps, &c, &ms);
+        if (st == NB_OK && best) *best = to_abi(c, ms);
+        return st;
+    });
+}
+
+nb_status nb_batch_profile(nb_batch_t b, int enable) {
+    if (!b) return set_error(NB_EINVAL, "null batch");
+    return guarded([&] { return b->batch.set_profile(enable != 0); });
+}
+
+nb_status nb_batch_profile_read(nb_batch_t b, nb_prof* out, int reset) {
+    if (!b) return set_error(NB_EINVAL, "null batch");
+    return guarded([&] { return b->batch.read_profile(out, reset != 0); });
 }
 
 }  // extern "C"

@@ -359,6 +359,14 @@ nb_status Batch::init(const std::vector<int64_t>& n_per_slot, int prec, cudaStre
     NB_TRY(alloc_((void**)&d_.sorted, nt * sizeof(uint32_t)));
     NB_TRY(alloc_((void**)&d_.scell, nt * sizeof(uint64_t)));
     NB_TRY(alloc_((void**)&d_.spos, nt * sizeof(float4)));
+    NB_TRY(alloc_((void**)&d_.slo, nt * sizeof(float4)));
+    NB_TRY(alloc_((void**)&d_.svel, nt * sizeof(float4)));
+    {
+        float* base = nullptr;
+        NB_TRY(alloc_((void**)&base, 6 * nt * sizeof(float)));
+        d_.plo = Vec3SoA{base, base + nt, base + 2 * nt};
+        d_.v32 = Vec3SoA{base + 3 * nt, base + 4 * nt, base + 5 * nt};
+    }
     NB_TRY(alloc_((void**)&d_.red, diag_scratch_doubles() * sizeof(double)));
     NB_TRY(alloc_((void**)&d_.diag_out, NB_DIAG_OUT * sizeof(double)));
     SysConst* scd = nullptr;
@@ -397,6 +405,7 @@ nb_status Batch::load(int s, const SystemInit& si, bool defer_forces) {
     for (int k = 0; k < 3; ++k) c.origin[k] = si.origin[k];
     c.grow_f0 = si.grow_f0;
     c.grow_rate = si.grow_rate;
+    c.grow_rel = si.grow_rate / si.grow_f0;
     c.grow_cap = si.grow_cap;
     c.xl1 = si.xl1;
     c.active = 1;
@@ -490,12 +499,8 @@ nb_status Batch::plan_pairs_() {
     const int64_t slots = (int64_t)sm_count_ * occ;
 
     std::vector<int> act;
-    double total = 0;
     for (int s = 0; s < nslots(); ++s)
-        if (sc_[s].active) {
-            act.push_back(s);
-            total += (double)sc_[s].n * (double)sc_[s].n;
-        }
+        if (sc_[s].active) act.push_back(s);
     items_.clear();
     int maxchunks = 1;
     dynamic_ = act.size() > 1;
@@ -504,33 +509,27 @@ nb_status Batch::plan_pairs_() {
         const int64_t nib = (c.n + I - 1) / I;
         const int64_t ntiles = (c.n + tile - 1) / tile;
         const int64_t smax = std::min<int64_t>(NB_MAX_CHUNKS, ntiles);
+        // Chunk count from the system's own size and the launch shape only
+        // (never from the rest of the batch), so a system gives bitwise the
+        // same result alone and in a batch: the smallest count whose items
+        // fill the persistent grid's waves to 96 %, with chunks of at least
+        // kMinChunkTiles tiles.
+        constexpr int64_t kMinChunkTiles = 16;
+        const int64_t smax_sys = std::max<int64_t>(1, std::min(smax, ntiles / kMinChunkTiles));
+        double best = -1;
         int64_t S = 1;
-        if (act.size() == 1) {
-            // fill the persistent grid evenly: smallest chunk count whose item
-            // count wastes at most 4 % of the last wave
-            double best = -1;
-            int64_t bestS = 1;
-            for (int64_t cand = 1; cand <= smax; ++cand) {
-                const int64_t items = nib * cand;
-                const int64_t waves = (items + slots - 1) / slots;
-                const double eff = (double)items / (double)(waves * slots);
-                if (eff > best + 1e-12) {
-                    best = eff;
-                    bestS = cand;
-                }
-                if (eff >= 0.96) {
-                    bestS = cand;
-                    break;
-                }
+        for (int64_t cand = 1; cand <= smax_sys; ++cand) {
+            const int64_t items = nib * cand;
+            const int64_t waves = (items + slots - 1) / slots;
+            const double eff = (double)items / (double)(waves * slots);
+            if (eff > best + 1e-12) {
+                best = eff;
+                S = cand;
             }
-            S = bestS;
-        } else {
-            // batched: items of roughly equal cost, about six per CTA slot
-            const double target =
-                std::max((double)I * tile * 8.0, total / ((double)slots * 6.0));
-            const double cost_full = (double)I * (double)(ntiles * tile);
-            S = (int64_t)std::llround(cost_full / target);
-            S = std::max<int64_t>(1, std::min(S, smax));
+            if (eff >= 0.96) {
+                S = cand;
+                break;
+            }
         }
         const int64_t tpc = (ntiles + S - 1) / S;  // tiles per chunk
         S = (ntiles + tpc - 1) / tpc;
@@ -802,6 +801,30 @@ nb_status Batch::eval_forces(int kofs, bool pot, bool energy) {
     return launch_pairs_(pot);
 }
 
+nb_status Batch::store_acc(int only) {
+    NB_CU(launch_store_acc(d_, only, stream_));
+    kernels_ += 1;
+    return NB_OK;
+}
+
+nb_status Batch::init_acc_subset(const std::vector<int>& slots) {
+    std::vector<int32_t> was(nslots());
+    for (int s = 0; s < nslots(); ++s) {
+        was[s] = sc_[s].active;
+        sc_[s].active = 0;
+    }
+    for (int s : slots)
+        if (s >= 0 && s < nslots()) sc_[s].active = was[s];
+    planned_ = false;
+    consts_dirty_ = true;
+    nb_status st = init_acc(-1);
+    for (int s = 0; s < nslots(); ++s) sc_[s].active = was[s];
+    planned_ = false;
+    consts_dirty_ = true;
+    if (st != NB_OK) return st;
+    return push_consts_();
+}
+
 nb_status Batch::init_acc(int only) {
     NB_TRY(eval_forces(0, false, false));
     NB_CU(launch_store_acc(d_, only, stream_));
@@ -910,10 +933,18 @@ nb_status Batch::forces_out(int s, double* out, bool out_on_device) {
     return sync();
 }
 
-nb_status Batch::diagnostics(int s, nb_diag* out) {
+nb_status Batch::read_flags(std::vector<SysMut>& out) {
+    out.assign(nslots(), SysMut{});
+    NB_CU(cudaMemcpyAsync(out.data(), d_.sm, out.size() * sizeof(SysMut), cudaMemcpyDeviceToHost,
+                          stream_));
+    NB_CU(cudaStreamSynchronize(stream_));
+    return NB_OK;
+}
+
+nb_status Batch::diagnostics(int s, nb_diag* out, bool energy) {
     if (s < 0 || s >= nslots() || !sc_[s].active) return set_error(NB_ENOTFOUND, "no system %d", s);
     if (!out) return set_error(NB_EINVAL, "null output");
-    NB_TRY(eval_forces(0, true, true));
+    if (energy) NB_TRY(eval_forces(0, true, true));
     NB_CU(launch_diag(d_, s, stream_));
     double v[NB_DIAG_OUT];
     SysMut m{};
@@ -925,9 +956,9 @@ nb_status Batch::diagnostics(int s, nb_diag* out) {
     out->step = m.k;
     out->time = (double)m.k * c.dt;
     out->e_kin = v[1];
-    out->e_grav = v[19];
-    out->e_rep = v[20];
-    out->e_tot = v[1] + v[19] + v[20];
+    out->e_grav = energy ? v[19] : NAN;
+    out->e_rep = energy ? v[20] : NAN;
+    out->e_tot = energy ? v[1] + v[19] + v[20] : NAN;
     for (int d = 0; d < 3; ++d) {
         out->p[d] = v[2 + d];
         out->l[d] = v[5 + d];

@@ -64,10 +64,19 @@ public:
     // Evaluate forces at the current state and store them as the integrator's
     // a^k of system `only` (-1: every active system).
     nb_status init_acc(int only = -1);
+    // A = the last force evaluation, for system `only` (-1: every active system)
+    nb_status store_acc(int only);
+    // a^k of the listed (active) systems only: the others sit out the force
+    // evaluation and keep their state
+    nb_status init_acc_subset(const std::vector<int>& slots);
 
     nb_status sync();                 // wait + report device-side flags
     nb_status forces_out(int s, double* out, bool out_on_device);
-    nb_status diagnostics(int s, nb_diag* out);
+    // energy = false skips the potential-energy force pass (e_grav and e_rep
+    // are then NaN): O(N) instead of O(N^2)
+    nb_status diagnostics(int s, nb_diag* out, bool energy = true);
+    // wait for the stream and copy every system's device flags
+    nb_status read_flags(std::vector<SysMut>& out);
     nb_status get_state(int s, double* xv, double* a, nb_ckpt_meta* meta);
     nb_status set_state(int s, const double* xv, const double* a, const nb_ckpt_meta* meta);
 

@@ -21,16 +21,20 @@
 //      fixed order; a candidate must carry the visited cell's id (hash
 //      collisions are skipped) and pass an FP32 distance pre-test on the
 //      FP32 copy with a margin that covers its rounding.
-// Precision.  Every decision is taken in FP64 from the FP64 state, as in
-// the direct FP64 sum: the difference d = x_j - x_i, d^2, the contact test
-// (R_i + R_j)^2 - d^2 > 0 and the closing test d.(v_j - v_i) < 0.  The force
-// magnitude is then evaluated in FP32 from those FP64 quantities: the
-// overlap depth is (Rs^2 - d^2)/(Rs + r) with Rs^2 - d^2 formed by one FP64
-// fused multiply-add, so the volume pi (4R + r) depth^2 / 12 suffers no
-// cancellation and the FP32 relative error of the force stays ~1e-7.  FP64
-// throughput on this GPU is a small fraction of FP32, so this keeps the
-// FP64 work to ~16 operations per contact.  The energy variant (used by the
-// diagnostics) evaluates the whole term in FP64.
+// Precision.  Both decisions of a pair -- contact, (R_i + R_j)^2 - d^2 > 0,
+// and closing, d.(v_j - v_i) < 0 -- come out as the direct FP64 sum takes
+// them.  The common case settles them in FP32: d is the difference of the
+// double-float positions (hi + lo, ~1e-7 relative to |d| itself, not to
+// |x|), v the FP32 velocity copy, and each decision is accepted only when
+// its FP32 value clears a bound on its rounding error; otherwise (and for
+// contacts shallower than 1e-3 (R_i + R_j)^2 in Rs^2 - d^2, where the FP32
+// depth would lose digits) the pair is redone from the FP64 state.  The
+// force magnitude is FP32 with the overlap depth (Rs^2 - d^2)/(Rs + r), so
+// the volume pi (4R + r) depth^2 / 12 suffers no cancellation and its
+// relative error stays ~1e-7.  FP64 throughput on this GPU is a small
+// fraction of FP32, which is why FP64 is kept off the common path.  The
+// FP64 force path and the energy variant (diagnostics) evaluate every
+// candidate in FP64.
 #include "nb_device.cuh"
 
 namespace nb {
@@ -151,6 +155,8 @@ __global__ void scatter_kernel(BatchDev b, int kofs) {
     b.sorted[slot] = (uint32_t)i;
     b.scell[slot] = b.cellid[i];
     b.spos[slot] = make_float4(b.pj.x[i], b.pj.y[i], b.pj.z[i], (float)R);
+    b.slo[slot] = make_float4(b.plo.x[i], b.plo.y[i], b.plo.z[i], (float)b.E[i].y);
+    b.svel[slot] = make_float4(b.v32.x[i], b.v32.y[i], b.v32.z[i], __int_as_float(s));
 }
 
 // Insertion sort of every bucket by element index (buckets hold a few
@@ -164,20 +170,26 @@ __global__ void bucket_sort_kernel(BatchDev b) {
     uint32_t* s = b.sorted + base;
     uint64_t* sc = b.scell + base;
     float4* sp = b.spos + base;
+    float4* sl = b.slo + base;
+    float4* sv = b.svel + base;
     for (uint32_t u = 1; u < c; ++u) {
         const uint32_t v = s[u];
         const uint64_t vc = sc[u];
-        const float4 vp = sp[u];
+        const float4 vp = sp[u], vl = sl[u], vv = sv[u];
         uint32_t w = u;
         while (w > 0 && s[w - 1] > v) {
             s[w] = s[w - 1];
             sc[w] = sc[w - 1];
             sp[w] = sp[w - 1];
+            sl[w] = sl[w - 1];
+            sv[w] = sv[w - 1];
             --w;
         }
         s[w] = v;
         sc[w] = vc;
         sp[w] = vp;
+        sl[w] = vl;
+        sv[w] = vv;
     }
 }
 
@@ -185,8 +197,63 @@ __device__ __forceinline__ float max_abs3(float4 p) {
     return fmaxf(fabsf(p.x), fmaxf(fabsf(p.y), fabsf(p.z)));
 }
 
-// FULL64: the whole term in FP64 (the FP64 force path and the diagnostics);
-// ENERGY: also the repulsion energy (implies FULL64).
+// Contact of (i, j) from the FP64 state, with the decisions of the direct
+// FP64 sum; the magnitude in FP32 (FULL64: in FP64, and the repulsion energy
+// with ENERGY).  Adds to the accumulators.
+template <bool FULL64, bool ENERGY>
+__device__ __forceinline__ void contact_fp64(const BatchDev& b, const SysConst& c, uint32_t i,
+                                             uint32_t j, int64_t dend, double scale,
+                                             const double4_32a& xi, const double4_32a& vi,
+                                             const double2& ei, double Ri, float inv_m,
+                                             float& ax, float& ay, float& az, double& eax,
+                                             double& eay, double& eaz, double& er) {
+    const double4_32a xj = b.X[j];
+    const double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+    const double d2 = fma(dx, dx, fma(dy, dy, dz * dz));
+    const double2 ej = b.E[j];
+    const double Rs = Ri + ej.x * ((int64_t)j < dend ? scale : 1.0);
+    const double gap2 = fma(Rs, Rs, -d2);  // Rs^2 - d^2
+    if (!(d2 > 0.0) || !(gap2 > -1e-12 * d2)) return;
+    if (!(gap2 > 1e-12 * d2)) {
+        // within rounding of the contact distance: decide as sqrt(d^2) < Rs,
+        // exactly as the direct sum does
+        if (!(sqrt(d2) < Rs)) return;
+    }
+    const double4_32a vj = b.V[j];
+    const double closing = fma(dx, vj.x - vi.x, fma(dy, vj.y - vi.y, dz * (vj.z - vi.z)));
+    if (FULL64) {
+        const double r = sqrt(d2);
+        const double R = 0.5 * Rs;
+        const double g = 0.5 * (ei.y + ej.y);
+        const double pi = 3.14159265358979323846;
+        const double vol = pi * (4.0 / 3.0 * R * R * R - R * R * r + r * r * r / 12.0);
+        const double cf = closing < 0.0 ? 1.0 : c.beta;
+        const double f = -cf * g * vol / (xi.w * r);
+        eax += f * dx;
+        eay += f * dy;
+        eaz += f * dz;
+        if (ENERGY) {
+            const double U = pi * (R * R * R * R - 4.0 / 3.0 * R * R * R * r + 0.5 * R * R * r * r -
+                                   r * r * r * r / 48.0);
+            er += 0.5 * g * U;
+        }
+    } else {
+        const float d2f = (float)d2;
+        const float r = sqrtf(d2f);
+        const float Rsf = (float)Rs;
+        const float depth = fmaxf((float)gap2, 0.f) / (Rsf + r);
+        const float vol = 3.14159265358979f / 12.f * (2.f * Rsf + r) * depth * depth;
+        const float g = 0.5f * (float)(ei.y + ej.y);
+        const float cf = closing < 0.0 ? 1.f : (float)c.beta;
+        const float f = -cf * g * vol * inv_m / r;
+        ax = fmaf(f, (float)dx, ax);
+        ay = fmaf(f, (float)dy, ay);
+        az = fmaf(f, (float)dz, az);
+    }
+}
+
+// FULL64: every candidate through contact_fp64 in FP64 (the FP64 force path
+// and the diagnostics); ENERGY: also the repulsion energy (implies FULL64).
 template <bool FULL64, bool ENERGY>
 __global__ void __launch_bounds__(128) contact_kernel(BatchDev b, int kofs, uint32_t total_idx) {
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -201,12 +268,14 @@ __global__ void __launch_bounds__(128) contact_kernel(BatchDev b, int kofs, uint
     const double4_32a vi = b.V[i];
     const double2 ei = b.E[i];
     const double Ri = ei.x * ((int64_t)i < dend ? scale : 1.0);
-    const float4 pi4 = b.spos[t];
-    // FP32 pre-test |d| < R_i + R_j with a margin covering the rounding of
-    // both FP32 coordinates (2^-24 relative each, per axis) and of R_j
-    const float Rif = (float)Ri;
+    const float4 pi4 = b.spos[t];  // hi position, current radius
+    const float4 li4 = b.slo[t];   // lo position, gamma
+    const float4 vi4 = b.svel[t];  // FP32 velocity
+    const float Rif = pi4.w;
+    const float gif = li4.w;
     const float mi = max_abs3(pi4);
-    const float inv_m = (float)(1.0 / xi.w);
+    const float vmi = max_abs3(vi4);
+    const float inv_m = 1.0f / (float)xi.w;
     long long cx, cy, cz;
     unpack_cell(b.scell[t], cx, cy, cz);
     const uint32_t mask = b.nbucket - 1;
@@ -229,60 +298,52 @@ __global__ void __launch_bounds__(128) contact_kernel(BatchDev b, int kofs, uint
                 for (uint32_t slot = beg; slot < end; ++slot) {
                     if (b.scell[slot] != cell) continue;  // hash collision
                     const float4 pj = b.spos[slot];
-                    const float dxf = pj.x - pi4.x, dyf = pj.y - pi4.y, dzf = pj.z - pi4.z;
-                    const float tol =
-                        (Rif + pj.w) * 1.0001f + 2.5e-7f * (mi + max_abs3(pj));
-                    if (dxf * dxf + dyf * dyf + dzf * dzf > tol * tol) continue;
+                    const float dxh = pj.x - pi4.x, dyh = pj.y - pi4.y, dzh = pj.z - pi4.z;
+                    // pre-test on the hi parts; the margin covers their rounding
+                    // (2^-24 relative per coordinate) and that of the radii
+                    const float tol = (Rif + pj.w) * 1.0001f + 2.5e-7f * (mi + max_abs3(pj));
+                    if (dxh * dxh + dyh * dyh + dzh * dzh > tol * tol) continue;
+                    const float4 vj4 = b.svel[slot];
+                    if (__float_as_int(vj4.w) != s) continue;  // another system
                     const uint32_t j = b.sorted[slot];
-                    if (j == i || b.sys_of[j] != s) continue;
-                    // FP64 decisions
-                    const double4_32a xj = b.X[j];
-                    const double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
-                    const double d2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                    const double Rs = Ri + b.E[j].x * ((int64_t)j < dend ? scale : 1.0);
-                    const double gap2 = fma(Rs, Rs, -d2);  // Rs^2 - d^2
-                    if (!(d2 > 0.0) || !(gap2 > -1e-12 * d2)) continue;
-                    if (!(gap2 > 1e-12 * d2)) {
-                        // within rounding of the contact distance: decide as
-                        // sqrt(d^2) < Rs, exactly as the direct sum does
-                        if (!(sqrt(d2) < Rs)) continue;
-                    }
-                    const double4_32a vj = b.V[j];
-                    const double closing =
-                        fma(dx, vj.x - vi.x, fma(dy, vj.y - vi.y, dz * (vj.z - vi.z)));
-                    const double2 ej = b.E[j];
+                    if (j == i) continue;
                     if (FULL64) {
-                        // full FP64 evaluation
-                        const double r = sqrt(d2);
-                        const double R = 0.5 * Rs;
-                        const double g = 0.5 * (ei.y + ej.y);
-                        const double pi = 3.14159265358979323846;
-                        const double vol =
-                            pi * (4.0 / 3.0 * R * R * R - R * R * r + r * r * r / 12.0);
-                        const double cf = closing < 0.0 ? 1.0 : c.beta;
-                        const double f = -cf * g * vol / (xi.w * r);
-                        eax += f * dx;
-                        eay += f * dy;
-                        eaz += f * dz;
-                        if (ENERGY) {
-                            const double U = pi * (R * R * R * R - 4.0 / 3.0 * R * R * R * r +
-                                                   0.5 * R * R * r * r - r * r * r * r / 48.0);
-                            er += 0.5 * g * U;
-                        }
-                    } else {
-                        // FP32 magnitude from the FP64 geometry
-                        const float d2f = (float)d2;
-                        const float r = sqrtf(d2f);
-                        const float Rsf = (float)Rs;
-                        const float depth = fmaxf((float)gap2, 0.f) / (Rsf + r);
-                        const float vol = pif / 12.f * (2.f * Rsf + r) * depth * depth;
-                        const float g = 0.5f * (float)(ei.y + ej.y);
-                        const float cf = closing < 0.0 ? 1.f : beta;
-                        const float f = -cf * g * vol * inv_m / r;
-                        ax = fmaf(f, (float)dx, ax);
-                        ay = fmaf(f, (float)dy, ay);
-                        az = fmaf(f, (float)dz, az);
+                        contact_fp64<true, ENERGY>(b, c, i, j, dend, scale, xi, vi, ei, Ri, inv_m,
+                                                   ax, ay, az, eax, eay, eaz, er);
+                        continue;
                     }
+                    // double-float difference: hi parts exact-ish, lo parts small
+                    const float4 lj4 = b.slo[slot];
+                    const float dx = dxh + (lj4.x - li4.x);
+                    const float dy = dyh + (lj4.y - li4.y);
+                    const float dz = dzh + (lj4.z - li4.z);
+                    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    const float Rs = Rif + pj.w;
+                    const float Rs2 = Rs * Rs;
+                    const float gap2 = Rs2 - d2;
+                    // |rounding of gap2| <= ~1.2e-6 Rs^2 near the contact distance
+                    const float eb = 4e-6f * Rs2;
+                    if (gap2 < -eb) continue;  // certainly apart
+                    const float dvx = vj4.x - vi4.x, dvy = vj4.y - vi4.y, dvz = vj4.z - vi4.z;
+                    const float closing = fmaf(dx, dvx, fmaf(dy, dvy, dz * dvz));
+                    // rounding of the FP32 velocities and products
+                    const float cb = 1e-6f * (fabsf(dx) + fabsf(dy) + fabsf(dz)) *
+                                     (vmi + max_abs3(vj4) + 1e-30f);
+                    if (gap2 <= 1e-3f * Rs2 || !(d2 > 0.f) || fabsf(closing) <= cb) {
+                        // ambiguous, very shallow or coincident: from the FP64 state
+                        contact_fp64<false, false>(b, c, i, j, dend, scale, xi, vi, ei, Ri,
+                                                   inv_m, ax, ay, az, eax, eay, eaz, er);
+                        continue;
+                    }
+                    const float r = sqrtf(d2);
+                    const float depth = gap2 / (Rs + r);
+                    const float vol = pif / 12.f * (2.f * Rs + r) * depth * depth;
+                    const float g = 0.5f * (gif + lj4.w);
+                    const float cf = closing < 0.f ? 1.f : beta;
+                    const float f = -cf * g * vol * inv_m / r;
+                    ax = fmaf(f, dx, ax);
+                    ay = fmaf(f, dy, ay);
+                    az = fmaf(f, dz, az);
                 }
             }
     if (FULL64)

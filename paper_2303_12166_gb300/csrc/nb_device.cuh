@@ -36,8 +36,30 @@ __device__ __forceinline__ void unpack_cell(uint64_t p, long long& cx, long long
     cz = (long long)(p & m) - kCellLim;
 }
 
+// spread the low 21 bits of v to every third bit (Morton interleave)
+__device__ __forceinline__ uint64_t spread3(uint64_t v) {
+    v &= 0x1fffffULL;
+    v = (v | (v << 32)) & 0x1f00000000ffffULL;
+    v = (v | (v << 16)) & 0x1f0000ff0000ffULL;
+    v = (v | (v << 8)) & 0x100f00f00f00f00fULL;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ULL;
+    v = (v | (v << 2)) & 0x1249249249249249ULL;
+    return v;
+}
+
+// Bucket of a cell: its Morton code, whose low kBlockBits bits (a block of
+// 32^3 cells) are kept so that neighbouring cells land in neighbouring
+// buckets -- the scatter then stores spatial neighbours next to each other
+// -- while the block index above them is hashed with the system index.
+constexpr int kBlockBits = 15;
+
 __device__ __forceinline__ uint32_t bucket_of(int sys, uint64_t cell, uint32_t mask) {
-    return (uint32_t)mix64(cell ^ ((uint64_t)(sys + 1) * 0x9E3779B97F4A7C15ULL)) & mask;
+    const uint64_t m = 0x1fffffULL;
+    const uint64_t morton =
+        spread3(cell >> 42 & m) | (spread3(cell >> 21 & m) << 1) | (spread3(cell & m) << 2);
+    const uint64_t low = morton & ((1ULL << kBlockBits) - 1);
+    const uint64_t high = mix64((morton >> kBlockBits) ^ ((uint64_t)(sys + 1) * 0x9E3779B97F4A7C15ULL));
+    return (uint32_t)((high << kBlockBits) | low) & mask;
 }
 
 // Bin element i of system s at position x into the grid of edge h.
@@ -53,10 +75,11 @@ __device__ __forceinline__ void bin_element(const BatchDev& b, int s, int64_t i,
 }
 
 // Donor element radius at step k over its initial radius:
-// (f0 + rate min(k, cap)) / f0, cap < 0 meaning no cap.
+// (f0 + rate min(k, cap)) / f0 = 1 + (rate / f0) min(k, cap), cap < 0 meaning
+// no cap (one FP64 fused multiply-add; FP64 division is slow on this GPU).
 __device__ __forceinline__ double donor_scale(const SysConst& c, int64_t k) {
     const int64_t kk = (c.grow_cap >= 0 && k > c.grow_cap) ? c.grow_cap : k;
-    return (c.grow_f0 + c.grow_rate * (double)kk) / c.grow_f0;
+    return fma(c.grow_rel, (double)kk, 1.0);
 }
 
 // Edge of the contact grid's cells for the radii of step k: the largest

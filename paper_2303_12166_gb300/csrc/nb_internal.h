@@ -13,6 +13,9 @@
 //                                       reference point o, one array per
 //                                       component (the j-stream of the pair
 //                                       kernel)
+//   plo  3 x float                      (x-o) - pj: with pj a double-float
+//                                       copy of the position (contact term)
+//   v32  3 x float                      FP32 copy of the velocity
 //   sys_of int32                        owning system (-1 for padding)
 // Pair sums land in `part` (double4_32a per element and j-chunk); the contact
 // term in `cont` (double4_32a: a, e_rep).
@@ -35,6 +38,7 @@ struct SysConst {
     double dt, G, eps, beta;
     double origin[3];   // reference point of the FP32 copy pj
     double grow_f0, grow_rate;
+    double grow_rel;    // grow_rate / grow_f0
     int64_t grow_cap;   // < 0: no cap
     double rmax_donor0; // largest initial donor radius
     double rmax_acc;    // largest accretor radius
@@ -73,6 +77,12 @@ struct PosSoA {
     float* m;
 };
 
+struct Vec3SoA {
+    float* x;
+    float* y;
+    float* z;
+};
+
 // Device arrays of a batch (all pointers are device memory).
 struct BatchDev {
     int64_t ntot;          // total padded elements
@@ -82,6 +92,8 @@ struct BatchDev {
     double4_32a* A;
     double2* E;
     PosSoA pj;             // each ntot + NB_PAD (slack)
+    Vec3SoA plo;           // each ntot
+    Vec3SoA v32;           // each ntot
     int32_t* sys_of;
     double4_32a* part;         // NB chunks * ntot
     int32_t nchunk_alloc;  // chunks allocated in part
@@ -99,6 +111,8 @@ struct BatchDev {
     uint32_t* sorted;      // ntot: element indices, bucket by bucket
     uint64_t* scell;       // ntot: cell id of sorted[slot]
     float4* spos;          // ntot: FP32 position and current radius of sorted[slot]
+    float4* slo;           // ntot: low FP32 parts of the position, gamma
+    float4* svel;          // ntot: FP32 velocity, owning system (int bits)
     // diagnostics scratch
     double* red;           // per-block partial sums
     double* diag_out;      // final diagnostic values

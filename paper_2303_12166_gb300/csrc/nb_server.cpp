@@ -1,0 +1,322 @@
+// nb_server.cpp -- serving parameter-sweep runs by continuous batching.
+//
+// One host thread owns a Batch of fixed-size slots (as many as the device
+// memory budget allows).  Requests (a system description, parameters and a
+// step count) queue in arrival order; whenever slots are free the thread
+// admits queued requests -- builds their initial state, loads it into free
+// slots and evaluates their initial acceleration -- and then advances every
+// active system together by a chunk of steps: one persistent pair-kernel
+// launch, one contact pass and one update per step for all of them, replayed
+// from a CUDA graph while the set of active systems is unchanged.  The chunk
+// ends at the next completion, so a finished run is retired (its final
+// diagnostics recorded, its slot freed) without waiting for the others, and
+// requests that arrived meanwhile are admitted at once.  State stays on the
+// device for the whole run.
+//
+// A system's trajectory does not depend on what else shares the batch or on
+// how its steps are chunked (see nb_batch.cpp), so each result equals the
+// result of running the same request alone.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+
+#include "nb_batch.h"
+
+using nb::Batch;
+using nb::set_error;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    uint64_t ticket = 0;
+    nb_desc desc{};
+    nb_params params{};
+    std::vector<double> xv, mrg;  // copies of the optional caller arrays
+    int64_t nsteps = 0;
+    double t_submit = 0;
+};
+
+struct Active {
+    Request req;
+    int64_t done = 0;
+    double t_start = 0;
+};
+
+// Device bytes one element occupies in a slot (arrays of nb_internal.h with
+// `chunks` partial sums, the FP32 copy, the grid arrays at two buckets per
+// element), used to size the slots from the budget.
+size_t bytes_per_element(int chunks) {
+    return 4 * 32      // X, V, A, contact
+           + 16        // E
+           + 16        // FP32 copy
+           + 4 + 4 + 8 // owner, key, cell id
+           + 4 + 8 + 16  // sorted index, cell, position
+           + 2 * 12    // bucket counts, fills, starts
+           + (size_t)32 * chunks;
+}
+
+}  // namespace
+
+struct nb_server {
+    Batch batch;
+    int64_t slot_n = 0;
+    int nslots = 0;
+    int64_t tick_steps = 64;
+    Clock::time_point t0;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<Request> queue;
+    std::map<uint64_t, nb_result> done;
+    std::map<uint64_t, int> where;  // ticket -> 0 queued, 1 running
+    std::vector<int> slot_used;     // 0 free
+    std::vector<Active> active;     // per slot
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    nb_status fatal = NB_OK;
+    std::string fatal_msg;
+    std::thread worker;
+
+    double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+    void run();
+};
+
+void nb_server::run() {
+    for (;;) {
+        // ---- admit
+        std::vector<std::pair<int, Request>> admit;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            bool any_active = std::any_of(slot_used.begin(), slot_used.end(),
+                                          [](int u) { return u != 0; });
+            if (!any_active && queue.empty() && !stop)
+                cv.wait_for(lk, std::chrono::milliseconds(50));
+            if (stop) return;
+            for (int s = 0; s < nslots && !queue.empty(); ++s) {
+                if (slot_used[s]) continue;
+                Request r = std::move(queue.front());
+                queue.pop_front();
+                slot_used[s] = 1;
+                where[r.ticket] = 1;
+                admit.emplace_back(s, std::move(r));
+            }
+        }
+        std::vector<int> loaded;
+        for (auto& [s, r] : admit) {
+            nb::SystemInit si;
+            nb_desc d = r.desc;
+            d.xv_in = r.xv.empty() ? nullptr : r.xv.data();
+            d.mrg_in = r.mrg.empty() ? nullptr : r.mrg.data();
+            nb_status st = nb::build_system(d, r.params, si);
+            if (st == NB_OK && si.n > slot_n)
+                st = set_error(NB_EBUDGET, "request of %lld elements exceeds the slot size %lld",
+                               (long long)si.n, (long long)slot_n);
+            if (st == NB_OK && r.params.force_prec != batch.prec())
+                st = set_error(NB_EINVAL, "the server runs force_prec %d", batch.prec());
+            if (st == NB_OK) st = batch.load(s, si, true);
+            std::lock_guard<std::mutex> lk(mu);
+            if (st != NB_OK) {
+                nb_result res{};
+                res.status = st;
+                res.t_submit = r.t_submit;
+                res.t_start = res.t_finish = now();
+                done[r.ticket] = res;
+                where.erase(r.ticket);
+                slot_used[s] = 0;
+                continue;
+            }
+            active[s].req = std::move(r);
+            active[s].done = 0;
+            active[s].t_start = now();
+            loaded.push_back(s);
+        }
+        if (!loaded.empty()) {
+            // initial accelerations of the newcomers only
+            nb_status st = batch.init_acc_subset(loaded);
+            if (st != NB_OK) {
+                std::lock_guard<std::mutex> lk(mu);
+                fatal = st;
+                fatal_msg = nb::last_error();
+                return;
+            }
+        }
+        // ---- step every active system to the next completion (or a tick)
+        int64_t chunk = tick_steps;
+        bool any = false;
+        for (int s = 0; s < nslots; ++s)
+            if (slot_used[s] && batch.active(s)) {
+                any = true;
+                chunk = std::min(chunk, active[s].req.nsteps - active[s].done);
+            }
+        if (!any) continue;
+        nb_status st = chunk > 0 ? batch.step(chunk) : NB_OK;
+        std::vector<nb::SysMut> flags;
+        if (st == NB_OK) st = batch.read_flags(flags);
+        if (st != NB_OK) {
+            std::lock_guard<std::mutex> lk(mu);
+            fatal = st;
+            fatal_msg = nb::last_error();
+            return;
+        }
+        // ---- retire finished (or failed) runs
+        for (int s = 0; s < nslots; ++s) {
+            if (!slot_used[s] || !batch.active(s)) continue;
+            Active& a = active[s];
+            a.done += chunk;
+            nb_status rs = NB_OK;
+            if (flags[s].timeout) rs = NB_ETIMEOUT;
+            else if (flags[s].nonfinite) rs = NB_ENONFINITE;
+            if (a.done < a.req.nsteps && rs == NB_OK) continue;
+            nb_result res{};
+            res.status = rs;
+            res.n = batch.n_of(s);
+            res.steps = a.done;
+            res.t_submit = a.req.t_submit;
+            res.t_start = a.t_start;
+            nb_status ds = batch.diagnostics(s, &res.diag, false);
+            if (ds != NB_OK && res.status == NB_OK) res.status = ds;
+            batch.unload(s);
+            std::lock_guard<std::mutex> lk(mu);
+            res.t_finish = now();
+            done[a.req.ticket] = res;
+            where.erase(a.req.ticket);
+            slot_used[s] = 0;
+            cv.notify_all();
+        }
+    }
+}
+
+extern "C" {
+
+nb_status nb_server_create(size_t hbm_budget_bytes, int32_t max_slots, int64_t max_n, int32_t prec,
+                           void* stream, nb_server_t* out) {
+    try {
+        if (!out || max_slots < 1 || max_n < 1 || (prec != 32 && prec != 64))
+            return set_error(NB_EINVAL,
+                             "nb_server_create: need max_slots >= 1, max_n >= 1, prec 32 or 64");
+        *out = nullptr;
+        const int64_t npad = (max_n + nb::NB_PAD - 1) / nb::NB_PAD * nb::NB_PAD;
+        const size_t per_slot = bytes_per_element(4) * (size_t)npad;
+        const int64_t fit = (int64_t)(hbm_budget_bytes / std::max<size_t>(per_slot, 1));
+        const int nslots = (int)std::min<int64_t>(max_slots, fit);
+        if (nslots < 1)
+            return set_error(NB_EBUDGET,
+                             "nb_server_create: one slot of %lld elements needs ~%zu bytes, over "
+                             "the budget of %zu",
+                             (long long)max_n, per_slot, hbm_budget_bytes);
+        nb_server* srv = new nb_server();
+        srv->slot_n = npad;
+        srv->nslots = nslots;
+        srv->t0 = Clock::now();
+        srv->slot_used.assign(nslots, 0);
+        srv->active.assign(nslots, Active{});
+        srv->batch.set_use_graph(true);
+        nb_status st = srv->batch.init(std::vector<int64_t>(nslots, npad), prec,
+                                       static_cast<cudaStream_t>(stream));
+        if (st != NB_OK) {
+            delete srv;
+            return st;
+        }
+        srv->worker = std::thread([srv] { srv->run(); });
+        *out = srv;
+        return NB_OK;
+    } catch (const std::exception& e) {
+        return set_error(NB_EINVAL, "nb_server_create: %s", e.what());
+    }
+}
+
+nb_status nb_server_info(nb_server_t srv, int32_t* nslots, int64_t* slot_n, int64_t* device_bytes) {
+    if (!srv) return set_error(NB_EINVAL, "null server");
+    if (nslots) *nslots = srv->nslots;
+    if (slot_n) *slot_n = srv->slot_n;
+    if (device_bytes) *device_bytes = srv->batch.device_bytes();
+    return NB_OK;
+}
+
+nb_status nb_submit(nb_server_t srv, const nb_desc* desc, const nb_params* params, int64_t nsteps,
+                    uint64_t* ticket) {
+    if (!srv || !desc || !params || !ticket || nsteps < 0)
+        return set_error(NB_EINVAL, "nb_submit: null argument or negative step count");
+    try {
+        nb_status st = nb::check_params(*params);
+        if (st != NB_OK) return st;
+        Request r;
+        r.desc = *desc;
+        r.params = *params;
+        r.nsteps = nsteps;
+        const int64_t n = desc->n_donor + desc->n_accretor;
+        if (n < 1 || n > srv->slot_n)
+            return set_error(NB_EBUDGET, "nb_submit: %lld elements do not fit a slot of %lld",
+                             (long long)n, (long long)srv->slot_n);
+        if (desc->xv_in) r.xv.assign(desc->xv_in, desc->xv_in + 6 * n);
+        if (desc->mrg_in) r.mrg.assign(desc->mrg_in, desc->mrg_in + 3 * n);
+        r.desc.xv_in = nullptr;
+        r.desc.mrg_in = nullptr;
+        std::lock_guard<std::mutex> lk(srv->mu);
+        if (srv->fatal != NB_OK)
+            return set_error(srv->fatal, "server stopped: %s", srv->fatal_msg.c_str());
+        r.ticket = srv->next_ticket++;
+        r.t_submit = srv->now();
+        *ticket = r.ticket;
+        srv->where[r.ticket] = 0;
+        srv->queue.push_back(std::move(r));
+        srv->cv.notify_all();
+        return NB_OK;
+    } catch (const std::exception& e) {
+        return set_error(NB_EINVAL, "nb_submit: %s", e.what());
+    }
+}
+
+nb_status nb_poll(nb_server_t srv, uint64_t ticket, nb_result* out) {
+    if (!srv || !out) return set_error(NB_EINVAL, "nb_poll: null argument");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->done.find(ticket);
+    if (it != srv->done.end()) {
+        *out = it->second;
+        return NB_OK;
+    }
+    if (srv->where.count(ticket)) {
+        if (srv->fatal != NB_OK)
+            return set_error(srv->fatal, "server stopped: %s", srv->fatal_msg.c_str());
+        return NB_PENDING;
+    }
+    return set_error(NB_ENOTFOUND, "nb_poll: unknown ticket %llu", (unsigned long long)ticket);
+}
+
+nb_status nb_server_drain(nb_server_t srv, double timeout_s) {
+    if (!srv) return set_error(NB_EINVAL, "null server");
+    std::unique_lock<std::mutex> lk(srv->mu);
+    const auto deadline = Clock::now() + std::chrono::duration<double>(timeout_s);
+    while (!srv->where.empty() && srv->fatal == NB_OK) {
+        if (srv->cv.wait_until(lk, deadline) == std::cv_status::timeout && Clock::now() >= deadline)
+            return set_error(NB_ETIMEOUT, "nb_server_drain: %zu requests still open",
+                             srv->where.size());
+    }
+    if (srv->fatal != NB_OK) return set_error(srv->fatal, "server stopped: %s", srv->fatal_msg.c_str());
+    return NB_OK;
+}
+
+double nb_server_clock(nb_server_t srv) { return srv ? srv->now() : 0.0; }
+
+void nb_server_destroy(nb_server_t srv) {
+    if (!srv) return;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->stop = true;
+        srv->cv.notify_all();
+    }
+    if (srv->worker.joinable()) srv->worker.join();
+    try {
+        delete srv;
+    } catch (...) {
+    }
+}
+
+}  // extern "C"

@@ -43,12 +43,25 @@ __device__ __forceinline__ double3 total_acc(const BatchDev& b, const SysConst& 
     return make_double3(ax, ay, az);
 }
 
+// FP32 copies of element i: position relative to the reference point as a
+// double-float (hi in pj, lo in plo), G m, and the velocity.
 __device__ __forceinline__ void write_shadow(const BatchDev& b, const SysConst& c, int64_t i,
                                              const double4_32a& x) {
-    b.pj.x[i] = (float)(x.x - c.origin[0]);
-    b.pj.y[i] = (float)(x.y - c.origin[1]);
-    b.pj.z[i] = (float)(x.z - c.origin[2]);
+    const double rx = x.x - c.origin[0], ry = x.y - c.origin[1], rz = x.z - c.origin[2];
+    const float hx = (float)rx, hy = (float)ry, hz = (float)rz;
+    b.pj.x[i] = hx;
+    b.pj.y[i] = hy;
+    b.pj.z[i] = hz;
     b.pj.m[i] = (float)(c.G * x.w);
+    b.plo.x[i] = (float)(rx - (double)hx);
+    b.plo.y[i] = (float)(ry - (double)hy);
+    b.plo.z[i] = (float)(rz - (double)hz);
+}
+
+__device__ __forceinline__ void write_vel32(const BatchDev& b, int64_t i, const double4_32a& v) {
+    b.v32.x[i] = (float)v.x;
+    b.v32.y[i] = (float)v.y;
+    b.v32.z[i] = (float)v.z;
 }
 
 template <int MODE, bool KEYS>
@@ -83,6 +96,7 @@ __global__ void kick_kernel(BatchDev b, int only) {
         if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z)))
             atomicAdd(&b.sm[s].nonfinite, 1ull);
         b.V[i] = v;
+        write_vel32(b, i, v);
         return;
     }
     if (MODE == KICK_FINISH_START) {
@@ -99,6 +113,7 @@ __global__ void kick_kernel(BatchDev b, int only) {
     b.X[i] = x;
     b.V[i] = v;
     write_shadow(b, c, i, x);
+    write_vel32(b, i, v);
     if (KEYS) {
         const double h = cell_edge(c, b.sm[s].k + 1);
         if (c.contacts && h > 0.0) bin_element(b, s, i, x.x, x.y, x.z, h);
@@ -119,6 +134,7 @@ __global__ void shadow_kernel(BatchDev b) {
     const SysConst& c = b.sc[s];
     if (!c.active) return;
     write_shadow(b, c, i, b.X[i]);
+    write_vel32(b, i, b.V[i]);
 }
 
 __global__ void sum_forces_kernel(BatchDev b, int s, double* __restrict__ out) {

@@ -72,6 +72,11 @@ class nb_pair_cfg(ctypes.Structure):
                 ("min_blocks", _I32), ("nr_slots", _I32), ("reserved", _I32), ("ms", _D)]
 
 
+class nb_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("reserved", _I32), ("n", _I64), ("steps", _I64),
+                ("t_submit", _D), ("t_start", _D), ("t_finish", _D), ("diag", nb_diag)]
+
+
 class nb_info(ctypes.Structure):
     _fields_ = [("n", _I64), ("n_donor", _I64), ("n_accretor", _I64), ("m_donor", _D),
                 ("m_accretor", _D), ("r_donor0", _D), ("r_accretor", _D),
@@ -106,6 +111,28 @@ _sig("nb_set_state", ctypes.c_int, [_P, _P, _P, ctypes.POINTER(nb_ckpt_meta)])
 _sig("nb_profile", ctypes.c_int, [_P, ctypes.c_int])
 _sig("nb_autotune", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(nb_pair_cfg)])
 _sig("nb_pair_forces_noalloc", ctypes.c_int, [_P, _I64, _D, _D, _P, _P])
+_sig("nb_batch_create", ctypes.c_int,
+     [ctypes.POINTER(nb_desc), ctypes.POINTER(nb_params), _I32, _P, ctypes.POINTER(_P)])
+_sig("nb_batch_destroy", None, [_P])
+_sig("nb_batch_info", ctypes.c_int, [_P, _I32, ctypes.POINTER(nb_info)])
+_sig("nb_batch_step", ctypes.c_int, [_P, _I64])
+_sig("nb_batch_sync", ctypes.c_int, [_P])
+_sig("nb_batch_forces", ctypes.c_int, [_P, _I32, _P, ctypes.c_int])
+_sig("nb_batch_diagnostics", ctypes.c_int, [_P, _I32, ctypes.POINTER(nb_diag)])
+_sig("nb_batch_get_state", ctypes.c_int, [_P, _I32, _P, _P, ctypes.POINTER(nb_ckpt_meta)])
+_sig("nb_batch_set_pair_cfg", ctypes.c_int, [_P, ctypes.POINTER(nb_pair_cfg)])
+_sig("nb_batch_autotune", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(nb_pair_cfg)])
+_sig("nb_batch_profile", ctypes.c_int, [_P, ctypes.c_int])
+_sig("nb_batch_profile_read", ctypes.c_int, [_P, ctypes.POINTER(nb_prof), ctypes.c_int])
+_sig("nb_server_create", ctypes.c_int, [ctypes.c_size_t, _I32, _I64, _I32, _P, ctypes.POINTER(_P)])
+_sig("nb_server_info", ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64),
+                                      ctypes.POINTER(_I64)])
+_sig("nb_submit", ctypes.c_int, [_P, ctypes.POINTER(nb_desc), ctypes.POINTER(nb_params), _I64,
+                                 ctypes.POINTER(_U64)])
+_sig("nb_poll", ctypes.c_int, [_P, _U64, ctypes.POINTER(nb_result)])
+_sig("nb_server_drain", ctypes.c_int, [_P, _D])
+_sig("nb_server_clock", _D, [_P])
+_sig("nb_server_destroy", None, [_P])
 _sig("nb_set_pair_cfg", ctypes.c_int, [_P, ctypes.POINTER(nb_pair_cfg)])
 _sig("nb_get_pair_cfg", ctypes.c_int, [_P, ctypes.POINTER(nb_pair_cfg)])
 _sig("nb_profile_read", ctypes.c_int, [_P, ctypes.POINTER(nb_prof), ctypes.c_int])
@@ -307,6 +334,199 @@ def nb_profile_read(h, reset: bool = False) -> dict:
     p = nb_prof()
     _check(_lib.nb_profile_read(_P(h), ctypes.byref(p), 1 if reset else 0), "nb_profile_read")
     return {name: getattr(p, name) for name, _ in nb_prof._fields_}
+
+
+# ------------------------------------------------------------------ batches
+def nb_batch_create(descs, params, stream=None):
+    """descs/params: sequences of nb_desc / nb_params (same length)."""
+    n = len(descs)
+    if n != len(params) or n < 1:
+        raise ValueError("need as many params as descs, at least one")
+    da = (nb_desc * n)(*descs)
+    pa = (nb_params * n)(*params)
+    h = _P()
+    _check(_lib.nb_batch_create(da, pa, n, _P(_stream_ptr(stream)), ctypes.byref(h)),
+           "nb_batch_create")
+    return h.value
+
+
+def nb_batch_destroy(h) -> None:
+    _lib.nb_batch_destroy(_P(h))
+
+
+def nb_batch_info(h, sys: int) -> nb_info:
+    info = nb_info()
+    _check(_lib.nb_batch_info(_P(h), int(sys), ctypes.byref(info)), "nb_batch_info")
+    return info
+
+
+def nb_batch_step(h, nsteps: int) -> None:
+    _check(_lib.nb_batch_step(_P(h), int(nsteps)), "nb_batch_step")
+
+
+def nb_batch_sync(h) -> None:
+    _check(_lib.nb_batch_sync(_P(h)), "nb_batch_sync")
+
+
+def nb_batch_forces(h, sys: int):
+    n = nb_batch_info(h, sys).n
+    a = np.empty((n, 3), dtype=np.float64)
+    _check(_lib.nb_batch_forces(_P(h), int(sys), a.ctypes.data_as(_P), 0), "nb_batch_forces")
+    return a
+
+
+def nb_batch_diagnostics(h, sys: int) -> dict:
+    d = nb_diag()
+    _check(_lib.nb_batch_diagnostics(_P(h), int(sys), ctypes.byref(d)), "nb_batch_diagnostics")
+    return _diag_dict(d)
+
+
+def nb_batch_get_state(h, sys: int, with_acc: bool = True):
+    n = nb_batch_info(h, sys).n
+    xv = np.empty((n, 6), dtype=np.float64)
+    a = np.empty((n, 3), dtype=np.float64) if with_acc else None
+    meta = nb_ckpt_meta()
+    _check(_lib.nb_batch_get_state(_P(h), int(sys), xv.ctypes.data_as(_P),
+                                   a.ctypes.data_as(_P) if a is not None else None,
+                                   ctypes.byref(meta)), "nb_batch_get_state")
+    return xv, a, meta
+
+
+def nb_batch_set_pair_cfg(h, tile, i_per_thread, threads, min_blocks, nr_slots=0) -> None:
+    c = nb_pair_cfg(tile, i_per_thread, threads, min_blocks, nr_slots, 0, 0.0)
+    _check(_lib.nb_batch_set_pair_cfg(_P(h), ctypes.byref(c)), "nb_batch_set_pair_cfg")
+
+
+def nb_batch_autotune(h, reps: int = 2) -> dict:
+    c = nb_pair_cfg()
+    _check(_lib.nb_batch_autotune(_P(h), int(reps), ctypes.byref(c)), "nb_batch_autotune")
+    return _cfg_dict(c)
+
+
+def nb_batch_profile(h, enable: bool) -> None:
+    _check(_lib.nb_batch_profile(_P(h), 1 if enable else 0), "nb_batch_profile")
+
+
+def nb_batch_profile_read(h, reset: bool = False) -> dict:
+    p = nb_prof()
+    _check(_lib.nb_batch_profile_read(_P(h), ctypes.byref(p), 1 if reset else 0),
+           "nb_batch_profile_read")
+    return {name: getattr(p, name) for name, _ in nb_prof._fields_}
+
+
+class Batch:
+    """Owning wrapper of an nb_batch_t handle."""
+
+    def __init__(self, descs, params, stream=None):
+        self.h = nb_batch_create(descs, params, stream)
+        self.nsys = len(descs)
+
+    def info(self, s):
+        return nb_batch_info(self.h, s)
+
+    def step(self, nsteps):
+        nb_batch_step(self.h, nsteps)
+
+    def sync(self):
+        nb_batch_sync(self.h)
+
+    def forces(self, s):
+        return nb_batch_forces(self.h, s)
+
+    def diagnostics(self, s):
+        return nb_batch_diagnostics(self.h, s)
+
+    def get_state(self, s, with_acc=True):
+        return nb_batch_get_state(self.h, s, with_acc)
+
+    def set_pair_cfg(self, *cfg):
+        nb_batch_set_pair_cfg(self.h, *cfg)
+
+    def autotune(self, reps=2):
+        return nb_batch_autotune(self.h, reps)
+
+    def profile(self, enable=True):
+        nb_batch_profile(self.h, enable)
+
+    def profile_read(self, reset=False):
+        return nb_batch_profile_read(self.h, reset)
+
+    def close(self):
+        if self.h:
+            nb_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ serving
+def nb_server_create(hbm_budget_bytes: int, max_slots: int, max_n: int, prec: int = 32,
+                     stream=None):
+    h = _P()
+    _check(_lib.nb_server_create(int(hbm_budget_bytes), int(max_slots), int(max_n), int(prec),
+                                 _P(_stream_ptr(stream)), ctypes.byref(h)), "nb_server_create")
+    return h.value
+
+
+def nb_server_info(h) -> dict:
+    ns, sn, db = _I32(), _I64(), _I64()
+    _check(_lib.nb_server_info(_P(h), ctypes.byref(ns), ctypes.byref(sn), ctypes.byref(db)),
+           "nb_server_info")
+    return {"nslots": ns.value, "slot_n": sn.value, "device_bytes": db.value}
+
+
+def nb_submit(h, desc: nb_desc, params: nb_params, nsteps: int, xv_in=None, mrg_in=None) -> int:
+    keep = []
+    if xv_in is not None:
+        a = np.ascontiguousarray(xv_in, dtype=np.float64).reshape(-1)
+        keep.append(a)
+        desc.xv_in = _dptr(a)
+    if mrg_in is not None:
+        a = np.ascontiguousarray(mrg_in, dtype=np.float64).reshape(-1)
+        keep.append(a)
+        desc.mrg_in = _dptr(a)
+    t = _U64()
+    try:
+        _check(_lib.nb_submit(_P(h), ctypes.byref(desc), ctypes.byref(params), int(nsteps),
+                              ctypes.byref(t)), "nb_submit")
+    finally:
+        desc.xv_in = None
+        desc.mrg_in = None
+    return t.value
+
+
+def nb_poll(h, ticket: int):
+    """Returns a dict when the run has finished, None while it is pending."""
+    r = nb_result()
+    st = _lib.nb_poll(_P(h), _U64(int(ticket)), ctypes.byref(r))
+    if st == NB_PENDING:
+        return None
+    _check(st, "nb_poll")
+    out = {name: getattr(r, name) for name, _ in nb_result._fields_ if name != "diag"}
+    out["diag"] = _diag_dict(r.diag)
+    return out
+
+
+def nb_server_drain(h, timeout_s: float) -> None:
+    _check(_lib.nb_server_drain(_P(h), float(timeout_s)), "nb_server_drain")
+
+
+def nb_server_clock(h) -> float:
+    return float(_lib.nb_server_clock(_P(h)))
+
+
+def nb_server_destroy(h) -> None:
+    _lib.nb_server_destroy(_P(h))
 
 
 class System:

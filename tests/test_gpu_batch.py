@@ -1,0 +1,159 @@
+"""Batched and served forms through the C ABI.
+
+* A system advanced inside a batch (one kernel launch per phase for all
+  systems) gives bitwise the state it gives alone.
+* A batch's forces match the FP64 oracle per system.
+* The server (continuous batching) returns, for every run, the result of
+  running it alone; its admission respects the device-memory budget.
+"""
+import numpy as np
+import pytest
+
+from nbtest import oracle_ic, rms_rel
+
+pytestmark = pytest.mark.gpu
+
+SYSTEMS = [
+    dict(desc=dict(n_donor=512, n_accretor=512, q=0.5, f_donor=0.8, f_accretor=0.5,
+                   sigma_v=1e-3, seed=1),
+         params=dict(eps=0.01, dt=1e-3, beta=0.5)),
+    dict(desc=dict(n_donor=1900, n_accretor=600, q=0.3, f_donor=0.9, f_accretor=0.5,
+                   expand_rate=2e-3, expand_steps=-1, sigma_v=1e-3, seed=2),
+         params=dict(eps=0.005, dt=5e-4, beta=0.3)),
+    dict(desc=dict(n_donor=350, n_accretor=350, q=0.9, f_donor=0.7, f_accretor=0.6,
+                   sigma_v=2e-3, seed=3),
+         params=dict(eps=0.008, dt=8e-4, beta=0.7)),
+]
+
+
+@pytest.fixture(scope="module")
+def nbm():
+    from paper_2303_12166_gb300 import build
+    build.build()
+    from paper_2303_12166_gb300 import nbody
+    return nbody
+
+
+def _descs(nbm, systems):
+    return ([nbm.nb_desc_default(**s["desc"]) for s in systems],
+            [nbm.nb_params_default(**s["params"]) for s in systems])
+
+
+def _alone(nbm, s, nsteps, stream=None):
+    with nbm.System(nbm.nb_desc_default(**s["desc"]), nbm.nb_params_default(**s["params"]),
+                    stream=stream) as sysm:
+        sysm.step(nsteps)
+        sysm.sync()
+        xv, a, meta = sysm.get_state()
+        d = sysm.diagnostics()
+    return xv, a, meta, d
+
+
+def test_batch_alone_vs_mix_bitwise(nbm):
+    import torch
+    descs, params = _descs(nbm, SYSTEMS)
+    stream = torch.cuda.Stream()
+    with nbm.Batch(descs, params, stream=stream) as b:
+        b.step(6)
+        b.step(6)
+        b.sync()
+        mixed = [b.get_state(s) for s in range(len(SYSTEMS))]
+    for s, sysdef in enumerate(SYSTEMS):
+        xv, a, meta, _ = _alone(nbm, sysdef, 12)
+        assert mixed[s][2].step == 12
+        assert np.array_equal(mixed[s][0], xv), f"system {s} positions/velocities differ"
+        assert np.array_equal(mixed[s][1], a), f"system {s} accelerations differ"
+
+
+def test_batch_forces_match_oracle(nbm, orc):
+    descs, params = _descs(nbm, SYSTEMS)
+    with nbm.Batch(descs, params) as b:
+        for s, sysdef in enumerate(SYSTEMS):
+            a = b.forces(s)
+            d = dict(sysdef["desc"])
+            d.setdefault("stream", 0)
+            p = dict(sysdef["params"], G=1.0, kappa_gamma=8.0, rl_coeff=0.69)
+            ox, ov, om, oR, og = oracle_ic(orc, d, p)
+            ref = orc.forces(ox, ov, om, oR, og, G=1.0, eps=p["eps"], beta=p["beta"])
+            assert rms_rel(a, ref) <= 1e-5
+
+
+def test_batch_diagnostics_per_system(nbm):
+    descs, params = _descs(nbm, SYSTEMS)
+    with nbm.Batch(descs, params) as b:
+        b.step(3)
+        for s, sysdef in enumerate(SYSTEMS):
+            d = b.diagnostics(s)
+            _, _, _, ref = _alone(nbm, sysdef, 3)
+            assert d["step"] == 3
+            for k in ("e_kin", "e_grav", "e_rep"):
+                assert d[k] == ref[k]
+            assert np.array_equal(d["p"], ref["p"]) and np.array_equal(d["l"], ref["l"])
+
+
+def _server_requests():
+    reqs = []
+    for k in range(6):
+        s = SYSTEMS[k % 3]
+        reqs.append((s, 5 + 4 * k))
+    return reqs
+
+
+def test_server_results_equal_alone(nbm):
+    import torch
+    stream = torch.cuda.Stream()
+    srv = nbm.nb_server_create(4 << 30, 3, 4096, 32, stream)
+    try:
+        info = nbm.nb_server_info(srv)
+        assert info["nslots"] == 3 and info["slot_n"] >= 4096
+        tickets = []
+        for s, nsteps in _server_requests():
+            d = nbm.nb_desc_default(**s["desc"])
+            p = nbm.nb_params_default(**s["params"])
+            tickets.append(nbm.nb_submit(srv, d, p, nsteps))
+        nbm.nb_server_drain(srv, 120.0)
+        results = [nbm.nb_poll(srv, t) for t in tickets]
+    finally:
+        nbm.nb_server_destroy(srv)
+    for (s, nsteps), r in zip(_server_requests(), results):
+        assert r["status"] == nbm.NB_OK
+        assert r["steps"] == nsteps
+        assert r["t_submit"] <= r["t_start"] <= r["t_finish"]
+        _, _, _, ref = _alone(nbm, s, nsteps)
+        d = r["diag"]
+        assert d["step"] == nsteps
+        assert d["e_kin"] == ref["e_kin"]
+        assert np.array_equal(d["p"], ref["p"]) and np.array_equal(d["l"], ref["l"])
+        assert np.array_equal(d["com"], ref["com"])
+        assert d["n_past_L1"] == ref["n_past_L1"]
+        assert np.isnan(d["e_grav"])
+
+
+def test_server_budget_and_errors(nbm):
+    # a budget that holds a single slot: runs are served one after another
+    one_slot = 4096 * 600
+    with pytest.raises(nbm.NbError) as ei:
+        nbm.nb_server_create(1000, 4, 4096, 32)
+    assert ei.value.status == nbm.NB_EBUDGET
+    srv = nbm.nb_server_create(one_slot, 4, 4096, 32)
+    try:
+        assert nbm.nb_server_info(srv)["nslots"] == 1
+        s = SYSTEMS[0]
+        t1 = nbm.nb_submit(srv, nbm.nb_desc_default(**s["desc"]),
+                           nbm.nb_params_default(**s["params"]), 8)
+        t2 = nbm.nb_submit(srv, nbm.nb_desc_default(**s["desc"]),
+                           nbm.nb_params_default(**s["params"]), 8)
+        with pytest.raises(nbm.NbError) as ei:
+            nbm.nb_submit(srv, nbm.nb_desc_default(n_donor=5000, n_accretor=5000),
+                          nbm.nb_params_default(), 1)
+        assert ei.value.status == nbm.NB_EBUDGET
+        with pytest.raises(nbm.NbError) as ei:
+            nbm.nb_poll(srv, 999999)
+        assert ei.value.status == nbm.NB_ENOTFOUND
+        nbm.nb_server_drain(srv, 60.0)
+        r1, r2 = nbm.nb_poll(srv, t1), nbm.nb_poll(srv, t2)
+        assert r1["status"] == r2["status"] == nbm.NB_OK
+        assert r2["t_start"] >= r1["t_finish"]
+        assert r1["diag"]["e_kin"] == r2["diag"]["e_kin"]
+    finally:
+        nbm.nb_server_destroy(srv)
