@@ -51,6 +51,26 @@ def _dist():
     return ws, rank, local
 
 
+def _pair_traffic(workload, cfg):
+    """DRAM bytes per launch of the pair kernel from the committed ncu capture,
+    if it was taken on this workload and launch shape with the current kernel
+    source; otherwise None."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "pair_f32_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        rec = json.load(f)
+    with open(os.path.join(ROOT, "paper_2303_12166_gb300", "csrc", "nb_pair.cu"), "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    key = ",".join(str(cfg[k]) for k in ("tile", "i_per_thread", "threads", "min_blocks",
+                                         "nr_slots"))
+    if rec.get("workload") != workload or rec.get("pair_cfg") != key or \
+            rec.get("kernel_source_sha256_16") != sha:
+        return None
+    return float(rec["dram_bytes_per_launch"])
+
+
 def _measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -298,6 +318,32 @@ def measure_batched(nbm, torch, dev, stream, args, ws, rank):
     return out
 
 
+def measure_fp64_path(nbm, torch, dev, stream, args):
+    """The FP64-force path (FP64 pair kernel) against the FP32 path on the
+    65,536-element binary: one force pass each, CUDA events."""
+    w = _workload("binary_64k")
+    out = {"workload": "binary_64k"}
+    for prec in (32, 64):
+        desc = nbm.nb_desc_default(n_donor=w["n_donor"], n_accretor=w["n_accretor"], q=w["q"],
+                                   f_donor=w["f_donor"], f_accretor=w["f_accretor"],
+                                   sigma_v=w["sigma_v"], seed=w["seed"])
+        params = nbm.nb_params_default(eps=w["eps"], dt=w["dt"], beta=0.5, force_prec=prec)
+        with nbm.System(desc, params, stream=stream) as sy:
+            if prec == 32:
+                sy.autotune(1)
+            sy.step(1)
+            sy.sync()
+            sy.profile(True)
+            sy.profile_read(reset=True)
+            sy.step(1)
+            sy.sync()
+            p = sy.profile_read(reset=True)
+        n = w["n_donor"] + w["n_accretor"]
+        out[f"fp{prec}_pair_pairs_per_s"] = float(n) * n / (p["pair_ms"] * 1e-3)
+    out["fp32_over_fp64"] = out["fp32_pair_pairs_per_s"] / out["fp64_pair_pairs_per_s"]
+    return out
+
+
 def measure_served(nbm, stream, args):
     """Poisson arrivals (20/s) of sweep runs: element count log-uniform in
     [4,096, 262,144], steps uniform in [1,000, 20,000] divided by
@@ -430,11 +476,12 @@ def run_ours(args):
 
     working_set = sysm.info.device_bytes
     sysm.close()
-    batched = served = None
+    batched = served = fp64_path = None
     if not args.no_extras:
         batched = measure_batched(nbm, torch, dev, stream, args, ws, rank)
         if rank == 0 and ws == 1:
             served = measure_served(nbm, stream, args)
+            fp64_path = measure_fp64_path(nbm, torch, dev, stream, args)
     if rank == 0:
         cfg = _config(args.workload, w, {
             "force_prec": 64 if args.fp64 else 32,
@@ -449,7 +496,8 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.fp64 else "f32", "data": "synthetic", "config": cfg,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_pairs,
-                         "unit": "pairs/s", "frac": achieved / peak_pairs, "traffic": None,
+                         "unit": "pairs/s", "frac": achieved / peak_pairs,
+                         "traffic": None if args.fp64 else _pair_traffic(args.workload, tuned),
                          "peak_basis": f"{props.multi_processor_count} SMs x {sm_max_mhz:.0f} MHz "
                                        f"({peak_src} sm_max_mhz) x {MUFU_PER_SM_CLK} MUFU/clk/SM / "
                                        f"{MUFU_PER_PAIR} MUFU per pair",
@@ -463,6 +511,7 @@ def run_ours(args):
             "clocks": clk.summary(),
             "batched": batched,
             "served": served,
+            "fp64_path": fp64_path,
         }
         print(json.dumps(line), flush=True)
     if dist:

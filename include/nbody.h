@@ -239,6 +239,12 @@ nb_status nb_autotune(nb_system_t sys, int reps, nb_pair_cfg* best);
 nb_status nb_set_pair_cfg(nb_system_t sys, const nb_pair_cfg* cfg);
 nb_status nb_get_pair_cfg(nb_system_t sys, nb_pair_cfg* cfg);
 
+/* Failure-detection self-test: a kernel waits on a device barrier that
+ * nothing completes, with the same bounded wait the pair kernel uses, and
+ * gives up after budget_clocks SM clocks.  Returns NB_ETIMEOUT (the expected
+ * outcome) after which the context stays usable; no fault, no hang. */
+nb_status nb_selftest_device_wait(int64_t budget_clocks, void* stream);
+
 /* Enable (1) or disable (0) per-phase event timing of subsequent calls;
  * while enabled, multi-step calls are not captured in CUDA graphs. */
 nb_status nb_profile(nb_system_t sys, int enable);

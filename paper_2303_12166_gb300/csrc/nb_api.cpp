@@ -219,6 +219,26 @@ nb_status nb_get_pair_cfg(nb_system_t sys, nb_pair_cfg* cfg) {
     return NB_OK;
 }
 
+nb_status nb_selftest_device_wait(int64_t budget_clocks, void* stream) {
+    return guarded([&]() -> nb_status {
+        if (budget_clocks < 0) return set_error(NB_EINVAL, "budget must be >= 0");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        unsigned int* flag = nullptr;
+        cudaError_t e = cudaMallocAsync((void**)&flag, sizeof(unsigned int), s);
+        if (e == cudaSuccess) e = nb::launch_wait_selftest(budget_clocks, flag, s);
+        unsigned int timed_out = 0;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&timed_out, flag, sizeof timed_out, cudaMemcpyDeviceToHost, s);
+        if (flag) cudaFreeAsync(flag, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess)
+            return set_error(NB_ECUDA, "nb_selftest_device_wait: %s", cudaGetErrorString(e));
+        if (timed_out) return set_error(NB_ETIMEOUT, "device wait gave up after %lld clocks",
+                                        (long long)budget_clocks);
+        return NB_OK;
+    });
+}
+
 nb_status nb_profile(nb_system_t sys, int enable) {
     if (!sys) return set_error(NB_EINVAL, "null system");
     return guarded([&] { return sys->batch.set_profile(enable != 0); });

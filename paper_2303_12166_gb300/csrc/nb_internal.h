@@ -144,6 +144,8 @@ constexpr int kF64Tile = 128;
 cudaError_t launch_pair_f64(const BatchDev& b, const PairItem* items, int nitems, int grid,
                             bool with_pot, int* counter, cudaStream_t s);
 int pair_f64_occupancy();
+// one thread waits (bounded by `budget` clocks) on a barrier nothing completes
+cudaError_t launch_wait_selftest(long long budget, unsigned int* timed_out, cudaStream_t s);
 
 // Update kernels.  With build_keys the drift kernel also bins the new
 // positions into the contact grid of step k+1 (b.cnt must be zeroed).

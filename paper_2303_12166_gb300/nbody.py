@@ -109,6 +109,7 @@ _sig("nb_diagnostics", ctypes.c_int, [_P, ctypes.POINTER(nb_diag)])
 _sig("nb_get_state", ctypes.c_int, [_P, _P, _P, ctypes.POINTER(nb_ckpt_meta)])
 _sig("nb_set_state", ctypes.c_int, [_P, _P, _P, ctypes.POINTER(nb_ckpt_meta)])
 _sig("nb_profile", ctypes.c_int, [_P, ctypes.c_int])
+_sig("nb_selftest_device_wait", ctypes.c_int, [_I64, _P])
 _sig("nb_autotune", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(nb_pair_cfg)])
 _sig("nb_pair_forces_noalloc", ctypes.c_int, [_P, _I64, _D, _D, _P, _P])
 _sig("nb_batch_create", ctypes.c_int,
@@ -324,6 +325,11 @@ def nb_pair_forces_noalloc(xyzm_ptr: int, n: int, G: float, eps: float, acc_ptr:
     _check(_lib.nb_pair_forces_noalloc(_P(xyzm_ptr), int(n), float(G), float(eps),
                                        _P(acc_ptr), _P(_stream_ptr(stream))),
            "nb_pair_forces_noalloc")
+
+
+def nb_selftest_device_wait(budget_clocks: int, stream=None) -> int:
+    """Returns the status (NB_ETIMEOUT expected); does not raise."""
+    return int(_lib.nb_selftest_device_wait(int(budget_clocks), _P(_stream_ptr(stream))))
 
 
 def nb_profile(h, enable: bool) -> None:

@@ -325,3 +325,14 @@ def test_graph_replay_equals_direct_launches(nbm):
     for a, b in zip(r_direct[:3], r_graph[:3]):
         assert np.array_equal(a, b)
     assert r_graph[3].step == 14
+
+
+def test_bounded_device_wait_times_out_cleanly(nbm, orc):
+    """A device wait on a barrier that nothing completes gives up after its
+    budget and reports NB_ETIMEOUT; the context stays usable."""
+    import time
+    t0 = time.perf_counter()
+    st = nbm.nb_selftest_device_wait(20_000_000)  # ~10 ms of SM clocks
+    assert st == nbm.NB_ETIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    test_forces_binary_1k(nbm, orc, 32, 1e-5)
