@@ -36,11 +36,34 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libnb_oracle.so")
 _lock = threading.Lock()
 _lib = None
+_LIB_OVERRIDE = None  # set on a separately loaded copy of this module (see load_variant)
+
+
+def load_variant(lib_path: str):
+    """A separate instance of this module bound to another compiled oracle
+    library (used by the tests that plant mistakes in copies of the oracle)."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(f"oracle_variant_{abs(hash(lib_path))}",
+                                                  os.path.abspath(__file__))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod._LIB_OVERRIDE = lib_path
+    return mod
 
 _D = ctypes.c_double
 _I64 = ctypes.c_int64
 _U64 = ctypes.c_uint64
 _P = ctypes.c_void_p
+
+
+def compile_source(src: str, lib_path: str) -> str:
+    """Compile a C file with the oracle's flags into a shared library."""
+    tmp = lib_path + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fno-fast-math", "-ffp-contract=off", "-fopenmp",
+           "-shared", "-fPIC", "-std=c99", "-D_DEFAULT_SOURCE", src, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 def build(force: bool = False) -> str:
@@ -49,12 +72,7 @@ def build(force: bool = False) -> str:
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-fno-fast-math", "-ffp-contract=off", "-fopenmp",
-           "-shared", "-fPIC", "-std=c99", "-D_DEFAULT_SOURCE", _SRC, "-o", tmp, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    return compile_source(_SRC, _LIB_PATH)
 
 
 def _load():
@@ -62,7 +80,7 @@ def _load():
     with _lock:
         if _lib is not None:
             return _lib
-        lib = ctypes.CDLL(build())
+        lib = ctypes.CDLL(build() if _LIB_OVERRIDE is None else _LIB_OVERRIDE)
         lib.orc_roche_rL.restype = _D
         lib.orc_roche_rL.argtypes = [_D, _D]
         lib.orc_roche_phi.restype = _D
