@@ -71,9 +71,10 @@ typedef struct nb_params {
 } nb_params;
 
 /* One binary system.  Without xv_in the initial state follows this recipe:
- * total mass 1, separation sep, q = m_donor/m_accretor, accretor centre at
- * x = -sep q/(1+q), donor centre at x = +sep/(1+q), orbit about +z with
- * omega = sqrt(G/sep^3).  Each star is a uniform ball of radius
+ * total mass 1, separation sep (the semi-major axis; the run starts at
+ * periapsis, r_p = sep (1 - ecc)), q = m_donor/m_accretor, accretor centre
+ * at x = -r_p q/(1+q), donor centre at x = +r_p/(1+q), orbit about +z with
+ * omega = sqrt(G (1+ecc) / (sep^3 (1-ecc)^3)) (sqrt(G/sep^3) when circular).  Each star is a uniform ball of radius
  * f * r_L * sep (r_L from Eq. 3: r_L(q) for the donor, r_L(1/q) for the
  * accretor); element mass = star mass / count, element radius = star
  * radius * count^(-1/3).  Points are drawn uniformly in the ball (rejection
@@ -98,6 +99,10 @@ typedef struct nb_desc {
     const double* mrg_in;  /* optional host array, n x 3 (mass, radius,
                               gamma) per element; replaces the star-derived
                               values (growth still scales donor radii) */
+    double ecc;            /* orbital eccentricity, 0 <= ecc < 1: the run starts
+                              at periapsis, separation sep (1 - ecc), rigid
+                              rotation at the periapsis rate
+                              sqrt(G (1+ecc) / (sep^3 (1-ecc)^3)); 0: circular */
 } nb_desc;
 
 /* FP64 diagnostics of a system's state (computed on the GPU). */
@@ -121,6 +126,16 @@ typedef struct nb_diag {
                               plane through L1 (Eq. 2) normal to the axis */
     double m_past_L1;      /* their mass */
     int64_t n_nonfinite;   /* elements with a non-finite position/velocity */
+    int64_t n_in_accretor_lobe; /* donor elements inside the accretor's Roche
+                              lobe: past the L1 plane with phi >= phi(L1), phi
+                              the potential of Eq. 2 in the frame of the two
+                              star centres (separation as unit, z the orbital
+                              axis) */
+    double m_in_accretor_lobe;
+    int64_t n_unbound;     /* donor elements with positive energy in the field
+                              of the two stars as point masses at their centres:
+                              |v - v_cm|^2/2 - G M_a/|x - c_a| - G M_d/|x - c_d| > 0 */
+    double m_unbound;
 } nb_diag;
 
 /* Checkpoint metadata returned by nb_get_state and accepted by nb_set_state. */
@@ -160,9 +175,11 @@ typedef struct nb_pair_cfg {
     int32_t i_per_thread;  /* i-elements held in registers per thread */
     int32_t threads;       /* threads per block */
     int32_t min_blocks;    /* resident blocks per SM the registers are sized for */
-    int32_t nr_slots;      /* i-elements per thread whose reciprocal is computed
-                              by Newton-Raphson on the FP32 pipe instead of MUFU */
-    int32_t reserved;
+    int32_t nr_slots;      /* i-elements (i-element pairs when i_packed) per thread
+                              whose reciprocal is computed by Newton-Raphson on
+                              the FP32 pipe instead of MUFU */
+    int32_t i_packed;      /* 1: two i-elements per packed FP32x2 register (the
+                              j-stream duplicated); 0: two j-elements */
     double ms;             /* measured time of one pair pass (autotune), else 0 */
 } nb_pair_cfg;
 
@@ -185,6 +202,21 @@ double nb_roche_rL(double q, double coeff);
 /* Inner Lagrangian point of Eq. 2: distance from the star of mass m1 toward
  * the star of mass m2 = q m1, in units of the separation. */
 double nb_roche_L1(double q);
+
+/* Scenario presets after the three qualitative runs of the paper's results
+ * section (Fig. 5): parameter sets only, with n elements (3/4 in the
+ * donor); the physical outcome is not a parity claim.
+ *   NB_PRESET_COMPACT_ACCRETOR  main-sequence donor filling its lobe onto a
+ *                               compact (white-dwarf-like) accretor: small,
+ *                               stiff accretor elements, conservative transfer
+ *   NB_PRESET_TWO_MAIN_SEQUENCE two main-sequence stars of similar mass, both
+ *                               close to their lobes (non-conservative case B)
+ *   NB_PRESET_RED_GIANT         a rapidly expanding giant donor and a
+ *                               main-sequence accretor (Algol-like) */
+#define NB_PRESET_COMPACT_ACCRETOR 0
+#define NB_PRESET_TWO_MAIN_SEQUENCE 1
+#define NB_PRESET_RED_GIANT 2
+nb_status nb_preset(int32_t which, int64_t n, nb_desc* desc, nb_params* params);
 
 /* ---- single system ---------------------------------------------------- */
 

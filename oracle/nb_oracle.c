@@ -293,9 +293,12 @@ void orc_run(int64_t n, int64_t n_donor, double *x, double *v, const double *m,
 
 /* ------------------------------------------------------------------------ */
 /* Initial conditions: two uniform-density spheres of equal-mass elements.   */
-/* Units G = 1 is not assumed: G is a parameter.  Total mass 1, separation a,*/
-/* q = m_donor / m_accretor, accretor centre at x = -a q/(1+q), donor centre */
-/* at x = +a/(1+q), orbit about the z axis with omega = sqrt(G/a^3).         */
+/* Units G = 1 is not assumed: G is a parameter.  Total mass 1, semi-major   */
+/* axis a, eccentricity e, q = m_donor / m_accretor; the orbit starts at     */
+/* periapsis, separation r_p = a (1 - e): accretor centre at x = -r_p q/(1+q)*/
+/* donor centre at x = +r_p/(1+q), orbit about the z axis with the           */
+/* periapsis angular rate omega = sqrt(G (1+e) / (a^3 (1-e)^3)) (vis-viva;   */
+/* e = 0: the circular orbit, omega = sqrt(G/a^3)).                          */
 /* Element mass = star mass / element count; element radius = star radius *  */
 /* count^{-1/3} (equal volumes fill the star's volume exactly).              */
 /* Star radius: donor f_d r_L(q) a, accretor f_a r_L(1/q) a (Eq. 3).         */
@@ -313,7 +316,7 @@ void orc_run(int64_t n, int64_t n_donor, double *x, double *v, const double *m,
 /* ------------------------------------------------------------------------ */
 void orc_make_ic(int64_t n_d, int64_t n_a, double q, double sep, double f_d,
                  double f_a, double sigma_v, uint64_t seed, uint64_t stream,
-                 int no_spin, double G, double kappa, double rl_coeff,
+                 int no_spin, double G, double kappa, double rl_coeff, double ecc,
                  double *x, double *v, double *m, double *R, double *gam)
 {
     orc_rng g;
@@ -321,8 +324,9 @@ void orc_make_ic(int64_t n_d, int64_t n_a, double q, double sep, double f_d,
     double M_a = 1.0 / (1.0 + q), M_d = q / (1.0 + q);
     double Rs_d = f_d * orc_roche_rL(q, rl_coeff) * sep;
     double Rs_a = f_a * orc_roche_rL(1.0 / q, rl_coeff) * sep;
-    double cx_a = -sep * q / (1.0 + q), cx_d = sep / (1.0 + q);
-    double omega = sqrt(G * 1.0 / (sep * sep * sep));
+    double rp = sep * (1.0 - ecc);
+    double cx_a = -rp * q / (1.0 + q), cx_d = rp / (1.0 + q);
+    double omega = sqrt(G * 1.0 * (1.0 + ecc) / (sep * sep * sep * (1.0 - ecc) * (1.0 - ecc) * (1.0 - ecc)));
     double me_d = n_d > 0 ? M_d / (double)n_d : 0.0;
     double me_a = n_a > 0 ? M_a / (double)n_a : 0.0;
     double Re_d = n_d > 0 ? Rs_d / cbrt((double)n_d) : 0.0;

@@ -104,7 +104,7 @@ def _load():
                                 _I64, _I64, _D, _D, _I64, _P, _P, _P]
         lib.orc_make_ic.restype = None
         lib.orc_make_ic.argtypes = [_I64, _I64, _D, _D, _D, _D, _D, _U64, _U64,
-                                    ctypes.c_int, _D, _D, _D, _P, _P, _P, _P, _P]
+                                    ctypes.c_int, _D, _D, _D, _D, _P, _P, _P, _P, _P]
         lib.orc_splitmix_u01.restype = None
         lib.orc_splitmix_u01.argtypes = [_U64, _U64, _I64, _P]
         lib.orc_num_threads.restype = ctypes.c_int
@@ -240,8 +240,9 @@ def run(x, v, m, R0, gam, *, G=1.0, eps=0.0, beta=1.0, dt=1e-3, nsteps=1,
 # ---------------------------------------------------------------- initial conditions
 def make_ic(n_donor, n_accretor, q, *, sep=1.0, f_donor=0.8, f_accretor=0.5,
             sigma_v=1e-3, seed=0, stream=0, no_spin=False, G=1.0, kappa_gamma=8.0,
-            rl_coeff=0.69):
-    """Two uniform spheres of equal-mass elements on a circular orbit (see nb_oracle.c)."""
+            rl_coeff=0.69, ecc=0.0):
+    """Two uniform spheres of equal-mass elements starting at periapsis of an
+    orbit of semi-major axis ``sep`` and eccentricity ``ecc`` (see nb_oracle.c)."""
     n = int(n_donor) + int(n_accretor)
     x = np.zeros((n, 3))
     v = np.zeros((n, 3))
@@ -252,7 +253,8 @@ def make_ic(n_donor, n_accretor, q, *, sep=1.0, f_donor=0.8, f_accretor=0.5,
                         float(f_donor), float(f_accretor), float(sigma_v),
                         int(seed) & 0xFFFFFFFFFFFFFFFF, int(stream) & 0xFFFFFFFFFFFFFFFF,
                         1 if no_spin else 0, float(G), float(kappa_gamma),
-                        float(rl_coeff), _ptr(x), _ptr(v), _ptr(m), _ptr(R), _ptr(gam))
+                        float(rl_coeff), float(ecc), _ptr(x), _ptr(v), _ptr(m), _ptr(R),
+                        _ptr(gam))
     return x, v, m, R, gam
 
 
@@ -270,9 +272,19 @@ def diagnostics(x, v, m, R, gam, *, G=1.0, eps=0.0, n_donor=0, q=None, rl_L1=Non
     E_kin = 1/2 sum m v^2; E_grav = -sum_{i<j} G m_i m_j/(r+eps) (Eq. 4's
     potential); E_rep = sum_{contacts} gamma_ij U(r; R_ij) (potential of the
     Eq. 5 repulsion); P = sum m v; L = sum m x cross v; centres of mass of the
-    whole system and of each star's original elements.  With ``q`` given,
-    ``n_past_L1``/``m_past_L1`` count donor elements on the accretor's side of
-    the plane through L1 (Eq. 2) normal to the line between the star centres.
+    whole system and of each star's original elements.  With ``q`` given
+    (donor mass / accretor mass), for the donor's elements:
+
+    * ``n_past_L1``/``m_past_L1``: on the accretor's side of the plane through
+      L1 (Eq. 2) normal to the line between the star centres;
+    * ``n_in_acc_lobe``/``m_in_acc_lobe``: inside the accretor's Roche lobe,
+      i.e. on that side of the plane with phi >= phi(L1), phi the normalised
+      potential of Eq. 2 in the frame with the accretor's centre at the
+      origin, the donor's at x = 1 (the current separation as unit), z along
+      the orbital axis +z;
+    * ``n_unbound``/``m_unbound``: with positive energy per unit mass in the
+      field of the two stars taken as point masses at their centres,
+      1/2 |v - v_cm|^2 - G M_a/|x - c_a| - G M_d/|x - c_d| > 0.
     """
     x = _f64(x, (-1, 3))
     n = x.shape[0]
@@ -303,4 +315,28 @@ def diagnostics(x, v, m, R, gam, *, G=1.0, eps=0.0, n_donor=0, q=None, rl_L1=Non
             past = proj < xl1 * sep
             out["n_past_L1"] = int(past.sum())
             out["m_past_L1"] = float(m[:nd][past].sum())
+            # Roche frame: x along the axis, z the orbital axis, y = z cross x
+            ex = d / sep
+            ez = np.array([0.0, 0.0, 1.0]) - ex[2] * ex
+            ez = ez / np.sqrt(ez @ ez)
+            ey = np.cross(ez, ex)
+            rel = (x[:nd] - ca) / sep
+            phi_c = roche_phi(q, xl1, 0.0, 0.0)
+            inlobe = np.zeros(nd, dtype=bool)
+            for k in range(nd):
+                xi, yi, zi = rel[k] @ ex, rel[k] @ ey, rel[k] @ ez
+                if xi < xl1:
+                    inlobe[k] = roche_phi(q, xi, yi, zi) >= phi_c
+            out["n_in_acc_lobe"] = int(inlobe.sum())
+            out["m_in_acc_lobe"] = float(m[:nd][inlobe].sum())
+            Ma, Md = m[nd:].sum(), m[:nd].sum()
+            vcm = (m[:, None] * v).sum(axis=0) / m.sum()
+            dv = v[:nd] - vcm
+            ra = np.linalg.norm(x[:nd] - ca, axis=1)
+            rd = np.linalg.norm(x[:nd] - cd, axis=1)
+            with np.errstate(divide="ignore"):  # an element at a centre is bound
+                e = 0.5 * np.sum(dv * dv, axis=1) - G * Ma / ra - G * Md / rd
+            unb = e > 0
+            out["n_unbound"] = int(unb.sum())
+            out["m_unbound"] = float(m[:nd][unb].sum())
     return out

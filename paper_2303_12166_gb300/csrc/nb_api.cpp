@@ -1,6 +1,7 @@
 // nb_api.cpp -- extern "C" entry points of include/nbody.h for single
 // systems.  Every entry point catches all C++ exceptions and returns a
 // status; nothing throws across the ABI.
+#include <cmath>
 #include <cstring>
 #include <exception>
 #include <map>
@@ -50,6 +51,7 @@ nb_pair_cfg to_abi(const nb::PairCfg& c, double ms) {
     o.threads = c.threads;
     o.min_blocks = c.minb;
     o.nr_slots = c.nr;
+    o.i_packed = c.ipk;
     o.ms = ms;
     return o;
 }
@@ -107,6 +109,51 @@ nb_status nb_desc_default(nb_desc* d) {
 }
 
 double nb_roche_rL(double q, double coeff) { return nb::model_roche_rL(q, coeff); }
+
+nb_status nb_preset(int32_t which, int64_t n, nb_desc* d, nb_params* p) {
+    if (!d || !p) return set_error(NB_EINVAL, "null argument");
+    if (n < 4) return set_error(NB_EINVAL, "a preset needs n >= 4");
+    nb_desc_default(d);
+    nb_params_default(p);
+    d->n_donor = (3 * n) / 4;
+    d->n_accretor = n - d->n_donor;
+    // element radius falls as n^(-1/3); the contact oscillation period with
+    // it (kappa fixed), so the step is scaled from its value at 16,384
+    const double dt_scale = std::pow(16384.0 / (double)n, 0.5);
+    switch (which) {
+        case NB_PRESET_COMPACT_ACCRETOR:
+            d->q = 0.6;
+            d->f_donor = 0.9;
+            d->f_accretor = 0.2;
+            d->expand_rate = 2.5e-5;
+            d->expand_steps = 16000;
+            p->eps = 0.005;
+            p->dt = 1e-4 * dt_scale;
+            p->beta = 0.4;
+            return NB_OK;
+        case NB_PRESET_TWO_MAIN_SEQUENCE:
+            d->q = 0.8;
+            d->f_donor = 0.95;
+            d->f_accretor = 0.9;
+            d->expand_rate = 2.0e-5;
+            d->expand_steps = 10000;
+            p->eps = 0.005;
+            p->dt = 2.5e-4 * dt_scale;
+            p->beta = 0.5;
+            return NB_OK;
+        case NB_PRESET_RED_GIANT:
+            d->q = 0.45;
+            d->f_donor = 1.0;
+            d->f_accretor = 0.45;
+            d->expand_rate = 6.0e-5;
+            d->expand_steps = 8000;
+            p->eps = 0.005;
+            p->dt = 2.5e-4 * dt_scale;
+            p->beta = 0.5;
+            return NB_OK;
+    }
+    return set_error(NB_EINVAL, "unknown preset %d", (int)which);
+}
 double nb_roche_L1(double q) { return nb::model_roche_L1(q); }
 
 nb_status nb_create_system(const nb_desc* desc, const nb_params* params, void* stream,
@@ -207,8 +254,8 @@ nb_status nb_autotune(nb_system_t sys, int reps, nb_pair_cfg* best) {
 nb_status nb_set_pair_cfg(nb_system_t sys, const nb_pair_cfg* cfg) {
     if (!sys || !cfg) return set_error(NB_EINVAL, "null argument");
     return guarded([&] {
-        nb::PairCfg c{cfg->tile, cfg->i_per_thread, cfg->threads, 0, cfg->min_blocks,
-                      cfg->nr_slots};
+        nb::PairCfg c{cfg->tile,     cfg->i_per_thread, cfg->threads, 0, cfg->min_blocks,
+                      cfg->nr_slots, cfg->i_packed};
         return sys->batch.set_pair_cfg(c);
     });
 }
@@ -336,8 +383,8 @@ nb_status nb_batch_get_state(nb_batch_t b, int32_t sys, double* xv_out, double* 
 nb_status nb_batch_set_pair_cfg(nb_batch_t b, const nb_pair_cfg* cfg) {
     if (!b || !cfg) return set_error(NB_EINVAL, "null argument");
     return guarded([&] {
-        nb::PairCfg c{cfg->tile, cfg->i_per_thread, cfg->threads, 0, cfg->min_blocks,
-                      cfg->nr_slots};
+        nb::PairCfg c{cfg->tile,     cfg->i_per_thread, cfg->threads, 0, cfg->min_blocks,
+                      cfg->nr_slots, cfg->i_packed};
         return b->batch.set_pair_cfg(c);
     });
 }

@@ -125,6 +125,8 @@ nb_status build_system(const nb_desc& d, const nb_params& p, SystemInit& out) {
     if (!finite_pos(d.sep)) return set_error(NB_EINVAL, "sep must be > 0");
     if (!finite_pos(d.f_donor) || !finite_pos(d.f_accretor))
         return set_error(NB_EINVAL, "f_donor and f_accretor must be > 0");
+    if (!(std::isfinite(d.ecc) && d.ecc >= 0.0 && d.ecc < 1.0))
+        return set_error(NB_EINVAL, "ecc must be in [0, 1)");
     if (!(std::isfinite(d.expand_rate) && std::isfinite(d.sigma_v) && d.sigma_v >= 0))
         return set_error(NB_EINVAL, "expand_rate and sigma_v must be finite, sigma_v >= 0");
     if (d.expand_rate < 0) {
@@ -147,8 +149,10 @@ nb_status build_system(const nb_desc& d, const nb_params& p, SystemInit& out) {
     const double rl_a = model_roche_rL(1.0 / q, p.rl_coeff);
     const double star_rd = d.f_donor * rl_d * a;
     const double star_ra = d.f_accretor * rl_a * a;
-    const double cen_d = a / (1.0 + q), cen_a = -a * q / (1.0 + q);
-    const double omega = std::sqrt(p.G / (a * a * a));
+    // start at periapsis of an orbit with semi-major axis a, eccentricity e
+    const double e = d.ecc, rp = a * (1.0 - e);
+    const double cen_d = rp / (1.0 + q), cen_a = -rp * q / (1.0 + q);
+    const double omega = std::sqrt(p.G * (1.0 + e) / (a * a * a * (1.0 - e) * (1.0 - e) * (1.0 - e)));
 
     // element mass = star mass / count; radius = star radius count^(-1/3);
     // repulsion strength kappa G m^2 N^(2/3) / R^5
@@ -232,6 +236,7 @@ nb_status build_system(const nb_desc& d, const nb_params& p, SystemInit& out) {
     out.grow_rate = d.expand_rate;
     out.grow_cap = d.expand_steps;
     out.xl1 = model_roche_L1(q);
+    out.q = q;
     // reference point of the FP32 copy: the initial centre of mass
     double c[3] = {0, 0, 0}, mt = 0;
     for (int64_t i = 0; i < n; ++i) {
@@ -341,6 +346,7 @@ nb_status Batch::init(const std::vector<int64_t>& n_per_slot, int prec, cudaStre
         float* base = nullptr;
         NB_TRY(alloc_((void**)&base, 4 * stride * sizeof(float)));
         d_.pj = PosSoA{base, base + stride, base + 2 * stride, base + 3 * stride};
+        NB_TRY(alloc_((void**)&d_.jd, 2 * stride * sizeof(float4)));
     }
     NB_TRY(alloc_((void**)&d_.sys_of, nt * sizeof(int32_t)));
     NB_TRY(alloc_((void**)&d_.cont, nt * sizeof(double4_32a)));
@@ -408,6 +414,7 @@ nb_status Batch::load(int s, const SystemInit& si, bool defer_forces) {
     c.grow_rel = si.grow_rate / si.grow_f0;
     c.grow_cap = si.grow_cap;
     c.xl1 = si.xl1;
+    c.q = si.q;
     c.active = 1;
     c.contacts = si.contacts;
     double rd = 0, ra = 0;
@@ -453,6 +460,7 @@ nb_status Batch::load(int s, const SystemInit& si, bool defer_forces) {
     NB_CU(cudaMemsetAsync(d_.pj.y + c.off, 0, npad * sizeof(float), stream_));
     NB_CU(cudaMemsetAsync(d_.pj.z + c.off, 0, npad * sizeof(float), stream_));
     NB_CU(cudaMemsetAsync(d_.pj.m + c.off, 0, npad * sizeof(float), stream_));
+    NB_CU(cudaMemsetAsync(d_.jd + 2 * c.off, 0, 2 * npad * sizeof(float4), stream_));
     SysMut m0{};
     NB_CU(cudaMemcpyAsync(d_.sm + s, &m0, sizeof m0, cudaMemcpyHostToDevice, stream_));
     consts_dirty_ = true;
@@ -969,8 +977,12 @@ nb_status Batch::diagnostics(int s, nb_diag* out, bool energy) {
     out->separation = v[28];
     const int64_t kk = (c.grow_cap >= 0 && m.k > c.grow_cap) ? c.grow_cap : m.k;
     out->r_donor = (c.grow_f0 + c.grow_rate * (double)kk) / c.grow_f0;
-    out->n_past_L1 = (int64_t)std::llround(v[32]);
-    out->m_past_L1 = v[33];
+    out->n_past_L1 = (int64_t)std::llround(v[38]);
+    out->m_past_L1 = v[39];
+    out->n_in_accretor_lobe = (int64_t)std::llround(v[40]);
+    out->m_in_accretor_lobe = v[41];
+    out->n_unbound = (int64_t)std::llround(v[42]);
+    out->m_unbound = v[43];
     out->n_nonfinite = (int64_t)std::llround(v[21]);
     return NB_OK;
 }

@@ -13,6 +13,8 @@
 //                                       reference point o, one array per
 //                                       component (the j-stream of the pair
 //                                       kernel)
+//   jd   float4 x 2 ((x,x,y,y),(z,z,Gm,Gm)) the same j-stream with every
+//                                       value duplicated (i-packed pair kernel)
 //   plo  3 x float                      (x-o) - pj: with pj a double-float
 //                                       copy of the position (contact term)
 //   v32  3 x float                      FP32 copy of the velocity
@@ -43,6 +45,7 @@ struct SysConst {
     double rmax_donor0; // largest initial donor radius
     double rmax_acc;    // largest accretor radius
     double xl1;         // L1 distance from the accretor (units of separation)
+    double q;           // donor mass / accretor mass (Roche geometry of Eq. 2)
     int32_t active;     // 0: skipped by every kernel
     int32_t contacts;   // 0: gravity only
     int32_t nchunks;    // j-chunks whose partial sums form the pair term
@@ -92,6 +95,7 @@ struct BatchDev {
     double4_32a* A;
     double2* E;
     PosSoA pj;             // each ntot + NB_PAD (slack)
+    float4* jd;            // 2 * (ntot + NB_PAD)
     Vec3SoA plo;           // each ntot
     Vec3SoA v32;           // each ntot
     int32_t* sys_of;
@@ -127,6 +131,7 @@ struct PairCfg {
     int grid;      // persistent grid size
     int minb;      // resident blocks per SM the register budget is sized for
     int nr;        // i-slots per thread whose reciprocal runs on the FP32 pipe
+    int ipk;       // 1: two i-elements per packed register (j duplicated), 0: two j
 };
 // tmass: per global j-tile (index j / tile) the common G m of its elements,
 // or <= 0 if they differ (nullptr: always per pair).
@@ -174,10 +179,12 @@ uint64_t contact_max_buckets();
 //   [0] sum m  [1] E_kin  [2..4] P  [5..7] L  [8..10] sum m x
 //   [11] m donor  [12..14] sum m x donor  [15] m accretor  [16..18] sum m x accretor
 //   [19] E_grav  [20] E_rep  [21] non-finite count
-//   [22..24] com donor  [25..27] com accretor  [28] separation  [29..31] axis
-//   [32] donor elements past L1  [33] their mass
+//   [22..24] com donor  [25..27] com accretor  [28] separation
+//   [29..31] x axis (accretor -> donor)  [32..34] y axis  [35..37] z axis
+//   [38] donor elements past L1  [39] their mass  [40] in the accretor's
+//   lobe  [41] their mass  [42] unbound  [43] their mass
 constexpr int NB_DIAG_NV = 22;
-constexpr int NB_DIAG_OUT = 40;
+constexpr int NB_DIAG_OUT = 48;
 cudaError_t launch_diag(const BatchDev& b, int sys, cudaStream_t s);
 size_t diag_scratch_doubles();
 

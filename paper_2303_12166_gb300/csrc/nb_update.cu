@@ -52,7 +52,10 @@ __device__ __forceinline__ void write_shadow(const BatchDev& b, const SysConst& 
     b.pj.x[i] = hx;
     b.pj.y[i] = hy;
     b.pj.z[i] = hz;
-    b.pj.m[i] = (float)(c.G * x.w);
+    const float gm = (float)(c.G * x.w);
+    b.pj.m[i] = gm;
+    b.jd[2 * i] = make_float4(hx, hx, hy, hy);
+    b.jd[2 * i + 1] = make_float4(hz, hz, gm, gm);
     b.plo.x[i] = (float)(rx - (double)hx);
     b.plo.y[i] = (float)(ry - (double)hy);
     b.plo.z[i] = (float)(rz - (double)hz);
@@ -151,7 +154,7 @@ __global__ void sum_forces_kernel(BatchDev b, int s, double* __restrict__ out) {
 constexpr int kDiagThreads = 256;
 constexpr int kDiagBlocks = 296;  // fixed: the reduction order depends on n only
 constexpr int NV = NB_DIAG_NV;     // first-pass sums
-constexpr int NV2 = 2;            // second-pass sums
+constexpr int NV2 = 6;            // second-pass sums
 
 template <int NVAL>
 __device__ void block_reduce_store(double (&v)[NVAL], double* dst) {
@@ -217,9 +220,8 @@ __global__ void __launch_bounds__(kDiagThreads) diag_pass1_kernel(BatchDev b, in
     block_reduce_store<NV>(v, b.red);
 }
 
-// Sums the block partials in a fixed order and derives the L1 plane.
-// diag_out: [0, NV) sums, [NV .. NV+6) com_donor, com_accretor,
-// NV+6 separation, NV+7 .. NV+9 axis unit vector.
+// Sums the block partials in a fixed order and derives the frame of the two
+// star centres (see NB_DIAG_OUT in nb_internal.h for the layout).
 __global__ void diag_final1_kernel(BatchDev b, int s, int nblk) {
     __shared__ double tot[NV];
     if (threadIdx.x < NV) {
@@ -239,29 +241,78 @@ __global__ void diag_final1_kernel(BatchDev b, int s, int nblk) {
         }
         const double dx = cd[0] - ca[0], dy = cd[1] - ca[1], dz = cd[2] - ca[2];
         const double sep = sqrt(dx * dx + dy * dy + dz * dz);
+        double ex[3] = {0, 0, 0}, ey[3] = {0, 0, 0}, ez[3] = {0, 0, 1};
+        if (sep > 0) {
+            ex[0] = dx / sep;
+            ex[1] = dy / sep;
+            ex[2] = dz / sep;
+            // z: the orbital axis +z made orthogonal to x; y = z cross x
+            ez[0] = -ex[2] * ex[0];
+            ez[1] = -ex[2] * ex[1];
+            ez[2] = 1.0 - ex[2] * ex[2];
+            const double nz = sqrt(ez[0] * ez[0] + ez[1] * ez[1] + ez[2] * ez[2]);
+            for (int d = 0; d < 3; ++d) ez[d] = nz > 0 ? ez[d] / nz : 0.0;
+            ey[0] = ez[1] * ex[2] - ez[2] * ex[1];
+            ey[1] = ez[2] * ex[0] - ez[0] * ex[2];
+            ey[2] = ez[0] * ex[1] - ez[1] * ex[0];
+        }
         b.diag_out[NV + 6] = sep;
-        b.diag_out[NV + 7] = sep > 0 ? dx / sep : 0.0;
-        b.diag_out[NV + 8] = sep > 0 ? dy / sep : 0.0;
-        b.diag_out[NV + 9] = sep > 0 ? dz / sep : 0.0;
+        for (int d = 0; d < 3; ++d) {
+            b.diag_out[NV + 7 + d] = ex[d];
+            b.diag_out[NV + 10 + d] = ey[d];
+            b.diag_out[NV + 13 + d] = ez[d];
+        }
     }
+}
+
+// Normalised Roche potential of Eq. 2 (Kopal's form): mass m1 at the
+// origin, m2 = q m1 at (1, 0, 0), centre of mass at x = q/(1+q).
+__device__ __forceinline__ double roche_phi(double q, double x, double y, double z) {
+    const double r1 = sqrt(x * x + y * y + z * z);
+    const double r2 = sqrt((x - 1.0) * (x - 1.0) + y * y + z * z);
+    const double xc = x - q / (1.0 + q);
+    return 2.0 / ((1.0 + q) * r1) + 2.0 * q / ((1.0 + q) * r2) + xc * xc + y * y;
 }
 
 __global__ void __launch_bounds__(kDiagThreads) diag_pass2_kernel(BatchDev b, int s) {
     const SysConst& c = b.sc[s];
     const double* d = b.diag_out;
     const double ca[3] = {d[NV + 3], d[NV + 4], d[NV + 5]};
+    const double cd[3] = {d[NV + 0], d[NV + 1], d[NV + 2]};
     const double sep = d[NV + 6];
-    const double ux = d[NV + 7], uy = d[NV + 8], uz = d[NV + 9];
-    const double plane = c.xl1 * sep;
-    double v[NV2] = {0.0, 0.0};
+    const double ex[3] = {d[NV + 7], d[NV + 8], d[NV + 9]};
+    const double ey[3] = {d[NV + 10], d[NV + 11], d[NV + 12]};
+    const double ez[3] = {d[NV + 13], d[NV + 14], d[NV + 15]};
+    const double Md = d[11], Ma = d[15], Mt = d[0];
+    const double vcm[3] = {Mt > 0 ? d[2] / Mt : 0.0, Mt > 0 ? d[3] / Mt : 0.0,
+                           Mt > 0 ? d[4] / Mt : 0.0};
+    const double phi_c = roche_phi(c.q, c.xl1, 0.0, 0.0);
+    double v[NV2] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (c.n_donor > 0 && c.n_donor < c.n && sep > 0) {
         for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < c.n_donor;
              r += (int64_t)gridDim.x * blockDim.x) {
             const double4_32a x = b.X[c.off + r];
-            const double proj = (x.x - ca[0]) * ux + (x.y - ca[1]) * uy + (x.z - ca[2]) * uz;
-            if (proj < plane) {
+            const double4_32a u = b.V[c.off + r];
+            const double px = x.x - ca[0], py = x.y - ca[1], pz = x.z - ca[2];
+            const double xi = (px * ex[0] + py * ex[1] + pz * ex[2]) / sep;
+            if (xi < c.xl1) {
                 v[0] += 1.0;
                 v[1] += x.w;
+                const double yi = (px * ey[0] + py * ey[1] + pz * ey[2]) / sep;
+                const double zi = (px * ez[0] + py * ez[1] + pz * ez[2]) / sep;
+                if (roche_phi(c.q, xi, yi, zi) >= phi_c) {
+                    v[2] += 1.0;
+                    v[3] += x.w;
+                }
+            }
+            const double ux = u.x - vcm[0], uy = u.y - vcm[1], uz = u.z - vcm[2];
+            const double qx = x.x - cd[0], qy = x.y - cd[1], qz = x.z - cd[2];
+            const double ra = sqrt(px * px + py * py + pz * pz);
+            const double rd = sqrt(qx * qx + qy * qy + qz * qz);
+            const double e = 0.5 * (ux * ux + uy * uy + uz * uz) - c.G * Ma / ra - c.G * Md / rd;
+            if (e > 0.0) {
+                v[4] += 1.0;
+                v[5] += x.w;
             }
         }
     }
@@ -272,7 +323,7 @@ __global__ void diag_final2_kernel(BatchDev b, int nblk) {
     if (threadIdx.x < NV2) {
         double x = 0.0;
         for (int k = 0; k < nblk; ++k) x += b.red[k * NV2 + threadIdx.x];
-        b.diag_out[NV + 10 + threadIdx.x] = x;
+        b.diag_out[NV + 16 + threadIdx.x] = x;
     }
 }
 

@@ -46,7 +46,7 @@ class nb_desc(ctypes.Structure):
     _fields_ = [("n_donor", _I64), ("n_accretor", _I64), ("q", _D), ("sep", _D),
                 ("f_donor", _D), ("f_accretor", _D), ("expand_rate", _D),
                 ("expand_steps", _I64), ("sigma_v", _D), ("seed", _U64), ("stream", _U64),
-                ("xv_in", ctypes.POINTER(_D)), ("mrg_in", ctypes.POINTER(_D))]
+                ("xv_in", ctypes.POINTER(_D)), ("mrg_in", ctypes.POINTER(_D)), ("ecc", _D)]
 
 
 class nb_diag(ctypes.Structure):
@@ -54,7 +54,8 @@ class nb_diag(ctypes.Structure):
                 ("e_tot", _D), ("p", _D * 3), ("l", _D * 3), ("com", _D * 3),
                 ("com_donor", _D * 3), ("com_accretor", _D * 3), ("separation", _D),
                 ("r_donor", _D), ("n_past_L1", _I64), ("m_past_L1", _D),
-                ("n_nonfinite", _I64)]
+                ("n_nonfinite", _I64), ("n_in_accretor_lobe", _I64), ("m_in_accretor_lobe", _D),
+                ("n_unbound", _I64), ("m_unbound", _D)]
 
 
 class nb_ckpt_meta(ctypes.Structure):
@@ -69,7 +70,7 @@ class nb_prof(ctypes.Structure):
 
 class nb_pair_cfg(ctypes.Structure):
     _fields_ = [("tile", _I32), ("i_per_thread", _I32), ("threads", _I32),
-                ("min_blocks", _I32), ("nr_slots", _I32), ("reserved", _I32), ("ms", _D)]
+                ("min_blocks", _I32), ("nr_slots", _I32), ("i_packed", _I32), ("ms", _D)]
 
 
 class nb_result(ctypes.Structure):
@@ -98,6 +99,7 @@ _sig("nb_params_default", ctypes.c_int, [ctypes.POINTER(nb_params)])
 _sig("nb_desc_default", ctypes.c_int, [ctypes.POINTER(nb_desc)])
 _sig("nb_roche_rL", _D, [_D, _D])
 _sig("nb_roche_L1", _D, [_D])
+_sig("nb_preset", ctypes.c_int, [_I32, _I64, ctypes.POINTER(nb_desc), ctypes.POINTER(nb_params)])
 _sig("nb_create_system", ctypes.c_int,
      [ctypes.POINTER(nb_desc), ctypes.POINTER(nb_params), _P, ctypes.POINTER(_P)])
 _sig("nb_destroy", None, [_P])
@@ -203,6 +205,25 @@ def nb_roche_L1(q: float) -> float:
     return float(_lib.nb_roche_L1(float(q)))
 
 
+NB_PRESET_COMPACT_ACCRETOR, NB_PRESET_TWO_MAIN_SEQUENCE, NB_PRESET_RED_GIANT = 0, 1, 2
+
+
+def nb_preset(which: int, n: int):
+    """(desc, params) of a scenario preset with n elements."""
+    d, p = nb_desc(), nb_params()
+    _check(_lib.nb_preset(int(which), int(n), ctypes.byref(d), ctypes.byref(p)), "nb_preset")
+    return d, p
+
+
+def dump_state(system, path: str) -> None:
+    """Headless snapshot of a System: positions/velocities, step and the FP64
+    diagnostics, as a numpy .npz file."""
+    xv, a, meta = system.get_state()
+    d = system.diagnostics()
+    np.savez(path, xv=xv, a=a, step=meta.step, origin=np.array(meta.origin[:]),
+             **{f"diag_{k}": np.asarray(v) for k, v in d.items()})
+
+
 # ------------------------------------------------------------------ single system
 def nb_create_system(desc: nb_desc, params: nb_params, stream=None, xv_in=None, mrg_in=None):
     """Returns an opaque handle (int).  xv_in (n,6) / mrg_in (n,3) are optional
@@ -303,8 +324,8 @@ def nb_autotune(h, reps: int = 3) -> dict:
 
 
 def nb_set_pair_cfg(h, tile: int, i_per_thread: int, threads: int, min_blocks: int,
-                    nr_slots: int = 0) -> None:
-    c = nb_pair_cfg(tile, i_per_thread, threads, min_blocks, nr_slots, 0, 0.0)
+                    nr_slots: int = 0, i_packed: int = 0) -> None:
+    c = nb_pair_cfg(tile, i_per_thread, threads, min_blocks, nr_slots, i_packed, 0.0)
     _check(_lib.nb_set_pair_cfg(_P(h), ctypes.byref(c)), "nb_set_pair_cfg")
 
 
@@ -398,8 +419,9 @@ def nb_batch_get_state(h, sys: int, with_acc: bool = True):
     return xv, a, meta
 
 
-def nb_batch_set_pair_cfg(h, tile, i_per_thread, threads, min_blocks, nr_slots=0) -> None:
-    c = nb_pair_cfg(tile, i_per_thread, threads, min_blocks, nr_slots, 0, 0.0)
+def nb_batch_set_pair_cfg(h, tile, i_per_thread, threads, min_blocks, nr_slots=0,
+                          i_packed=0) -> None:
+    c = nb_pair_cfg(tile, i_per_thread, threads, min_blocks, nr_slots, i_packed, 0.0)
     _check(_lib.nb_batch_set_pair_cfg(_P(h), ctypes.byref(c)), "nb_batch_set_pair_cfg")
 
 
@@ -570,8 +592,8 @@ class System:
     def autotune(self, reps: int = 3) -> dict:
         return nb_autotune(self.h, reps)
 
-    def set_pair_cfg(self, tile, i_per_thread, threads, min_blocks, nr_slots=0):
-        nb_set_pair_cfg(self.h, tile, i_per_thread, threads, min_blocks, nr_slots)
+    def set_pair_cfg(self, tile, i_per_thread, threads, min_blocks, nr_slots=0, i_packed=0):
+        nb_set_pair_cfg(self.h, tile, i_per_thread, threads, min_blocks, nr_slots, i_packed)
 
     def pair_cfg(self) -> dict:
         return nb_get_pair_cfg(self.h)

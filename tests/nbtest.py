@@ -34,4 +34,5 @@ def oracle_ic(orc, desc, params):
                        f_donor=desc["f_donor"], f_accretor=desc["f_accretor"],
                        sigma_v=desc["sigma_v"], seed=desc["seed"], stream=desc["stream"],
                        G=params["G"], kappa_gamma=params["kappa_gamma"],
-                       rl_coeff=params["rl_coeff"])
+                       rl_coeff=params["rl_coeff"], ecc=desc.get("ecc", 0.0),
+                       no_spin=bool(params.get("flags", 0) & 2))

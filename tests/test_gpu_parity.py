@@ -194,7 +194,38 @@ def test_diagnostics_match_oracle(nbm, orc):
     assert np.allclose(d["com_donor"], ref["com_donor"], rtol=0, atol=1e-14)
     assert d["separation"] == pytest.approx(ref["separation"], rel=1e-13)
     assert d["n_past_L1"] == ref["n_past_L1"]
+    assert d["n_in_accretor_lobe"] == ref["n_in_acc_lobe"]
+    assert d["n_unbound"] == ref["n_unbound"]
+    assert d["m_unbound"] == pytest.approx(ref["m_unbound"], rel=1e-12, abs=1e-300)
     assert d["n_nonfinite"] == 0
+
+
+def test_mass_transfer_accounting_matches_oracle(nbm, orc):
+    """Donor elements past L1, inside the accretor's lobe and unbound, after
+    the violent first steps of the 1,024-element binary (elements are
+    ejected) and for a hand-placed state with elements moved into the
+    accretor's lobe."""
+    desc, params = workload_kwargs("binary_1k")
+    with _make(nbm, desc, params) as s:
+        s.step(60)
+        d = s.diagnostics()
+        x, v, _, _ = _state(s)
+    ox, ov, om, oR, og = oracle_ic(orc, desc, params)
+    ref = orc.diagnostics(x, v, om, oR, og, eps=params["eps"], n_donor=desc["n_donor"], q=desc["q"])
+    assert ref["n_unbound"] > 0  # the pinned IC recipe ejects elements
+    for k_lib, k_ref in [("n_past_L1", "n_past_L1"), ("n_in_accretor_lobe", "n_in_acc_lobe"),
+                         ("n_unbound", "n_unbound")]:
+        assert d[k_lib] == ref[k_ref], k_lib
+    # elements moved into the accretor's lobe
+    x2 = x.copy()
+    ca = ref["com_accretor"]
+    x2[:20] = ca + 0.02 * (np.arange(20)[:, None] % 3 - 1.0)
+    xv = np.concatenate([x2, v], 1)
+    with _make(nbm, desc, params, xv_in=xv) as s:
+        d2 = s.diagnostics()
+    ref2 = orc.diagnostics(x2, v, om, oR, og, eps=params["eps"], n_donor=desc["n_donor"],
+                           q=desc["q"])
+    assert d2["n_in_accretor_lobe"] == ref2["n_in_acc_lobe"] >= 10
 
 
 # ---------------------------------------------------------------- determinism, checkpoints
@@ -266,9 +297,12 @@ def test_gravity_only_flag(nbm, orc):
 
 # ---------------------------------------------------------------- launch variants
 def _variants():
-    return [(128, 4, 256, 2, 0), (128, 4, 256, 2, 1), (256, 4, 256, 2, 1), (64, 4, 256, 2, 1),
-            (128, 8, 128, 2, 0), (128, 8, 128, 2, 1), (128, 8, 128, 2, 2), (256, 8, 128, 2, 2),
-            (128, 2, 256, 3, 0), (128, 4, 128, 4, 1)]
+    return [(128, 4, 256, 2, 0, 0), (128, 4, 256, 2, 1, 0), (256, 4, 256, 2, 1, 0),
+            (64, 4, 256, 2, 1, 0), (128, 8, 128, 2, 0, 0), (128, 8, 128, 2, 1, 0),
+            (128, 8, 128, 2, 2, 0), (256, 8, 128, 2, 2, 0), (128, 2, 256, 3, 0, 0),
+            (128, 4, 128, 4, 1, 0), (128, 8, 128, 2, 0, 1), (128, 8, 128, 2, 1, 1),
+            (128, 8, 128, 3, 0, 1), (128, 8, 128, 3, 1, 1), (64, 8, 128, 3, 1, 1),
+            (128, 4, 256, 2, 1, 1), (128, 4, 256, 3, 1, 1)]
 
 
 @pytest.mark.parametrize("cfg", _variants())
@@ -296,7 +330,7 @@ def test_autotune_keeps_parity(nbm, orc):
     with _make(nbm, desc, params) as s:
         best = s.autotune(2)
         assert (best["tile"], best["i_per_thread"], best["threads"], best["min_blocks"],
-                best["nr_slots"]) in _variants()
+                best["nr_slots"], best["i_packed"]) in _variants()
         assert best["ms"] > 0
         cfg = s.pair_cfg()
         assert cfg["tile"] == best["tile"]

@@ -41,7 +41,9 @@ MUTANTS = [
     ("L1 equation sign", "(1.0 + q) * mid - q;", "(1.0 + q) * mid + q;"),
     ("lens potential without r^4 term", "\n                   - r * r * r * r / 48.0);",
      ");"),
-    ("donor centre at q/(1+q)", "cx_d = sep / (1.0 + q);", "cx_d = sep * q / (1.0 + q);"),
+    ("donor centre at q/(1+q)", "cx_d = rp / (1.0 + q);", "cx_d = rp * q / (1.0 + q);"),
+    ("periapsis rate with (1-e) squared", "(1.0 - ecc) * (1.0 - ecc) * (1.0 - ecc)));",
+     "(1.0 - ecc) * (1.0 - ecc)));"),
     ("element radius N^-1/2", "Re_d = n_d > 0 ? Rs_d / cbrt((double)n_d) : 0.0;",
      "Re_d = n_d > 0 ? Rs_d / sqrt((double)n_d) : 0.0;"),
     ("coincident elements not skipped", "if (!(d2 > 0.0)) continue;               "
@@ -68,6 +70,7 @@ def _pins():
         (mod.test_head_on_restitution_is_sqrt_beta, {}),
         (mod.test_kdk_time_reversible, {}),
         (mod.test_ic_recipe, {}),
+        (mod.test_eccentric_ic_follows_kepler, {}),
     ]
 
 

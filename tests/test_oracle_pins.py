@@ -481,3 +481,43 @@ def test_diagnostics_L1_count(orc):
     d2 = orc.diagnostics(x2, v, m, R, gam, eps=0.01, n_donor=nd, q=q)
     assert d2["n_past_L1"] == 5
     assert d2["m_past_L1"] == pytest.approx(5 * m[0], rel=1e-14)
+
+
+def test_diagnostics_lobe_and_unbound(orc):
+    """Donor elements placed at the accretor's centre are inside its Roche
+    lobe (the potential of Eq. 2 diverges there), elements placed just past
+    L1 on the donor side are not, and an element given a large outward
+    velocity is unbound while the initial state has none."""
+    q, nd = 0.5, 64
+    x, v, m, R, gam = orc.make_ic(nd, 64, q, f_donor=0.8, f_accretor=0.5, seed=2)
+    d = orc.diagnostics(x, v, m, R, gam, eps=0.01, n_donor=nd, q=q)
+    assert d["n_in_acc_lobe"] == 0 and d["n_unbound"] == 0
+    ca, cd, sep = d["com_accretor"], d["com_donor"], d["separation"]
+    x2, v2 = x.copy(), v.copy()
+    ax = (cd - ca) / sep
+    x2[:3] = ca + 0.05 * sep * np.array([0.0, 1.0, 0.0])           # near the accretor
+    x2[3:5] = ca + (orc.roche_L1(q) + 0.02) * sep * ax              # just past L1, donor side
+    v2[5] = v2[5] + 50.0 * ax                                        # fast escaper
+    d2 = orc.diagnostics(x2, v2, m, R, gam, eps=0.01, n_donor=nd, q=q)
+    assert d2["n_in_acc_lobe"] == 3
+    assert d2["n_past_L1"] == 3
+    assert d2["n_unbound"] == 1
+    assert d2["m_unbound"] == pytest.approx(m[5], rel=1e-14)
+
+
+def test_eccentric_ic_follows_kepler(orc):
+    """The eccentric initial state (periapsis, vis-viva rate) of two tiny
+    stars of one element each, no spin, no jitter, no softening and no
+    contact, follows the Kepler orbit of Kepler's equation."""
+    e, q = 0.4, 0.5
+    x, v, m, R, gam = orc.make_ic(1, 1, q, f_donor=1e-7, f_accretor=1e-7, sigma_v=0.0,
+                                  seed=1, no_spin=True, ecc=e)
+    T = 2.0
+    xe, _, _ = orc.run(x, v, m, np.zeros(2), np.zeros(2), G=1.0, eps=0.0, dt=5e-4,
+                       nsteps=int(T / 5e-4))
+    ref = _kepler_rel(e, 1.0, 1.0, T)
+    assert np.abs((xe[0] - xe[1]) - ref).max() < 1e-5
+    # e = 0 is the circular recipe unchanged
+    a = orc.make_ic(8, 8, q, seed=3)
+    b = orc.make_ic(8, 8, q, seed=3, ecc=0.0)
+    assert all(np.array_equal(u, w) for u, w in zip(a, b))
