@@ -64,7 +64,7 @@ def _pair_traffic(workload, cfg):
     with open(os.path.join(ROOT, "paper_2303_12166_gb300", "csrc", "nb_pair.cu"), "rb") as f:
         sha = hashlib.sha256(f.read()).hexdigest()[:16]
     key = ",".join(str(cfg[k]) for k in ("tile", "i_per_thread", "threads", "min_blocks",
-                                         "nr_slots", "i_packed"))
+                                         "nr_slots", "i_packed", "shared_rcp"))
     if rec.get("workload") != workload or rec.get("pair_cfg") != key or \
             rec.get("kernel_source_sha256_16") != sha:
         return None
@@ -274,7 +274,7 @@ def measure_batched(nbm, torch, dev, stream, args, ws, rank):
            "pairs_per_s": pairs * args.batched_steps / el,
            "ms_per_step": ms / args.batched_steps,
            "pair_cfg": {k: tuned[k] for k in ("tile", "i_per_thread", "threads", "min_blocks",
-                                               "nr_slots", "i_packed")},
+                                               "nr_slots", "i_packed", "shared_rcp")},
            "phase_ms": {"pair": prof["pair_ms"], "contact": prof["contact_ms"],
                         "update": prof["update_ms"]},
            "gpu_launches": int(prof["kernels"])}
@@ -486,7 +486,7 @@ def run_ours(args):
         cfg = _config(args.workload, w, {
             "force_prec": 64 if args.fp64 else 32,
             "pair_cfg": {k: tuned[k] for k in ("tile", "i_per_thread", "threads", "min_blocks",
-                                                "nr_slots", "i_packed")},
+                                                "nr_slots", "i_packed", "shared_rcp")},
             "l2": f"no flush: per-step working set {working_set / 1e6:.0f} MB > L2 129 MB"
             if working_set > L2_BYTES else f"working set {working_set / 1e6:.0f} MB",
             "parallelism": f"replicas x{ws}"})
@@ -538,7 +538,7 @@ def main(argv=None):
     ap.add_argument("--served-requests", type=int, default=32)
     ap.add_argument("--served-steps-div", type=int, default=100)
     ap.add_argument("--pair-cfg", default="",
-                    help="tile,i_per_thread,threads,min_blocks,nr_slots,i_packed (skips the "
+                    help="tile,i_per_thread,threads,min_blocks,nr_slots,i_packed,shared_rcp (skips the "
                          "autotuner)")
     args = ap.parse_args(argv)
     if args.impl == "reference":

@@ -180,6 +180,10 @@ typedef struct nb_pair_cfg {
                               the FP32 pipe instead of MUFU */
     int32_t i_packed;      /* 1: two i-elements per packed FP32x2 register (the
                               j-stream duplicated); 0: two j-elements */
+    int32_t shared_rcp;    /* 1: the two pairs of a packed register share one
+                              MUFU reciprocal (1/a = b/(ab)); needs eps >= 1e-4,
+                              else the plain reciprocal is used */
+    int32_t reserved;
     double ms;             /* measured time of one pair pass (autotune), else 0 */
 } nb_pair_cfg;
 

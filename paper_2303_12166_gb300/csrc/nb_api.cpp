@@ -52,6 +52,7 @@ nb_pair_cfg to_abi(const nb::PairCfg& c, double ms) {
     o.min_blocks = c.minb;
     o.nr_slots = c.nr;
     o.i_packed = c.ipk;
+    o.shared_rcp = c.shr;
     o.ms = ms;
     return o;
 }
@@ -255,7 +256,7 @@ nb_status nb_set_pair_cfg(nb_system_t sys, const nb_pair_cfg* cfg) {
     if (!sys || !cfg) return set_error(NB_EINVAL, "null argument");
     return guarded([&] {
         nb::PairCfg c{cfg->tile,     cfg->i_per_thread, cfg->threads, 0, cfg->min_blocks,
-                      cfg->nr_slots, cfg->i_packed};
+                      cfg->nr_slots, cfg->i_packed, cfg->shared_rcp};
         return sys->batch.set_pair_cfg(c);
     });
 }
@@ -384,7 +385,7 @@ nb_status nb_batch_set_pair_cfg(nb_batch_t b, const nb_pair_cfg* cfg) {
     if (!b || !cfg) return set_error(NB_EINVAL, "null argument");
     return guarded([&] {
         nb::PairCfg c{cfg->tile,     cfg->i_per_thread, cfg->threads, 0, cfg->min_blocks,
-                      cfg->nr_slots, cfg->i_packed};
+                      cfg->nr_slots, cfg->i_packed, cfg->shared_rcp};
         return b->batch.set_pair_cfg(c);
     });
 }

@@ -117,7 +117,7 @@ private:
     std::vector<int64_t> k_;
     std::vector<std::vector<double>> mass_;  // host copy of element masses
     std::vector<double> rmax_d0_, rmax_a_;
-    PairCfg cfg_{128, 4, 256, 0, 2, 1, 0};
+    PairCfg cfg_{128, 4, 256, 0, 2, 1, 0, 0};
     float* tmass_d_ = nullptr;   // per j-tile common G m (see launch_pair_f32)
     int64_t tmass_cap_ = 0;
     std::vector<PairItem> items_;

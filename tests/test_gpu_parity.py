@@ -297,12 +297,13 @@ def test_gravity_only_flag(nbm, orc):
 
 # ---------------------------------------------------------------- launch variants
 def _variants():
-    return [(128, 4, 256, 2, 0, 0), (128, 4, 256, 2, 1, 0), (256, 4, 256, 2, 1, 0),
-            (64, 4, 256, 2, 1, 0), (128, 8, 128, 2, 0, 0), (128, 8, 128, 2, 1, 0),
-            (128, 8, 128, 2, 2, 0), (256, 8, 128, 2, 2, 0), (128, 2, 256, 3, 0, 0),
-            (128, 4, 128, 4, 1, 0), (128, 8, 128, 2, 0, 1), (128, 8, 128, 2, 1, 1),
-            (128, 8, 128, 3, 0, 1), (128, 8, 128, 3, 1, 1), (64, 8, 128, 3, 1, 1),
-            (128, 4, 256, 2, 1, 1), (128, 4, 256, 3, 1, 1)]
+    return [(128, 4, 256, 2, 0, 0, 0), (128, 4, 256, 2, 1, 0, 0), (256, 4, 256, 2, 1, 0, 0),
+            (64, 4, 256, 2, 1, 0, 0), (128, 8, 128, 2, 0, 0, 0), (128, 8, 128, 2, 1, 0, 0),
+            (128, 8, 128, 2, 2, 0, 0), (256, 8, 128, 2, 2, 0, 0), (128, 2, 256, 3, 0, 0, 0),
+            (128, 4, 128, 4, 1, 0, 0), (128, 8, 128, 2, 0, 1, 0), (128, 8, 128, 2, 1, 1, 0),
+            (128, 8, 128, 3, 0, 1, 0), (128, 8, 128, 3, 1, 1, 0), (64, 8, 128, 3, 1, 1, 0),
+            (128, 4, 256, 2, 1, 1, 0), (128, 4, 256, 3, 1, 1, 0), (128, 8, 128, 2, 0, 0, 1),
+            (128, 8, 128, 2, 1, 0, 1), (256, 8, 128, 2, 0, 0, 1), (128, 4, 256, 2, 0, 0, 1)]
 
 
 @pytest.mark.parametrize("cfg", _variants())
@@ -330,7 +331,7 @@ def test_autotune_keeps_parity(nbm, orc):
     with _make(nbm, desc, params) as s:
         best = s.autotune(2)
         assert (best["tile"], best["i_per_thread"], best["threads"], best["min_blocks"],
-                best["nr_slots"], best["i_packed"]) in _variants()
+                best["nr_slots"], best["i_packed"], best["shared_rcp"]) in _variants()
         assert best["ms"] > 0
         cfg = s.pair_cfg()
         assert cfg["tile"] == best["tile"]
@@ -370,3 +371,21 @@ def test_bounded_device_wait_times_out_cleanly(nbm, orc):
     assert st == nbm.NB_ETIMEOUT
     assert time.perf_counter() - t0 < 30.0
     test_forces_binary_1k(nbm, orc, 32, 1e-5)
+
+
+@pytest.mark.parametrize("cfg", [(128, 8, 128, 2, 0, 0, 1), (256, 8, 128, 2, 0, 0, 1)])
+def test_shared_reciprocal_falls_back_without_softening(nbm, orc, cfg):
+    """With eps < 1e-4 the shared-reciprocal variants use the plain
+    reciprocal (the product of two denominators could underflow); the
+    result still matches the oracle, here with eps = 0."""
+    n = 1500
+    x, v = synth.cloud(n, 91, radius=0.5, speed=0.2)
+    m = 0.5 + synth.u01(91, 3, n)
+    desc = dict(n_donor=n // 2, n_accretor=n - n // 2, q=0.5)
+    params = dict(eps=0.0, dt=1e-3, beta=0.5, flags=nbm.NB_GRAVITY_ONLY)
+    mrg = np.stack([m, np.zeros(n), np.zeros(n)], 1)
+    with _make(nbm, desc, params, xv_in=np.concatenate([x, v], 1), mrg_in=mrg) as s:
+        s.set_pair_cfg(*cfg)
+        a = s.forces()
+    ref = orc.forces(x, v, m, np.zeros(n), np.zeros(n), G=1.0, eps=0.0)
+    assert rms_rel(a, ref) <= 1e-5
