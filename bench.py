@@ -39,9 +39,27 @@ WORKLOADS = {
 }
 METRIC = "pair-interactions/s"
 L2_BYTES = 129e6
-# MUFU (special-function unit) issue rate per SM per clock and MUFU ops per pair
+# ALU roofline of one pair (Eq. 4) on an SM: 128 FP32 lanes and 16 MUFU
+# (special-function) results per clock (the latter measured).  A pair costs 12
+# FP32 operations (dx, dy, dz, 3 for d2, r + eps, 2 for the denominator, 3
+# accumulations) and 2 MUFU (square root, reciprocal); sharing one reciprocal
+# between two pairs trades 0.5 MUFU for 1.5 FP32 per pair.  The bound is the
+# best split between the two pipes.
+FP32_PER_SM_CLK = 128
 MUFU_PER_SM_CLK = 16
-MUFU_PER_PAIR = 2
+FP32_PER_PAIR = 12.0
+MUFU_PER_PAIR = 2.0
+SHARED_RCP_FP32, SHARED_RCP_MUFU = 1.5, 0.5
+
+
+def pairs_per_sm_clk():
+    """Pairs per clock per SM at the best split x of shared reciprocals:
+    max over x in [0, 1] of min(FP32 rate / FP32 ops, MUFU rate / MUFU ops)."""
+    x = (MUFU_PER_PAIR * FP32_PER_SM_CLK / MUFU_PER_SM_CLK - FP32_PER_PAIR) / (
+        SHARED_RCP_FP32 + SHARED_RCP_MUFU * FP32_PER_SM_CLK / MUFU_PER_SM_CLK)
+    x = min(max(x, 0.0), 1.0)
+    return min(FP32_PER_SM_CLK / (FP32_PER_PAIR + SHARED_RCP_FP32 * x),
+               MUFU_PER_SM_CLK / (MUFU_PER_PAIR - SHARED_RCP_MUFU * x)), x
 
 
 def _dist():
@@ -443,11 +461,12 @@ def run_ours(args):
     pairs_step = float(n) * float(n)
     value = pairs_step * args.steps * ws / (ms_max * 1e-3)
 
-    # roofline of the pair kernel: MUFU-bound pairs/s of the device
+    # roofline of the pair kernel: ALU-bound pairs/s of the device
     props = torch.cuda.get_device_properties(dev)
     peaks, peak_src = _measured_peaks()
     sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_pairs = props.multi_processor_count * sm_max_mhz * 1e6 * MUFU_PER_SM_CLK / MUFU_PER_PAIR
+    ppc, x_opt = pairs_per_sm_clk()
+    peak_pairs = props.multi_processor_count * sm_max_mhz * 1e6 * ppc
     pair_ms = prof["pair_ms"] / max(prof["pair_launches"], 1)
     achieved = pairs_step / (pair_ms * 1e-3)
 
@@ -499,8 +518,11 @@ def run_ours(args):
                          "unit": "pairs/s", "frac": achieved / peak_pairs,
                          "traffic": None if args.fp64 else _pair_traffic(args.workload, tuned),
                          "peak_basis": f"{props.multi_processor_count} SMs x {sm_max_mhz:.0f} MHz "
-                                       f"({peak_src} sm_max_mhz) x {MUFU_PER_SM_CLK} MUFU/clk/SM / "
-                                       f"{MUFU_PER_PAIR} MUFU per pair",
+                                       f"({peak_src} sm_max_mhz) x {ppc:.3f} pairs/clk/SM: "
+                                       f"{FP32_PER_SM_CLK} FP32 lanes and {MUFU_PER_SM_CLK} MUFU "
+                                       f"per clk per SM, {FP32_PER_PAIR:g} FP32 + "
+                                       f"{MUFU_PER_PAIR:g} MUFU per pair, a fraction "
+                                       f"{x_opt:.3f} of reciprocals shared",
                          "kernel": "pair_f32_kernel",
                          "kernel_ms": pair_ms},
             "cpu_baseline": cpu,

@@ -180,9 +180,10 @@ typedef struct nb_pair_cfg {
                               the FP32 pipe instead of MUFU */
     int32_t i_packed;      /* 1: two i-elements per packed FP32x2 register (the
                               j-stream duplicated); 0: two j-elements */
-    int32_t shared_rcp;    /* 1: the two pairs of a packed register share one
-                              MUFU reciprocal (1/a = b/(ab)); needs eps >= 1e-4,
-                              else the plain reciprocal is used */
+    int32_t shared_rcp;    /* i-elements per thread (0 .. i_per_thread - nr_slots)
+                              whose two pairs per packed register share one
+                              MUFU reciprocal (1/a = b/(ab)); used while
+                              eps >= 1e-4, else the plain reciprocal */
     int32_t reserved;
     double ms;             /* measured time of one pair pass (autotune), else 0 */
 } nb_pair_cfg;
@@ -272,8 +273,15 @@ nb_status nb_set_state(nb_system_t sys, const double* xv_in, const double* a_in,
  * NULL) receives it.  Results are cached per element count and precision
  * for the life of the process.  The state is not changed. */
 nb_status nb_autotune(nb_system_t sys, int reps, nb_pair_cfg* best);
+/* Select a pair-kernel variant; it must be one of nb_pair_cfg_variants'
+ * (NB_EINVAL otherwise).  The field ms is ignored. */
 nb_status nb_set_pair_cfg(nb_system_t sys, const nb_pair_cfg* cfg);
 nb_status nb_get_pair_cfg(nb_system_t sys, nb_pair_cfg* cfg);
+/* The built pair-kernel variants (an implementation detail of this library;
+ * the paper has no counterpart).  Writes min(cap, total) of them to out
+ * (caller-owned, may be NULL when cap is 0) and the total to *count.  Needs
+ * no GPU. */
+nb_status nb_pair_cfg_variants(nb_pair_cfg* out, int32_t cap, int32_t* count);
 
 /* Failure-detection self-test: a kernel waits on a device barrier that
  * nothing completes, with the same bounded wait the pair kernel uses, and

@@ -267,6 +267,16 @@ nb_status nb_get_pair_cfg(nb_system_t sys, nb_pair_cfg* cfg) {
     return NB_OK;
 }
 
+nb_status nb_pair_cfg_variants(nb_pair_cfg* out, int32_t cap, int32_t* count) {
+    if (!count || cap < 0 || (cap > 0 && !out)) return set_error(NB_EINVAL, "bad argument");
+    return guarded([&] {
+        const std::vector<nb::PairCfg> v = nb::pair_cfgs();
+        for (int32_t i = 0; i < cap && i < (int32_t)v.size(); ++i) out[i] = to_abi(v[i], 0.0);
+        *count = (int32_t)v.size();
+        return NB_OK;
+    });
+}
+
 nb_status nb_selftest_device_wait(int64_t budget_clocks, void* stream) {
     return guarded([&]() -> nb_status {
         if (budget_clocks < 0) return set_error(NB_EINVAL, "budget must be >= 0");

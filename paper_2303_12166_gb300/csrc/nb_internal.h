@@ -132,7 +132,7 @@ struct PairCfg {
     int minb;      // resident blocks per SM the register budget is sized for
     int nr;        // i-slots per thread whose reciprocal runs on the FP32 pipe
     int ipk;       // 1: two i-elements per packed register (j duplicated), 0: two j
-    int shr;       // 1: the two halves of a packed register share one reciprocal
+    int shr;       // i-slots whose two packed pairs share one MUFU reciprocal
 };
 // tmass: per global j-tile (index j / tile) the common G m of its elements,
 // or <= 0 if they differ (nullptr: always per pair).

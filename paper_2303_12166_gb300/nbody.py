@@ -139,6 +139,8 @@ _sig("nb_server_clock", _D, [_P])
 _sig("nb_server_destroy", None, [_P])
 _sig("nb_set_pair_cfg", ctypes.c_int, [_P, ctypes.POINTER(nb_pair_cfg)])
 _sig("nb_get_pair_cfg", ctypes.c_int, [_P, ctypes.POINTER(nb_pair_cfg)])
+_sig("nb_pair_cfg_variants", ctypes.c_int,
+     [ctypes.POINTER(nb_pair_cfg), _I32, ctypes.POINTER(_I32)])
 _sig("nb_profile_read", ctypes.c_int, [_P, ctypes.POINTER(nb_prof), ctypes.c_int])
 
 
@@ -335,6 +337,20 @@ def nb_get_pair_cfg(h) -> dict:
     c = nb_pair_cfg()
     _check(_lib.nb_get_pair_cfg(_P(h), ctypes.byref(c)), "nb_get_pair_cfg")
     return _cfg_dict(c)
+
+
+PAIR_CFG_FIELDS = ("tile", "i_per_thread", "threads", "min_blocks", "nr_slots", "i_packed",
+                   "shared_rcp")
+
+
+def nb_pair_cfg_variants() -> list:
+    """Every built pair-kernel variant as a tuple in PAIR_CFG_FIELDS order."""
+    count = _I32(0)
+    _check(_lib.nb_pair_cfg_variants(None, 0, ctypes.byref(count)), "nb_pair_cfg_variants")
+    arr = (nb_pair_cfg * max(count.value, 1))()
+    _check(_lib.nb_pair_cfg_variants(arr, count.value, ctypes.byref(count)),
+           "nb_pair_cfg_variants")
+    return [tuple(getattr(arr[i], f) for f in PAIR_CFG_FIELDS) for i in range(count.value)]
 
 
 NB_NOALLOC_MAX_N = 16384

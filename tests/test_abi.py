@@ -52,6 +52,22 @@ def test_host_calls(lib_path, orc):
         assert nbm.nb_roche_L1(q) == pytest.approx(orc.roche_L1(q), abs=1e-14)
 
 
+def test_pair_variant_table(lib_path):
+    """The variant table is readable without a GPU and every entry respects
+    the slot split: Newton-Raphson plus shared-reciprocal slots <= i per
+    thread, and the shared reciprocal only on the j-packed kernel."""
+    from paper_2303_12166_gb300 import nbody as nbm
+    v = nbm.nb_pair_cfg_variants()
+    assert len(v) >= 20 and len(set(v)) == len(v)
+    for tile, bi, nt, minb, nr, ipk, shr in v:
+        assert tile in (64, 128, 256) and nt % 32 == 0 and minb >= 1
+        assert nr >= 0 and shr >= 0 and (nr * (2 if ipk else 1) + shr) <= bi
+        assert not (ipk and shr)
+    with pytest.raises(nbm.NbError) as ei:
+        nbm._check(nbm._lib.nb_pair_cfg_variants(None, 1, ctypes.byref(nbm._I32())), "x")
+    assert ei.value.status == nbm.NB_EINVAL
+
+
 def test_invalid_parameters_rejected(lib_path):
     from paper_2303_12166_gb300 import nbody as nbm
     cases = [dict(dt=0.0), dict(beta=1.5), dict(eps=-1.0), dict(force_prec=16)]

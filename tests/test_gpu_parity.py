@@ -297,13 +297,10 @@ def test_gravity_only_flag(nbm, orc):
 
 # ---------------------------------------------------------------- launch variants
 def _variants():
-    return [(128, 4, 256, 2, 0, 0, 0), (128, 4, 256, 2, 1, 0, 0), (256, 4, 256, 2, 1, 0, 0),
-            (64, 4, 256, 2, 1, 0, 0), (128, 8, 128, 2, 0, 0, 0), (128, 8, 128, 2, 1, 0, 0),
-            (128, 8, 128, 2, 2, 0, 0), (256, 8, 128, 2, 2, 0, 0), (128, 2, 256, 3, 0, 0, 0),
-            (128, 4, 128, 4, 1, 0, 0), (128, 8, 128, 2, 0, 1, 0), (128, 8, 128, 2, 1, 1, 0),
-            (128, 8, 128, 3, 0, 1, 0), (128, 8, 128, 3, 1, 1, 0), (64, 8, 128, 3, 1, 1, 0),
-            (128, 4, 256, 2, 1, 1, 0), (128, 4, 256, 3, 1, 1, 0), (128, 8, 128, 2, 0, 0, 1),
-            (128, 8, 128, 2, 1, 0, 1), (256, 8, 128, 2, 0, 0, 1), (128, 4, 256, 2, 0, 0, 1)]
+    from paper_2303_12166_gb300 import build
+    build.build()
+    from paper_2303_12166_gb300 import nbody
+    return nbody.nb_pair_cfg_variants()
 
 
 @pytest.mark.parametrize("cfg", _variants())
@@ -373,7 +370,7 @@ def test_bounded_device_wait_times_out_cleanly(nbm, orc):
     test_forces_binary_1k(nbm, orc, 32, 1e-5)
 
 
-@pytest.mark.parametrize("cfg", [(128, 8, 128, 2, 0, 0, 1), (256, 8, 128, 2, 0, 0, 1)])
+@pytest.mark.parametrize("cfg", [(128, 8, 128, 2, 0, 0, 8), (256, 8, 128, 2, 0, 0, 6)])
 def test_shared_reciprocal_falls_back_without_softening(nbm, orc, cfg):
     """With eps < 1e-4 the shared-reciprocal variants use the plain
     reciprocal (the product of two denominators could underflow); the
