@@ -45,21 +45,30 @@ L2_BYTES = 129e6
 # accumulations) and 2 MUFU (square root, reciprocal); sharing one reciprocal
 # between two pairs trades 0.5 MUFU for 1.5 FP32 per pair.  The bound is the
 # best split between the two pipes.
+# With each unordered pair evaluated once (Newton's third law), one
+# evaluation (15 FP32: 3 more accumulations for the second element; 2 MUFU)
+# serves two pair interactions.
 FP32_PER_SM_CLK = 128
 MUFU_PER_SM_CLK = 16
 FP32_PER_PAIR = 12.0
+FP32_PER_PAIR_SYM = 15.0
 MUFU_PER_PAIR = 2.0
 SHARED_RCP_FP32, SHARED_RCP_MUFU = 1.5, 0.5
+PAIR_CFG_KEYS = ("tile", "i_per_thread", "threads", "min_blocks", "nr_slots", "i_packed",
+                 "shared_rcp", "symmetric")
 
 
-def pairs_per_sm_clk():
-    """Pairs per clock per SM at the best split x of shared reciprocals:
-    max over x in [0, 1] of min(FP32 rate / FP32 ops, MUFU rate / MUFU ops)."""
-    x = (MUFU_PER_PAIR * FP32_PER_SM_CLK / MUFU_PER_SM_CLK - FP32_PER_PAIR) / (
+def pairs_per_sm_clk(symmetric: bool = False):
+    """Pair interactions per clock per SM at the best split x of shared
+    reciprocals: max over x in [0, 1] of min(FP32 rate / FP32 ops, MUFU rate /
+    MUFU ops) per evaluation, times the interactions one evaluation serves."""
+    fp32 = FP32_PER_PAIR_SYM if symmetric else FP32_PER_PAIR
+    x = (MUFU_PER_PAIR * FP32_PER_SM_CLK / MUFU_PER_SM_CLK - fp32) / (
         SHARED_RCP_FP32 + SHARED_RCP_MUFU * FP32_PER_SM_CLK / MUFU_PER_SM_CLK)
     x = min(max(x, 0.0), 1.0)
-    return min(FP32_PER_SM_CLK / (FP32_PER_PAIR + SHARED_RCP_FP32 * x),
-               MUFU_PER_SM_CLK / (MUFU_PER_PAIR - SHARED_RCP_MUFU * x)), x
+    per_eval = min(FP32_PER_SM_CLK / (fp32 + SHARED_RCP_FP32 * x),
+                   MUFU_PER_SM_CLK / (MUFU_PER_PAIR - SHARED_RCP_MUFU * x))
+    return (2.0 if symmetric else 1.0) * per_eval, x
 
 
 def _dist():
@@ -81,8 +90,7 @@ def _pair_traffic(workload, cfg):
         rec = json.load(f)
     with open(os.path.join(ROOT, "paper_2303_12166_gb300", "csrc", "nb_pair.cu"), "rb") as f:
         sha = hashlib.sha256(f.read()).hexdigest()[:16]
-    key = ",".join(str(cfg[k]) for k in ("tile", "i_per_thread", "threads", "min_blocks",
-                                         "nr_slots", "i_packed", "shared_rcp"))
+    key = ",".join(str(cfg[k]) for k in PAIR_CFG_KEYS)
     if rec.get("workload") != workload or rec.get("pair_cfg") != key or \
             rec.get("kernel_source_sha256_16") != sha:
         return None
@@ -291,8 +299,7 @@ def measure_batched(nbm, torch, dev, stream, args, ws, rank):
            "value": len(systems) * args.batched_steps / el, "unit": "system-steps/s",
            "pairs_per_s": pairs * args.batched_steps / el,
            "ms_per_step": ms / args.batched_steps,
-           "pair_cfg": {k: tuned[k] for k in ("tile", "i_per_thread", "threads", "min_blocks",
-                                               "nr_slots", "i_packed", "shared_rcp")},
+           "pair_cfg": {k: tuned[k] for k in PAIR_CFG_KEYS},
            "phase_ms": {"pair": prof["pair_ms"], "contact": prof["contact_ms"],
                         "update": prof["update_ms"]},
            "gpu_launches": int(prof["kernels"])}
@@ -465,7 +472,8 @@ def run_ours(args):
     props = torch.cuda.get_device_properties(dev)
     peaks, peak_src = _measured_peaks()
     sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    ppc, x_opt = pairs_per_sm_clk()
+    sym = bool(tuned.get("symmetric", 0)) and not args.fp64
+    ppc, x_opt = pairs_per_sm_clk(sym)
     peak_pairs = props.multi_processor_count * sm_max_mhz * 1e6 * ppc
     pair_ms = prof["pair_ms"] / max(prof["pair_launches"], 1)
     achieved = pairs_step / (pair_ms * 1e-3)
@@ -504,8 +512,7 @@ def run_ours(args):
     if rank == 0:
         cfg = _config(args.workload, w, {
             "force_prec": 64 if args.fp64 else 32,
-            "pair_cfg": {k: tuned[k] for k in ("tile", "i_per_thread", "threads", "min_blocks",
-                                                "nr_slots", "i_packed", "shared_rcp")},
+            "pair_cfg": {k: tuned[k] for k in PAIR_CFG_KEYS},
             "l2": f"no flush: per-step working set {working_set / 1e6:.0f} MB > L2 129 MB"
             if working_set > L2_BYTES else f"working set {working_set / 1e6:.0f} MB",
             "parallelism": f"replicas x{ws}"})
@@ -520,10 +527,12 @@ def run_ours(args):
                          "peak_basis": f"{props.multi_processor_count} SMs x {sm_max_mhz:.0f} MHz "
                                        f"({peak_src} sm_max_mhz) x {ppc:.3f} pairs/clk/SM: "
                                        f"{FP32_PER_SM_CLK} FP32 lanes and {MUFU_PER_SM_CLK} MUFU "
-                                       f"per clk per SM, {FP32_PER_PAIR:g} FP32 + "
-                                       f"{MUFU_PER_PAIR:g} MUFU per pair, a fraction "
-                                       f"{x_opt:.3f} of reciprocals shared",
-                         "kernel": "pair_f32_kernel",
+                                       f"per clk per SM, "
+                                       f"{FP32_PER_PAIR_SYM if sym else FP32_PER_PAIR:g} FP32 + "
+                                       f"{MUFU_PER_PAIR:g} MUFU per evaluation, "
+                                       f"{'2 interactions (i and j sides)' if sym else '1 interaction'}"
+                                       f" per evaluation, a fraction {x_opt:.3f} of reciprocals shared",
+                         "kernel": "pair_sym_kernel" if sym else "pair_f32_kernel",
                          "kernel_ms": pair_ms},
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -560,7 +569,7 @@ def main(argv=None):
     ap.add_argument("--served-requests", type=int, default=32)
     ap.add_argument("--served-steps-div", type=int, default=100)
     ap.add_argument("--pair-cfg", default="",
-                    help="tile,i_per_thread,threads,min_blocks,nr_slots,i_packed,shared_rcp (skips the "
+                    help="tile,i_per_thread,threads,min_blocks,nr_slots,i_packed,shared_rcp[,symmetric] (skips the "
                          "autotuner)")
     args = ap.parse_args(argv)
     if args.impl == "reference":

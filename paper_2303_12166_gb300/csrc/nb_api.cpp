@@ -53,6 +53,7 @@ nb_pair_cfg to_abi(const nb::PairCfg& c, double ms) {
     o.nr_slots = c.nr;
     o.i_packed = c.ipk;
     o.shared_rcp = c.shr;
+    o.symmetric = c.sym;
     o.ms = ms;
     return o;
 }
@@ -255,8 +256,9 @@ nb_status nb_autotune(nb_system_t sys, int reps, nb_pair_cfg* best) {
 nb_status nb_set_pair_cfg(nb_system_t sys, const nb_pair_cfg* cfg) {
     if (!sys || !cfg) return set_error(NB_EINVAL, "null argument");
     return guarded([&] {
-        nb::PairCfg c{cfg->tile,     cfg->i_per_thread, cfg->threads, 0, cfg->min_blocks,
-                      cfg->nr_slots, cfg->i_packed, cfg->shared_rcp};
+        nb::PairCfg c{cfg->tile,     cfg->i_per_thread, cfg->threads, 0,
+                      cfg->min_blocks, cfg->nr_slots, cfg->i_packed, cfg->shared_rcp,
+                      cfg->symmetric};
         return sys->batch.set_pair_cfg(c);
     });
 }
@@ -394,8 +396,9 @@ nb_status nb_batch_get_state(nb_batch_t b, int32_t sys, double* xv_out, double* 
 nb_status nb_batch_set_pair_cfg(nb_batch_t b, const nb_pair_cfg* cfg) {
     if (!b || !cfg) return set_error(NB_EINVAL, "null argument");
     return guarded([&] {
-        nb::PairCfg c{cfg->tile,     cfg->i_per_thread, cfg->threads, 0, cfg->min_blocks,
-                      cfg->nr_slots, cfg->i_packed, cfg->shared_rcp};
+        nb::PairCfg c{cfg->tile,     cfg->i_per_thread, cfg->threads, 0,
+                      cfg->min_blocks, cfg->nr_slots, cfg->i_packed, cfg->shared_rcp,
+                      cfg->symmetric};
         return b->batch.set_pair_cfg(c);
     });
 }

@@ -498,6 +498,12 @@ double Batch::pairs_per_step() const {
     return p;
 }
 
+// ordered pair interactions an item evaluates: in the symmetric list an
+// item against later blocks (j0 > i0) serves both sides
+static double item_pairs(const PairItem& it, bool sym) {
+    return (sym && it.j0 > it.i0 ? 2.0 : 1.0) * (double)it.iend_rel * (double)it.nj;
+}
+
 nb_status Batch::plan_pairs_() {
     if (planned_) return NB_OK;
     const bool f32 = prec_ == 32;
@@ -592,7 +598,62 @@ nb_status Batch::plan_pairs_() {
             return (int64_t)a.iend_rel * a.nj > (int64_t)b.iend_rel * b.nj;
         });
     }
-    if (maxchunks > d_.nchunk_alloc) {
+    int maxslots = maxchunks;
+    int64_t jp_total = 0;
+    sitems_.clear();
+    for (SysConst& c : sc_) c.sym = 0;
+    if (f32 && cfg_.sym) {
+        // Each unordered pair once: block K against itself (slot 0, one-sided)
+        // and against the later blocks in items of at most C tiles (slots
+        // 1, 2, ...), C from the system's own size and the launch shape only,
+        // so that a system gives bitwise the same result alone and in a batch.
+        const int64_t B = I;
+        const int64_t tpb = B / tile;
+        constexpr int64_t kItemsPerSlot = 24;
+        constexpr int64_t kMinChunkTiles = 16;
+        for (int s : act) {
+            SysConst& c = sc_[s];
+            const int64_t nbk = (c.n + B - 1) / B;
+            const int64_t ntiles = (c.n + tile - 1) / tile;
+            int64_t toff = 0;
+            for (int64_t K = 0; K < nbk; ++K) toff += std::max<int64_t>(0, ntiles - (K + 1) * tpb);
+            const int64_t C = std::max<int64_t>(
+                kMinChunkTiles, (toff + slots * kItemsPerSlot - 1) / (slots * kItemsPerSlot));
+            c.sym = 1;
+            c.sym_blk = (int32_t)B;
+            c.sym_tpb = (int32_t)tpb;
+            c.sym_chunk = (int32_t)C;
+            c.sym_ntiles = ntiles;
+            c.jp_off = jp_total;
+            jp_total += nbk * (nbk - 1) / 2 * B;
+            maxslots = std::max<int>(
+                maxslots, 1 + (int)((std::max<int64_t>(0, ntiles - tpb) + C - 1) / C));
+            for (int64_t K = 0; K < nbk; ++K) {
+                PairItem d{};
+                d.i0 = c.off + K * B;
+                d.iend_rel = (int32_t)std::min<int64_t>(B, c.n - K * B);
+                d.j0 = d.i0;
+                d.nj = (int32_t)(std::min<int64_t>(tpb, ntiles - K * tpb) * tile);
+                d.sys = s;
+                d.chunk = 0;
+                sitems_.push_back(d);
+                const int64_t jt0 = (K + 1) * tpb;
+                for (int64_t r = 0; jt0 + r * C < ntiles; ++r) {
+                    PairItem it = d;
+                    it.j0 = c.off + (jt0 + r * C) * tile;
+                    it.nj = (int32_t)(std::min<int64_t>(C, ntiles - jt0 - r * C) * tile);
+                    it.chunk = (int32_t)(1 + r);
+                    sitems_.push_back(it);
+                }
+            }
+        }
+        std::stable_sort(sitems_.begin(), sitems_.end(), [](const PairItem& a, const PairItem& b) {
+            return item_pairs(a, true) > item_pairs(b, true);
+        });
+        if (maxslots > NB_MAX_CHUNKS * 4)
+            return set_error(NB_EINVAL, "symmetric pair plan needs %d partial slots", maxslots);
+    }
+    if (maxslots > d_.nchunk_alloc) {
         // grow the partial-sum buffer (chunk-major)
         if (d_.part) {
             NB_CU(cudaStreamSynchronize(stream_));
@@ -601,26 +662,47 @@ nb_status Batch::plan_pairs_() {
             NB_CU(cudaFreeAsync(d_.part, stream_));
             bytes_ -= (int64_t)d_.nchunk_alloc * d_.ntot * (int64_t)sizeof(double4_32a);
         }
-        NB_TRY(alloc_((void**)&d_.part, (size_t)maxchunks * d_.ntot * sizeof(double4_32a)));
-        d_.nchunk_alloc = maxchunks;
+        NB_TRY(alloc_((void**)&d_.part, (size_t)maxslots * d_.ntot * sizeof(double4_32a)));
+        d_.nchunk_alloc = maxslots;
     }
-    if ((int)items_.size() > items_cap_) {
-        if (items_d_) {
+    if (jp_total > jpart_cap_) {
+        // j-side shares of the symmetric plan: three component arrays
+        if (d_.jpart.x) {
             NB_CU(cudaStreamSynchronize(stream_));
-            auto itp = std::find(allocs_.begin(), allocs_.end(), (void*)items_d_);
+            auto itp = std::find(allocs_.begin(), allocs_.end(), (void*)d_.jpart.x);
             if (itp != allocs_.end()) allocs_.erase(itp);
-            NB_CU(cudaFreeAsync(items_d_, stream_));
+            NB_CU(cudaFreeAsync(d_.jpart.x, stream_));
+            bytes_ -= 3 * jpart_cap_ * (int64_t)sizeof(float);
         }
-        items_cap_ = std::max<int>(64, (int)items_.size());
-        NB_TRY(alloc_((void**)&items_d_, (size_t)items_cap_ * sizeof(PairItem)));
+        float* base = nullptr;
+        NB_TRY(alloc_((void**)&base, 3 * (size_t)jp_total * sizeof(float)));
+        d_.jpart = Vec3SoA{base, base + jp_total, base + 2 * jp_total};
+        jpart_cap_ = jp_total;
     }
-    if (!items_.empty())
-        NB_CU(cudaMemcpyAsync(items_d_, items_.data(), items_.size() * sizeof(PairItem),
-                              cudaMemcpyHostToDevice, stream_));
-    cfg_.grid = (int)std::min<int64_t>((int64_t)items_.size(), slots);
+    auto upload = [&](const std::vector<PairItem>& v, PairItem*& dptr, int& cap) -> nb_status {
+        if ((int)v.size() > cap) {
+            if (dptr) {
+                NB_CU(cudaStreamSynchronize(stream_));
+                auto itp = std::find(allocs_.begin(), allocs_.end(), (void*)dptr);
+                if (itp != allocs_.end()) allocs_.erase(itp);
+                NB_CU(cudaFreeAsync(dptr, stream_));
+            }
+            cap = std::max<int>(64, (int)v.size());
+            NB_TRY(alloc_((void**)&dptr, (size_t)cap * sizeof(PairItem)));
+        }
+        if (!v.empty())
+            NB_CU(cudaMemcpyAsync(dptr, v.data(), v.size() * sizeof(PairItem),
+                                  cudaMemcpyHostToDevice, stream_));
+        return NB_OK;
+    };
+    NB_TRY(upload(items_, items_d_, items_cap_));
+    NB_TRY(upload(sitems_, sitems_d_, sitems_cap_));
+    pot_grid_ = (int)std::min<int64_t>((int64_t)items_.size(), slots);
+    cfg_.grid = f32 && cfg_.sym ? (int)std::min<int64_t>((int64_t)sitems_.size(), slots)
+                                : pot_grid_;
     consts_dirty_ = true;
     NB_TRY(push_consts_());
-    NB_CU(cudaStreamSynchronize(stream_));  // items_ host buffer is pageable
+    NB_CU(cudaStreamSynchronize(stream_));  // item host buffers are pageable
     planned_ = true;
     if (graph_exec_) {
         cudaGraphExecDestroy(graph_exec_);
@@ -631,17 +713,22 @@ nb_status Batch::plan_pairs_() {
 }
 
 nb_status Batch::launch_pairs_(bool pot, int nitems_limit) {
-    int n = (int)items_.size();
+    const bool sym = prec_ == 32 && cfg_.sym && !pot;
+    int n = (int)(sym ? sitems_ : items_).size();
     if (nitems_limit >= 0 && nitems_limit < n) n = nitems_limit;
     if (n == 0) return NB_OK;
     int* ctr = nullptr;
-    if (dynamic_) {
+    if (dynamic_ || sym) {
         NB_CU(cudaMemsetAsync(counter_d_, 0, sizeof(int), stream_));
         ctr = counter_d_;
     }
     cudaEvent_t ev = prof_begin_();
-    if (prec_ == 32) {
-        NB_CU(launch_pair_f32(d_, tmass_d_, items_d_, n, cfg_, pot, ctr, stream_));
+    if (prec_ == 32 && cfg_.sym && !pot) {
+        NB_CU(launch_pair_sym(d_, tmass_d_, sitems_d_, n, cfg_, ctr, stream_));
+    } else if (prec_ == 32) {
+        PairCfg c = cfg_;
+        c.grid = pot_grid_;
+        NB_CU(launch_pair_f32(d_, tmass_d_, items_d_, n, c, pot, ctr, stream_));
     } else {
         NB_CU(launch_pair_f64(d_, items_d_, n, cfg_.grid, pot, ctr, stream_));
     }
@@ -737,9 +824,10 @@ nb_status Batch::autotune(int reps, PairCfg* best, double* best_ms) {
         if ((st = plan_pairs_()) != NB_OK) break;
         // time about two waves of the persistent grid (items are equal-sized
         // within a system), normalised per pair interaction
-        const int nlim = std::min<int>((int)items_.size(), 2 * std::max(cfg_.grid, 1));
+        const std::vector<PairItem>& list = cfg_.sym ? sitems_ : items_;
+        const int nlim = std::min<int>((int)list.size(), 2 * std::max(cfg_.grid, 1));
         double pairs = 0;
-        for (int q = 0; q < nlim; ++q) pairs += (double)items_[q].iend_rel * items_[q].nj;
+        for (int q = 0; q < nlim; ++q) pairs += item_pairs(list[q], cfg_.sym != 0);
         if ((st = launch_pairs_(false, nlim)) != NB_OK) break;  // warm-up
         cudaEventRecord(e0, stream_);
         for (int r = 0; r < reps && st == NB_OK; ++r) st = launch_pairs_(false, nlim);
@@ -769,7 +857,7 @@ nb_status Batch::autotune(int reps, PairCfg* best, double* best_ms) {
     if (best) *best = cfg_;
     // report the time of one full pair pass at the measured rate
     double pairs_all = 0;
-    for (const PairItem& it : items_) pairs_all += (double)it.iend_rel * it.nj;
+    for (const PairItem& it : cfg_.sym ? sitems_ : items_) pairs_all += item_pairs(it, cfg_.sym != 0);
     if (best_ms) *best_ms = best_t * pairs_all;
     return NB_OK;
 }

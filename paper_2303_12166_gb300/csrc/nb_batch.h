@@ -89,7 +89,7 @@ public:
     cudaStream_t stream() const { return stream_; }
     int prec() const { return prec_; }
     const BatchDev& dev() const { return d_; }
-    int nitems() const { return (int)items_.size(); }
+    int nitems() const { return (int)(cfg_.sym && prec_ == 32 ? sitems_ : items_).size(); }
     // pair interactions evaluated per step (sum of n^2 over active systems)
     double pairs_per_step() const;
     // capture subsequent multi-step calls in a CUDA graph (per step count)
@@ -117,12 +117,17 @@ private:
     std::vector<int64_t> k_;
     std::vector<std::vector<double>> mass_;  // host copy of element masses
     std::vector<double> rmax_d0_, rmax_a_;
-    PairCfg cfg_{128, 4, 256, 0, 2, 1, 0, 0};
+    PairCfg cfg_{128, 4, 256, 0, 2, 1, 0, 0, 0};
     float* tmass_d_ = nullptr;   // per j-tile common G m (see launch_pair_f32)
     int64_t tmass_cap_ = 0;
-    std::vector<PairItem> items_;
+    std::vector<PairItem> items_;      // one-sided work list (also the potential pass)
     PairItem* items_d_ = nullptr;
     int items_cap_ = 0;
+    std::vector<PairItem> sitems_;     // symmetric work list (cfg_.sym)
+    PairItem* sitems_d_ = nullptr;
+    int sitems_cap_ = 0;
+    int pot_grid_ = 0;                 // persistent grid of the one-sided list
+    int64_t jpart_cap_ = 0;            // elements of each jpart component array
     int* counter_d_ = nullptr;
     bool dynamic_ = false;
     bool planned_ = false;

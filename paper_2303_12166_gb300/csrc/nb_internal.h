@@ -50,6 +50,18 @@ struct SysConst {
     int32_t contacts;   // 0: gravity only
     int32_t nchunks;    // j-chunks whose partial sums form the pair term
     float eps_f;        // eps in FP32
+    // Pair sums taken once per unordered pair (each side gets its share):
+    // blocks of sym_blk elements; block K's own partial slots are 0 (the
+    // block against itself) and 1..ceil(max(0, sym_ntiles - (K+1) sym_tpb) /
+    // sym_chunk) (the later blocks, sym_chunk tiles per slot); the share of
+    // element e of block K from each earlier block I sits in jpart at
+    // jp_off + (K (K-1)/2 + I) sym_blk + (e - K sym_blk).
+    int32_t sym;        // 1: the last force pass used this layout
+    int32_t sym_blk;
+    int32_t sym_tpb;    // j-tiles per block
+    int32_t sym_chunk;  // j-tiles per partial slot
+    int64_t sym_ntiles; // j-tiles of the system
+    int64_t jp_off;
 };
 
 // Device-written per-system record.
@@ -101,6 +113,7 @@ struct BatchDev {
     int32_t* sys_of;
     double4_32a* part;         // NB chunks * ntot
     int32_t nchunk_alloc;  // chunks allocated in part
+    Vec3SoA jpart;         // shares of later blocks' pair sums (see SysConst)
     double4_32a* cont;         // ntot
     const SysConst* sc;
     SysMut* sm;
@@ -133,6 +146,7 @@ struct PairCfg {
     int nr;        // i-slots per thread whose reciprocal runs on the FP32 pipe
     int ipk;       // 1: two i-elements per packed register (j duplicated), 0: two j
     int shr;       // i-slots whose two packed pairs share one MUFU reciprocal
+    int sym;       // 1: each unordered pair once, both elements get their share
 };
 // tmass: per global j-tile (index j / tile) the common G m of its elements,
 // or <= 0 if they differ (nullptr: always per pair).
@@ -141,6 +155,12 @@ struct PairCfg {
 cudaError_t launch_pair_f32(const BatchDev& b, const float* tmass, const PairItem* items,
                             int nitems, const PairCfg& cfg, bool with_pot, int* counter,
                             cudaStream_t s);
+// Pair term with each unordered pair evaluated once (cfg.sym): items of the
+// layout in SysConst (block against itself: j0 == i0, one-sided; block
+// against later blocks: j0 > i0, both sides).
+cudaError_t launch_pair_sym(const BatchDev& b, const float* tmass, const PairItem* items,
+                            int nitems, const PairCfg& cfg, int* counter, cudaStream_t s);
+int pair_sym_occupancy(const PairCfg& cfg);
 bool pair_cfg_supported(const PairCfg& cfg);
 std::vector<PairCfg> pair_cfgs();         // every built variant
 int pair_occupancy(const PairCfg& cfg);  // resident CTAs per SM

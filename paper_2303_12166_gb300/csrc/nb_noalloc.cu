@@ -176,7 +176,7 @@ extern "C" nb_status nb_pair_forces_noalloc(const double* xyzm, int64_t n, doubl
     unsigned char* base = static_cast<unsigned char*>(addr);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 
-    const PairCfg cfg0{kTile, kBI, kThreads, 0, kMinB, kNr, 0, 0};
+    const PairCfg cfg0{kTile, kBI, kThreads, 0, kMinB, kNr, 0, 0, 0};
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -1,0 +1,403 @@
+// nb_pair_sym.cu -- the pair term of Eq. 4 with every unordered pair (i, j)
+// evaluated once.
+//
+// The attraction is antisymmetric: with d = x_j - x_i and
+// s = 1 / (r (r + eps)^2), element i receives G m_j s d and element j
+// receives -G m_i s d (Newton's third law).  The one-sided kernel
+// (nb_pair.cu) evaluates s twice per unordered pair, once from each side;
+// here it is evaluated once and both shares are kept, which halves the
+// square roots and reciprocals (the MUFU work that bounds the one-sided
+// kernel) and leaves per unordered pair 15 FP32 operations instead of 24.
+//
+// Work split.  A system's elements form blocks of B = threads x BI elements.
+// Block K against itself is summed one-sided (item j0 == i0, partial slot
+// 0).  Block K against every later block is cut into items of at most
+// sym_chunk j-tiles (partial slots 1, 2, ...); such an item adds the i-side
+// sums to its partial slot as the one-sided kernel does and, per j-tile,
+// writes the j-side share of the whole i-block to its own place in `jpart`
+// (one place per (earlier block, element): nothing is added concurrently,
+// so the result is deterministic).  The kick kernel adds, for element e of
+// block K, its slots in order and then the shares of blocks 0 .. K-1 in
+// order.
+//
+// j-side sums inside a CTA.  Each thread holds BI i-elements and walks the
+// tile two j at a time, so for a group of 8 j (4 packed registers per
+// component) every lane has its own partial sum over its BI elements.  The
+// warp sum of the 8 values is a transposing reduction: at the xor-16, -8
+// and -4 shuffles every lane keeps one half of its values and receives the
+// other half from its partner, so after 3 steps (7 shuffles) each lane
+// holds one j's sum over 8 lanes; two butterfly steps (xor 2, 1) finish the
+// warp sum, 9 shuffles per component for 8 j instead of 40 for a butterfly
+// per j.  Lane (4 g + c) then writes component c (c < 3) of j = g into the
+// warp's row of the tile's ring slot in shared memory.  The warp that
+// finishes a tile last (a shared counter per ring slot) adds the rows of
+// all warps in warp order, applies -G m_i (uniform i-blocks; else the mass
+// was applied per pair), stores the tile's shares and only then releases
+// the ring slot, so no row is overwritten before it has been read.
+//
+// The i-side TwoSum accumulators live in shared memory (touched once per
+// tile), which leaves the registers to the pair arithmetic.
+#include "nb_pair_common.cuh"
+
+namespace nb {
+namespace {
+
+using namespace pairk;
+
+constexpr int kRowPad = 8;  // row stride TILE + 8: the three component rows hit distinct banks
+
+template <int TILE, int BI, int NT>
+struct SymSmem {
+    JTile<TILE> tile[kStages];
+    float row[kStages][NT / 32][3][TILE + kRowPad];
+    float acc[6][BI][NT];  // TwoSum (hi x, y, z, lo x, y, z) of the i-side sums
+};
+
+__device__ __forceinline__ f2 shfl_xor2(f2 v, int m) {
+    return __shfl_xor_sync(0xffffffffu, v, m);
+}
+
+__device__ __forceinline__ f2 sel2(bool c, f2 a, f2 b) { return c ? a : b; }
+
+// Sum over the warp of 8 values per lane (4 packed registers, j = 2q and
+// 2q + 1 in register q); returns the sum for j = (lane >> 2) & 7.
+__device__ __forceinline__ float warp_reduce8(const f2 (&v)[4], int lane) {
+    const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
+    // xor 16: lanes with bit 4 clear keep registers 0, 1; set: 2, 3
+    f2 k0 = add2(sel2(h4, v[2], v[0]), shfl_xor2(sel2(h4, v[0], v[2]), 16));
+    f2 k1 = add2(sel2(h4, v[3], v[1]), shfl_xor2(sel2(h4, v[1], v[3]), 16));
+    // xor 8: keep register 2 h4 + h3
+    const f2 k = add2(sel2(h3, k1, k0), shfl_xor2(sel2(h3, k0, k1), 8));
+    // xor 4: keep j = 2 (2 h4 + h3) + h2
+    float lo, hi;
+    upk(k, lo, hi);
+    float m = (h2 ? hi : lo) + __shfl_xor_sync(0xffffffffu, h2 ? lo : hi, 4);
+    m += __shfl_xor_sync(0xffffffffu, m, 2);
+    m += __shfl_xor_sync(0xffffffffu, m, 1);
+    return m;
+}
+
+// One j-tile against the thread's BI i-elements, both sides.  JUNI: the
+// tile's elements share G m_j (applied by the caller to the i-side sums);
+// IUNI: the i-block's elements share G m_i (applied to the j-side shares
+// when they are stored); otherwise the mass multiplies every pair.
+template <int TILE, int BI, bool JUNI, bool IUNI>
+__device__ __forceinline__ void sym_tile(const JTile<TILE>& tj, const f2 (&xi)[BI],
+                                         const f2 (&yi)[BI], const f2 (&zi)[BI],
+                                         const f2 (&gmi)[BI], f2 eps2, f2 (&ax)[BI],
+                                         f2 (&ay)[BI], f2 (&az)[BI], float* row, int lane) {
+    const f2 floor2 = pk(kD2Floor, kD2Floor);
+    const int jsel = (lane >> 2) & 7;
+    const int csel = lane & 3;
+#pragma unroll 1
+    for (int jb = 0; jb < TILE; jb += 8) {
+        f2 jx[4], jy[4], jz[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = jb + 2 * q;
+            const f2 px = *reinterpret_cast<const f2*>(&tj.x[j]);
+            const f2 py = *reinterpret_cast<const f2*>(&tj.y[j]);
+            const f2 pz = *reinterpret_cast<const f2*>(&tj.z[j]);
+            f2 pm = 0;
+            if (!JUNI) pm = *reinterpret_cast<const f2*>(&tj.m[j]);
+#pragma unroll
+            for (int b = 0; b < BI; ++b) {
+                const f2 dx = sub2(px, xi[b]);
+                const f2 dy = sub2(py, yi[b]);
+                const f2 dz = sub2(pz, zi[b]);
+                const f2 d2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, floor2)));
+                const f2 r = sqrt2(d2);
+                const f2 t1 = add2(r, eps2);
+                const f2 f = rcp2(mul2(mul2(t1, t1), r));
+                const f2 fi = JUNI ? f : mul2(f, pm);
+                ax[b] = fma2(fi, dx, ax[b]);
+                ay[b] = fma2(fi, dy, ay[b]);
+                az[b] = fma2(fi, dz, az[b]);
+                const f2 fj = IUNI ? f : mul2(f, gmi[b]);
+                if (b == 0) {
+                    jx[q] = mul2(fj, dx);
+                    jy[q] = mul2(fj, dy);
+                    jz[q] = mul2(fj, dz);
+                } else {
+                    jx[q] = fma2(fj, dx, jx[q]);
+                    jy[q] = fma2(fj, dy, jy[q]);
+                    jz[q] = fma2(fj, dz, jz[q]);
+                }
+            }
+        }
+        const float vx = warp_reduce8(jx, lane);
+        const float vy = warp_reduce8(jy, lane);
+        const float vz = warp_reduce8(jz, lane);
+        if (csel < 3) row[csel * (TILE + kRowPad) + jb + jsel] = csel == 0 ? vx : (csel == 1 ? vy : vz);
+    }
+}
+
+template <int TILE, int BI, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+    pair_sym_kernel(PosSoA pj, const float* __restrict__ tmass,
+                    const PairItem* __restrict__ items, int nitems,
+                    double4_32a* __restrict__ part, int64_t ntot, Vec3SoA jpart,
+                    const SysConst* __restrict__ sc, SysMut* __restrict__ sm,
+                    int* __restrict__ counter) {
+    constexpr int NW = NT / 32;
+    constexpr int B = NT * BI;
+    static_assert(B % TILE == 0, "a block is a whole number of tiles");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    SymSmem<TILE, BI, NT>& S = *reinterpret_cast<SymSmem<TILE, BI, NT>*>(smem_raw);
+    __shared__ alignas(8) uint64_t full[kStages];
+    __shared__ alignas(8) uint64_t empty[kStages];
+    __shared__ volatile int s_abort[2];
+    __shared__ int s_item;
+    __shared__ int s_cnt[kStages];
+    constexpr uint32_t kBytes = TILE * sizeof(float);
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    if (tid == 0) {
+        for (int st = 0; st < kStages; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], NW);
+            s_cnt[st] = 0;
+        }
+        fence_mbar_init();
+        s_abort[0] = s_abort[1] = 0;
+    }
+    fence_proxy_async();
+    __syncthreads();
+
+    uint32_t q_issue = 0;
+    uint32_t q_cons = 0;
+    int parity = 0;
+    auto issue = [&](int64_t j) -> bool {
+        const uint32_t q = q_issue++;
+        const int st = q % kStages;
+        const uint32_t n = q / kStages;
+        if (n >= 1 && !wait_or_abort(&empty[st], (n - 1) & 1, &s_abort[parity]))
+            return false;
+        mbar_expect_tx(&full[st], 4 * kBytes);
+        bulk_g2s(S.tile[st].x, pj.x + j, kBytes, &full[st]);
+        bulk_g2s(S.tile[st].y, pj.y + j, kBytes, &full[st]);
+        bulk_g2s(S.tile[st].z, pj.z + j, kBytes, &full[st]);
+        bulk_g2s(S.tile[st].m, pj.m + j, kBytes, &full[st]);
+        return true;
+    };
+
+    int idx = blockIdx.x;
+    if (counter) {
+        if (tid == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        idx = s_item;
+    }
+    while (idx < nitems) {
+        const PairItem item = items[idx];
+        const SysConst& c = sc[item.sys];
+        const bool both = item.j0 > item.i0;  // later blocks: both sides
+        const float eps = c.eps_f;
+        const f2 eps2 = pk(eps, eps);
+        const int ntiles = item.nj / TILE;
+        const int64_t gt0 = item.j0 / TILE;
+        const int64_t kblk = (item.i0 - c.off) / B;  // i-block index in the system
+
+        f2 xi[BI], yi[BI], zi[BI], gmi[BI];
+        // common G m of the i-block (> 0), else per element
+        float gI = -1.f;
+        if (both && tmass && item.iend_rel == B) {
+            const int64_t it0 = item.i0 / TILE;
+            gI = tmass[it0];
+            for (int k = 1; k < B / TILE; ++k)
+                if (tmass[it0 + k] != gI) gI = -1.f;
+        }
+#pragma unroll
+        for (int b = 0; b < BI; ++b) {
+            const int rel = b * NT + tid;
+            float x = 0.f, y = 0.f, z = 0.f, g = 0.f;
+            if (rel < item.iend_rel) {
+                x = pj.x[item.i0 + rel];
+                y = pj.y[item.i0 + rel];
+                z = pj.z[item.i0 + rel];
+                g = pj.m[item.i0 + rel];
+            }
+            xi[b] = pk(x, x);
+            yi[b] = pk(y, y);
+            zi[b] = pk(z, z);
+            gmi[b] = pk(g, g);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) S.acc[k][b][tid] = 0.f;
+        }
+
+        bool prod_ok = true;
+        if (tid == 0) {
+            for (int t = 0; t < kAhead && t < ntiles; ++t)
+                prod_ok = prod_ok && issue(item.j0 + (int64_t)t * TILE);
+        }
+        for (int t = 0; t < ntiles; ++t) {
+            if (tid == 0 && prod_ok && t + kAhead < ntiles)
+                prod_ok = issue(item.j0 + (int64_t)(t + kAhead) * TILE);
+            const uint32_t q = q_cons++;
+            const int st = q % kStages;
+            bool got = wait_or_abort(&full[st], (q / kStages) & 1, &s_abort[parity]);
+            got = __all_sync(0xffffffffu, got);
+            if (!got) s_abort[parity] = 1;
+
+            f2 ax[BI], ay[BI], az[BI], ap[BI];
+#pragma unroll
+            for (int b = 0; b < BI; ++b) ax[b] = ay[b] = az[b] = ap[b] = 0ull;
+            const float m = tmass ? tmass[gt0 + t] : -1.f;
+            float* row = &S.row[st][warp][0][0];
+            if (both) {
+                if (m > 0.f) {
+                    if (gI > 0.f)
+                        sym_tile<TILE, BI, true, true>(S.tile[st], xi, yi, zi, gmi, eps2, ax, ay,
+                                                       az, row, lane);
+                    else
+                        sym_tile<TILE, BI, true, false>(S.tile[st], xi, yi, zi, gmi, eps2, ax, ay,
+                                                        az, row, lane);
+                } else {
+                    if (gI > 0.f)
+                        sym_tile<TILE, BI, false, true>(S.tile[st], xi, yi, zi, gmi, eps2, ax, ay,
+                                                        az, row, lane);
+                    else
+                        sym_tile<TILE, BI, false, false>(S.tile[st], xi, yi, zi, gmi, eps2, ax,
+                                                         ay, az, row, lane);
+                }
+            } else if (m > 0.f) {
+                tile_pairs<TILE, BI, 0, 0, true, false>(S.tile[st], xi, yi, zi, eps2, ax, ay, az,
+                                                        ap);
+            } else {
+                tile_pairs<TILE, BI, 0, 0, false, false>(S.tile[st], xi, yi, zi, eps2, ax, ay, az,
+                                                         ap);
+            }
+            const float ms = m > 0.f ? m : 1.f;
+#pragma unroll
+            for (int b = 0; b < BI; ++b) {
+                float hx = S.acc[0][b][tid], hy = S.acc[1][b][tid], hz = S.acc[2][b][tid];
+                float lx = S.acc[3][b][tid], ly = S.acc[4][b][tid], lz = S.acc[5][b][tid];
+                two_sum_acc(hx, lx, ms * sum2(ax[b]));
+                two_sum_acc(hy, ly, ms * sum2(ay[b]));
+                two_sum_acc(hz, lz, ms * sum2(az[b]));
+                S.acc[0][b][tid] = hx;
+                S.acc[1][b][tid] = hy;
+                S.acc[2][b][tid] = hz;
+                S.acc[3][b][tid] = lx;
+                S.acc[4][b][tid] = ly;
+                S.acc[5][b][tid] = lz;
+            }
+            __syncwarp();
+            if (both) {
+                // the last warp to finish this tile stores the j-side shares
+                int last = 0;
+                if (lane == 0) {
+                    __threadfence_block();
+                    last = atomicAdd(&s_cnt[st], 1) == NW - 1;
+                }
+                last = __shfl_sync(0xffffffffu, last, 0);
+                if (last) {
+                    __threadfence_block();
+                    const int64_t jrel0 = item.j0 - c.off + (int64_t)t * TILE;
+                    const int64_t kj = jrel0 / B;
+                    const int64_t base =
+                        c.jp_off + (kj * (kj - 1) / 2 + kblk) * B + (jrel0 - kj * B);
+                    const float scale = gI > 0.f ? -gI : -1.f;
+                    for (int jj = lane; jj < TILE; jj += 32) {
+                        float sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+                        for (int w = 0; w < NW; ++w) {
+                            sx += S.row[st][w][0][jj];
+                            sy += S.row[st][w][1][jj];
+                            sz += S.row[st][w][2][jj];
+                        }
+                        jpart.x[base + jj] = scale * sx;
+                        jpart.y[base + jj] = scale * sy;
+                        jpart.z[base + jj] = scale * sz;
+                    }
+                    if (lane == 0) s_cnt[st] = 0;
+                    __syncwarp();
+                }
+            }
+            if (lane == 0) mbar_arrive(&empty[st]);  // this warp is done with the slot
+        }
+        if (tid == 0 && !prod_ok) s_abort[parity] = 1;
+
+        double4_32a* out = part + (int64_t)item.chunk * ntot + item.i0;
+#pragma unroll
+        for (int b = 0; b < BI; ++b) {
+            const int rel = b * NT + tid;
+            if (rel < item.iend_rel) {
+                out[rel] = make_double4_32a((double)S.acc[0][b][tid] + (double)S.acc[3][b][tid],
+                                            (double)S.acc[1][b][tid] + (double)S.acc[4][b][tid],
+                                            (double)S.acc[2][b][tid] + (double)S.acc[5][b][tid],
+                                            0.0);
+            }
+        }
+
+        if (counter) {
+            __syncthreads();
+            if (tid == 0) s_item = atomicAdd(counter, 1);
+        }
+        __syncthreads();
+        if (s_abort[parity]) {
+            if (tid == 0) {
+                atomicOr(&sm[item.sys].timeout, 1u);
+                const uint32_t q0 = q_issue > kStages ? q_issue - kStages : 0;
+                for (uint32_t q = q0; q < q_issue; ++q)
+                    mbar_wait_bounded(&full[q % kStages], (q / kStages) & 1);
+            }
+            return;
+        }
+        parity ^= 1;
+        idx = counter ? s_item : idx + (int)gridDim.x;
+    }
+}
+
+template <int TILE, int BI, int NT, int MINB>
+cudaError_t launch_sym_t(const BatchDev& b, const float* tmass, const PairItem* items, int nitems,
+                         int grid, int* counter, cudaStream_t s) {
+    // the dynamic shared-memory limit was raised by occupancy_sym, which
+    // every plan calls before its first launch (and outside graph capture)
+    constexpr size_t smem = sizeof(SymSmem<TILE, BI, NT>);
+    pair_sym_kernel<TILE, BI, NT, MINB><<<grid, NT, smem, s>>>(
+        b.pj, tmass, items, nitems, b.part, b.ntot, b.jpart, b.sc, b.sm, counter);
+    return cudaGetLastError();
+}
+
+// raises the kernel's dynamic shared-memory limit, then asks for occupancy
+template <int TILE, int BI, int NT, int MINB>
+int occupancy_sym() {
+    constexpr size_t smem = sizeof(SymSmem<TILE, BI, NT>);
+    if (cudaFuncSetAttribute(pair_sym_kernel<TILE, BI, NT, MINB>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return 0;
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_sym_kernel<TILE, BI, NT, MINB>, NT,
+                                                  smem);
+    return nb;
+}
+
+}  // namespace
+
+#define NB_SYM_IS(T, B, N, M)                                                                 \
+    (c.sym == 1 && c.tile == T && c.bi == B && c.threads == N && c.minb == M && c.nr == 0 &&  \
+     c.ipk == 0 && c.shr == 0)
+
+cudaError_t launch_pair_sym(const BatchDev& b, const float* tmass, const PairItem* items,
+                            int nitems, const PairCfg& c, int* counter, cudaStream_t s) {
+    if (nitems <= 0) return cudaSuccess;
+    const int grid = c.grid > 0 ? c.grid : nitems;
+#define NB_LAUNCH_SYM(T, B, N, M) \
+    if (NB_SYM_IS(T, B, N, M)) return launch_sym_t<T, B, N, M>(b, tmass, items, nitems, grid, counter, s);
+    NB_PAIR_SYM_CFGS(NB_LAUNCH_SYM)
+#undef NB_LAUNCH_SYM
+    return cudaErrorInvalidValue;
+}
+
+int pair_sym_occupancy(const PairCfg& c) {
+#define NB_OCC_SYM(T, B, N, M) \
+    if (NB_SYM_IS(T, B, N, M)) return occupancy_sym<T, B, N, M>();
+    NB_PAIR_SYM_CFGS(NB_OCC_SYM)
+#undef NB_OCC_SYM
+    return 0;
+}
+
+}  // namespace nb

@@ -28,11 +28,32 @@ __device__ __forceinline__ double kick1(double v, double hdt, double a) {
 
 __device__ __forceinline__ double3 total_acc(const BatchDev& b, const SysConst& c, int64_t i) {
     double ax = 0.0, ay = 0.0, az = 0.0;
-    for (int ch = 0; ch < c.nchunks; ++ch) {
-        const double4_32a p = b.part[(int64_t)ch * b.ntot + i];
-        ax += p.x;
-        ay += p.y;
-        az += p.z;
+    if (c.sym) {
+        // block K's own slots in order, then the shares of blocks 0 .. K-1
+        const int64_t rel = i - c.off;
+        const int64_t B = c.sym_blk;
+        const int64_t K = rel / B;
+        const int64_t rest = c.sym_ntiles - (K + 1) * c.sym_tpb;
+        const int nslot = 1 + (rest > 0 ? (int)((rest + c.sym_chunk - 1) / c.sym_chunk) : 0);
+        for (int ch = 0; ch < nslot; ++ch) {
+            const double4_32a p = b.part[(int64_t)ch * b.ntot + i];
+            ax += p.x;
+            ay += p.y;
+            az += p.z;
+        }
+        const int64_t base = c.jp_off + (K * (K - 1) / 2) * B + (rel - K * B);
+        for (int64_t I = 0; I < K; ++I) {
+            ax += (double)b.jpart.x[base + I * B];
+            ay += (double)b.jpart.y[base + I * B];
+            az += (double)b.jpart.z[base + I * B];
+        }
+    } else {
+        for (int ch = 0; ch < c.nchunks; ++ch) {
+            const double4_32a p = b.part[(int64_t)ch * b.ntot + i];
+            ax += p.x;
+            ay += p.y;
+            az += p.z;
+        }
     }
     if (c.contacts) {
         const double4_32a q = b.cont[i];

@@ -71,7 +71,7 @@ class nb_prof(ctypes.Structure):
 class nb_pair_cfg(ctypes.Structure):
     _fields_ = [("tile", _I32), ("i_per_thread", _I32), ("threads", _I32),
                 ("min_blocks", _I32), ("nr_slots", _I32), ("i_packed", _I32),
-                ("shared_rcp", _I32), ("reserved", _I32), ("ms", _D)]
+                ("shared_rcp", _I32), ("symmetric", _I32), ("ms", _D)]
 
 
 class nb_result(ctypes.Structure):
@@ -327,9 +327,10 @@ def nb_autotune(h, reps: int = 3) -> dict:
 
 
 def nb_set_pair_cfg(h, tile: int, i_per_thread: int, threads: int, min_blocks: int,
-                    nr_slots: int = 0, i_packed: int = 0, shared_rcp: int = 0) -> None:
-    c = nb_pair_cfg(tile, i_per_thread, threads, min_blocks, nr_slots, i_packed, shared_rcp, 0,
-                    0.0)
+                    nr_slots: int = 0, i_packed: int = 0, shared_rcp: int = 0,
+                    symmetric: int = 0) -> None:
+    c = nb_pair_cfg(tile, i_per_thread, threads, min_blocks, nr_slots, i_packed, shared_rcp,
+                    symmetric, 0.0)
     _check(_lib.nb_set_pair_cfg(_P(h), ctypes.byref(c)), "nb_set_pair_cfg")
 
 
@@ -340,7 +341,7 @@ def nb_get_pair_cfg(h) -> dict:
 
 
 PAIR_CFG_FIELDS = ("tile", "i_per_thread", "threads", "min_blocks", "nr_slots", "i_packed",
-                   "shared_rcp")
+                   "shared_rcp", "symmetric")
 
 
 def nb_pair_cfg_variants() -> list:
@@ -438,9 +439,9 @@ def nb_batch_get_state(h, sys: int, with_acc: bool = True):
 
 
 def nb_batch_set_pair_cfg(h, tile, i_per_thread, threads, min_blocks, nr_slots=0,
-                          i_packed=0, shared_rcp=0) -> None:
-    c = nb_pair_cfg(tile, i_per_thread, threads, min_blocks, nr_slots, i_packed, shared_rcp, 0,
-                    0.0)
+                          i_packed=0, shared_rcp=0, symmetric=0) -> None:
+    c = nb_pair_cfg(tile, i_per_thread, threads, min_blocks, nr_slots, i_packed, shared_rcp,
+                    symmetric, 0.0)
     _check(_lib.nb_batch_set_pair_cfg(_P(h), ctypes.byref(c)), "nb_batch_set_pair_cfg")
 
 
@@ -612,9 +613,9 @@ class System:
         return nb_autotune(self.h, reps)
 
     def set_pair_cfg(self, tile, i_per_thread, threads, min_blocks, nr_slots=0, i_packed=0,
-                     shared_rcp=0):
+                     shared_rcp=0, symmetric=0):
         nb_set_pair_cfg(self.h, tile, i_per_thread, threads, min_blocks, nr_slots, i_packed,
-                        shared_rcp)
+                        shared_rcp, symmetric)
 
     def pair_cfg(self) -> dict:
         return nb_get_pair_cfg(self.h)

@@ -328,7 +328,8 @@ def test_autotune_keeps_parity(nbm, orc):
     with _make(nbm, desc, params) as s:
         best = s.autotune(2)
         assert (best["tile"], best["i_per_thread"], best["threads"], best["min_blocks"],
-                best["nr_slots"], best["i_packed"], best["shared_rcp"]) in _variants()
+                best["nr_slots"], best["i_packed"], best["shared_rcp"],
+                best["symmetric"]) in _variants()
         assert best["ms"] > 0
         cfg = s.pair_cfg()
         assert cfg["tile"] == best["tile"]

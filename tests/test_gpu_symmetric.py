@@ -1,0 +1,205 @@
+"""The pair term with each unordered pair evaluated once (both elements get
+their share, Newton's third law) against the FP64 oracle, through the C ABI.
+
+The symmetric layout splits a system into blocks of threads x i-per-thread
+elements; these cases span several blocks, a ragged last block, blocks whose
+elements carry different masses (the donor/accretor boundary inside a block,
+per-element masses) and uniform blocks, with and without contacts.
+Tolerances are those of the one-sided FP32 path (1e-5 RMS-relative per
+step, 1e-4 on positions).
+"""
+import numpy as np
+import pytest
+
+import synth
+from nbtest import oracle_ic, rms_rel, workload_kwargs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nbm():
+    from paper_2303_12166_gb300 import build
+    build.build()
+    from paper_2303_12166_gb300 import nbody
+    return nbody
+
+
+def _sym_variants():
+    from paper_2303_12166_gb300 import build
+    build.build()
+    from paper_2303_12166_gb300 import nbody
+    return [c for c in nbody.nb_pair_cfg_variants() if c[7]]
+
+
+ONE_SIDED = (128, 8, 128, 2, 0, 0, 6, 0)
+
+
+def _make(nbm, desc, params, **kw):
+    return nbm.System(nbm.nb_desc_default(**desc), nbm.nb_params_default(**params), **kw)
+
+
+def _cloud_system(nbm, n, seed, contacts=True):
+    x, v = synth.cloud(n, seed, radius=0.4, speed=0.2)
+    st = synth.Stream(seed, 11)
+    m = 0.5 + st.uniform(n)
+    R = (0.01 + 0.01 * st.uniform(n)) if contacts else np.zeros(n)
+    gam = (1.0 + st.uniform(n)) if contacts else np.zeros(n)
+    desc = dict(n_donor=n // 2, n_accretor=n - n // 2, q=0.5)
+    params = dict(eps=0.003, dt=1e-3, beta=0.35)
+    s = _make(nbm, desc, params, xv_in=np.concatenate([x, v], 1),
+              mrg_in=np.stack([m, R, gam], 1))
+    return s, (x, v, m, R, gam)
+
+
+BINARY = dict(n_donor=6000, n_accretor=2500, q=0.4, f_donor=0.9, f_accretor=0.5,
+              sigma_v=1e-3, seed=3, stream=0)
+BINARY_P = dict(eps=0.005, dt=5e-4, beta=0.5)
+
+
+@pytest.mark.parametrize("cfg", _sym_variants())
+@pytest.mark.parametrize("n,contacts", [(3000, True), (4097, False), (5120, True)])
+def test_symmetric_forces_per_element_masses(nbm, orc, cfg, n, contacts):
+    s, (x, v, m, R, gam) = _cloud_system(nbm, n, 40 + n, contacts)
+    with s:
+        s.set_pair_cfg(*cfg)
+        a = s.forces()
+    ref = orc.forces(x, v, m, R, gam, G=1.0, eps=0.003, beta=0.35)
+    assert rms_rel(a, ref) <= 1e-5
+    assert np.abs(a - ref).max() <= 5e-4 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("cfg", _sym_variants())
+def test_symmetric_forces_binary(nbm, orc, cfg):
+    """Uniform-mass blocks of each star and one block holding both."""
+    with _make(nbm, BINARY, BINARY_P) as s:
+        s.set_pair_cfg(*cfg)
+        a = s.forces()
+        a_one = None
+        s.set_pair_cfg(*ONE_SIDED)
+        a_one = s.forces()
+    p = dict(BINARY_P, G=1.0, kappa_gamma=8.0, rl_coeff=0.69)
+    ox, ov, om, oR, og = oracle_ic(orc, BINARY, p)
+    ref = orc.forces(ox, ov, om, oR, og, G=1.0, eps=p["eps"], beta=p["beta"])
+    assert rms_rel(a, ref) <= 1e-5
+    # the two FP32 orders of summation agree far inside the tolerance
+    assert rms_rel(a, a_one) <= 2e-6
+
+
+def test_symmetric_momentum_balance(nbm):
+    """Gravity only: every evaluation hands equal and opposite forces to the
+    two elements, so sum m a vanishes to FP32 rounding of the shares."""
+    s, (x, v, m, R, gam) = _cloud_system(nbm, 6000, 77, contacts=False)
+    with s:
+        s.set_pair_cfg(*_sym_variants()[0])
+        a = s.forces()
+    p = (m[:, None] * a).sum(0)
+    scale = np.abs(m[:, None] * a).sum(0)
+    assert np.all(np.abs(p) <= 1e-6 * scale)
+
+
+def test_symmetric_trajectory(nbm, orc):
+    """100 steps of a 3,500-element binary with contacts and donor growth."""
+    desc = dict(n_donor=2600, n_accretor=900, q=0.3, f_donor=0.9, f_accretor=0.5,
+                expand_rate=1e-3, expand_steps=60, sigma_v=1e-3, seed=6, stream=0)
+    params = dict(eps=0.005, dt=5e-4, beta=0.5)
+    with _make(nbm, desc, params) as s:
+        s.set_pair_cfg(*_sym_variants()[0])
+        s.step(100)
+        s.sync()
+        xv, a, meta = s.get_state()
+        assert meta.step == 100
+    p = dict(params, G=1.0, kappa_gamma=8.0, rl_coeff=0.69)
+    ox, ov, om, oR, og = oracle_ic(orc, desc, p)
+    rx, rv, ra = orc.run(ox, ov, om, oR, og, G=1.0, eps=0.005, beta=0.5, dt=5e-4, nsteps=100,
+                         n_donor=2600, grow_f0=0.9, grow_rate=1e-3, grow_cap=60)
+    assert np.abs(xv[:, :3] - rx).max() <= 1e-4
+    assert np.sqrt(((xv[:, :3] - rx) ** 2).mean()) <= 1e-5
+
+
+def test_symmetric_alone_vs_batch_bitwise(nbm):
+    import torch
+    systems = [
+        (dict(n_donor=3000, n_accretor=1100, q=0.4, f_donor=0.9, f_accretor=0.5, sigma_v=1e-3,
+              seed=1), dict(eps=0.005, dt=5e-4, beta=0.5)),
+        (dict(n_donor=700, n_accretor=700, q=0.9, f_donor=0.7, f_accretor=0.6, sigma_v=2e-3,
+              seed=2), dict(eps=0.008, dt=8e-4, beta=0.7)),
+        (dict(n_donor=5000, n_accretor=2000, q=0.2, f_donor=0.95, f_accretor=0.4,
+              expand_rate=1e-3, expand_steps=-1, sigma_v=1e-3, seed=3),
+         dict(eps=0.004, dt=4e-4, beta=0.3)),
+    ]
+    cfg = _sym_variants()[0]
+    descs = [nbm.nb_desc_default(**d) for d, _ in systems]
+    params = [nbm.nb_params_default(**p) for _, p in systems]
+    stream = torch.cuda.Stream()
+    with nbm.Batch(descs, params, stream=stream) as b:
+        b.set_pair_cfg(*cfg)
+        b.step(5)
+        b.step(5)
+        b.sync()
+        mixed = [b.get_state(s) for s in range(len(systems))]
+    for s, (d, p) in enumerate(systems):
+        with _make(nbm, d, p) as one:
+            one.set_pair_cfg(*cfg)
+            one.step(10)
+            one.sync()
+            xv, a, meta = one.get_state()
+        assert np.array_equal(mixed[s][0], xv), f"system {s}: state differs"
+        assert np.array_equal(mixed[s][1], a), f"system {s}: accelerations differ"
+
+
+def test_symmetric_checkpoint_resume_bitwise(nbm):
+    cfg = _sym_variants()[0]
+    with _make(nbm, BINARY, BINARY_P) as s:
+        s.set_pair_cfg(*cfg)
+        s.step(4)
+        s.sync()
+        xv, a, meta = s.get_state()
+        s.step(6)
+        s.sync()
+        ref = s.get_state()
+    with _make(nbm, BINARY, BINARY_P) as r:
+        r.set_pair_cfg(*cfg)
+        r.set_state(xv, a, meta)
+        r.step(6)
+        r.sync()
+        got = r.get_state()
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+
+
+def test_symmetric_diagnostics_energy_uses_potential_pass(nbm, orc):
+    """The potential (diagnostics) is a one-sided pass; the symmetric layout
+    of the step passes is rebuilt afterwards."""
+    cfg = _sym_variants()[0]
+    with _make(nbm, BINARY, BINARY_P) as s:
+        s.set_pair_cfg(*cfg)
+        d = s.diagnostics()
+        a = s.forces()
+        x = s.get_state()[0]
+    p = dict(BINARY_P, G=1.0, kappa_gamma=8.0, rl_coeff=0.69)
+    ox, ov, om, oR, og = oracle_ic(orc, BINARY, p)
+    od = orc.diagnostics(ox, ov, om, oR, og, G=1.0, eps=p["eps"], n_donor=BINARY["n_donor"])
+    assert d["e_grav"] == pytest.approx(od["E_grav"], rel=1e-6)
+    ref = orc.forces(ox, ov, om, oR, og, G=1.0, eps=p["eps"], beta=p["beta"])
+    assert rms_rel(a, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("name,nrows", [("binary_64k", 256), ("binary_1m", 128)])
+def test_symmetric_full_size_sampled(nbm, orc, name, nrows):
+    """At the benchmark's sizes, in the symmetric launch shape the tuner
+    picks there: sampled rows against the oracle."""
+    desc, params = workload_kwargs(name)
+    cfg = (256, 8, 128, 2, 0, 0, 0, 1)
+    assert cfg in _sym_variants()
+    with _make(nbm, desc, params) as s:
+        s.set_pair_cfg(*cfg)
+        a = s.forces()
+        n = s.n
+    ox, ov, om, oR, og = oracle_ic(orc, desc, params)
+    nd = desc["n_donor"]
+    rows = np.unique(np.concatenate([
+        [0, 1, 1023, 1024, nd - 1, nd, nd + 1, n - 1025, n - 1024, n - 1],
+        (synth.u01(7, 9, nrows) * n).astype(np.int64)]))
+    ref = orc.forces_rows(rows, ox, ov, om, oR, og, G=1.0, eps=params["eps"],
+                          beta=params["beta"])
+    assert rms_rel(a[rows], ref) <= 1e-5
