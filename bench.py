@@ -78,21 +78,31 @@ def _dist():
     return ws, rank, local
 
 
+PAIR_SOURCES = ("nb_pair_common.cuh", "nb_pair.cu", "nb_pair_sym.cu")
+
+
+def pair_sources_sha():
+    """Hash of the pair kernels' sources (the traffic record is void once it changes)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in PAIR_SOURCES:
+        with open(os.path.join(ROOT, "paper_2303_12166_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def _pair_traffic(workload, cfg):
     """DRAM bytes per launch of the pair kernel from the committed ncu capture,
     if it was taken on this workload and launch shape with the current kernel
-    source; otherwise None."""
-    import hashlib
-    p = os.path.join(ROOT, "profiles", "pair_f32_kernel_traffic.json")
+    sources; otherwise None."""
+    p = os.path.join(ROOT, "profiles", "pair_kernel_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         rec = json.load(f)
-    with open(os.path.join(ROOT, "paper_2303_12166_gb300", "csrc", "nb_pair.cu"), "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()[:16]
     key = ",".join(str(cfg[k]) for k in PAIR_CFG_KEYS)
     if rec.get("workload") != workload or rec.get("pair_cfg") != key or \
-            rec.get("kernel_source_sha256_16") != sha:
+            rec.get("sources_sha256_16") != pair_sources_sha():
         return None
     return float(rec["dram_bytes_per_launch"])
 

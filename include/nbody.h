@@ -184,9 +184,11 @@ typedef struct nb_pair_cfg {
                               whose two pairs per packed register share one
                               MUFU reciprocal (1/a = b/(ab)); used while
                               eps >= 1e-4, else the plain reciprocal */
-    int32_t symmetric;     /* 1: every unordered pair evaluated once and both
-                              elements get their share (Newton's third law);
-                              then nr_slots, i_packed and shared_rcp are 0 */
+    int32_t symmetric;     /* >= 1: every unordered pair evaluated once and both
+                              elements get their share (Newton's third law),
+                              with this many groups of 8 j-elements in flight
+                              per thread; then nr_slots, i_packed and
+                              shared_rcp are 0.  0: one-sided sums */
     double ms;             /* measured time of one pair pass (autotune), else 0 */
 } nb_pair_cfg;
 

@@ -37,6 +37,12 @@
 //
 // The i-side TwoSum accumulators live in shared memory (touched once per
 // tile), which leaves the registers to the pair arithmetic.
+//
+// i-packed form (IPK): a packed register holds two i-elements of the thread
+// against one j (the duplicated j-stream ((x,x,y,y),(z,z,Gm,Gm)) of the
+// one-sided i-packed kernel), which halves the registers that hold the
+// i-elements and their sums; the two halves of a j's partial sum are added
+// before the same warp reduction.
 #include "nb_pair_common.cuh"
 
 namespace nb {
@@ -46,9 +52,18 @@ using namespace pairk;
 
 constexpr int kRowPad = 8;  // row stride TILE + 8: the three component rows hit distinct banks
 
-template <int TILE, int BI, int NT>
+template <int TILE, bool IPK>
+struct SymTileT {
+    typedef JTile<TILE> type;
+};
+template <int TILE>
+struct SymTileT<TILE, true> {
+    typedef JTileD<TILE> type;
+};
+
+template <int TILE, int BI, int NT, bool IPK>
 struct SymSmem {
-    JTile<TILE> tile[kStages];
+    typename SymTileT<TILE, IPK>::type tile[kStages];
     float row[kStages][NT / 32][3][TILE + kRowPad];
     float acc[6][BI][NT];  // TwoSum (hi x, y, z, lo x, y, z) of the i-side sums
 };
@@ -77,11 +92,13 @@ __device__ __forceinline__ float warp_reduce8(const f2 (&v)[4], int lane) {
     return m;
 }
 
-// One j-tile against the thread's BI i-elements, both sides.  JUNI: the
+// One j-tile against the thread's BI i-elements, both sides, U groups of 8 j
+// in flight (unrolled, so one group's reduction overlaps the next group's
+// pairs).  JUNI: the
 // tile's elements share G m_j (applied by the caller to the i-side sums);
 // IUNI: the i-block's elements share G m_i (applied to the j-side shares
 // when they are stored); otherwise the mass multiplies every pair.
-template <int TILE, int BI, bool JUNI, bool IUNI>
+template <int TILE, int BI, int U, bool JUNI, bool IUNI>
 __device__ __forceinline__ void sym_tile(const JTile<TILE>& tj, const f2 (&xi)[BI],
                                          const f2 (&yi)[BI], const f2 (&zi)[BI],
                                          const f2 (&gmi)[BI], f2 eps2, f2 (&ax)[BI],
@@ -89,7 +106,7 @@ __device__ __forceinline__ void sym_tile(const JTile<TILE>& tj, const f2 (&xi)[B
     const f2 floor2 = pk(kD2Floor, kD2Floor);
     const int jsel = (lane >> 2) & 7;
     const int csel = lane & 3;
-#pragma unroll 1
+#pragma unroll U
     for (int jb = 0; jb < TILE; jb += 8) {
         f2 jx[4], jy[4], jz[4];
 #pragma unroll
@@ -132,18 +149,91 @@ __device__ __forceinline__ void sym_tile(const JTile<TILE>& tj, const f2 (&xi)[B
     }
 }
 
-template <int TILE, int BI, int NT, int MINB>
+// The same warp sum for 8 scalar values per lane (j = q in value q).
+__device__ __forceinline__ float warp_reduce8s(const float (&v)[8], int lane) {
+    const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
+    float k[4], m2[2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        k[i] = (h4 ? v[i + 4] : v[i]) + __shfl_xor_sync(0xffffffffu, h4 ? v[i] : v[i + 4], 16);
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+        m2[i] = (h3 ? k[i + 2] : k[i]) + __shfl_xor_sync(0xffffffffu, h3 ? k[i] : k[i + 2], 8);
+    float m = (h2 ? m2[1] : m2[0]) + __shfl_xor_sync(0xffffffffu, h2 ? m2[0] : m2[1], 4);
+    m += __shfl_xor_sync(0xffffffffu, m, 2);
+    m += __shfl_xor_sync(0xffffffffu, m, 1);
+    return m;
+}
+
+// i-packed form of sym_tile: BP packed i-pairs per thread against one j at
+// a time.
+template <int TILE, int BP, int U, bool JUNI, bool IUNI>
+__device__ __forceinline__ void sym_tile_ip(const JTileD<TILE>& tj, const f2 (&xi)[BP],
+                                            const f2 (&yi)[BP], const f2 (&zi)[BP],
+                                            const f2 (&gmi)[BP], f2 eps2, f2 (&ax)[BP],
+                                            f2 (&ay)[BP], f2 (&az)[BP], float* row, int lane) {
+    const f2 floor2 = pk(kD2Floor, kD2Floor);
+    const int jsel = (lane >> 2) & 7;
+    const int csel = lane & 3;
+#pragma unroll U
+    for (int jb = 0; jb < TILE; jb += 8) {
+        float jx[8], jy[8], jz[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const f2* v = reinterpret_cast<const f2*>(&tj.v[2 * (jb + q)]);
+            const f2 px = v[0], py = v[1], pz = v[2];
+            f2 pm = 0;
+            if (!JUNI) pm = v[3];
+            f2 sx = 0, sy = 0, sz = 0;
+#pragma unroll
+            for (int p = 0; p < BP; ++p) {
+                const f2 dx = sub2(px, xi[p]);
+                const f2 dy = sub2(py, yi[p]);
+                const f2 dz = sub2(pz, zi[p]);
+                const f2 d2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, floor2)));
+                const f2 r = sqrt2(d2);
+                const f2 t1 = add2(r, eps2);
+                const f2 f = rcp2(mul2(mul2(t1, t1), r));
+                const f2 fi = JUNI ? f : mul2(f, pm);
+                ax[p] = fma2(fi, dx, ax[p]);
+                ay[p] = fma2(fi, dy, ay[p]);
+                az[p] = fma2(fi, dz, az[p]);
+                const f2 fj = IUNI ? f : mul2(f, gmi[p]);
+                if (p == 0) {
+                    sx = mul2(fj, dx);
+                    sy = mul2(fj, dy);
+                    sz = mul2(fj, dz);
+                } else {
+                    sx = fma2(fj, dx, sx);
+                    sy = fma2(fj, dy, sy);
+                    sz = fma2(fj, dz, sz);
+                }
+            }
+            jx[q] = sum2(sx);
+            jy[q] = sum2(sy);
+            jz[q] = sum2(sz);
+        }
+        const float vx = warp_reduce8s(jx, lane);
+        const float vy = warp_reduce8s(jy, lane);
+        const float vz = warp_reduce8s(jz, lane);
+        if (csel < 3) row[csel * (TILE + kRowPad) + jb + jsel] = csel == 0 ? vx : (csel == 1 ? vy : vz);
+    }
+}
+
+template <int TILE, int BI, int NT, int MINB, int U, bool IPK>
 __global__ void __launch_bounds__(NT, MINB)
-    pair_sym_kernel(PosSoA pj, const float* __restrict__ tmass,
+    pair_sym_kernel(PosSoA pj, const float4* __restrict__ jd, const float* __restrict__ tmass,
                     const PairItem* __restrict__ items, int nitems,
                     double4_32a* __restrict__ part, int64_t ntot, Vec3SoA jpart,
                     const SysConst* __restrict__ sc, SysMut* __restrict__ sm,
                     int* __restrict__ counter) {
     constexpr int NW = NT / 32;
     constexpr int B = NT * BI;
+    constexpr int NP = IPK ? BI / 2 : BI;  // packed i-registers per thread
     static_assert(B % TILE == 0, "a block is a whole number of tiles");
+    static_assert(!IPK || BI % 2 == 0, "the i-packed form needs an even slot count");
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    SymSmem<TILE, BI, NT>& S = *reinterpret_cast<SymSmem<TILE, BI, NT>*>(smem_raw);
+    SymSmem<TILE, BI, NT, IPK>& S = *reinterpret_cast<SymSmem<TILE, BI, NT, IPK>*>(smem_raw);
     __shared__ alignas(8) uint64_t full[kStages];
     __shared__ alignas(8) uint64_t empty[kStages];
     __shared__ volatile int s_abort[2];
@@ -175,11 +265,16 @@ __global__ void __launch_bounds__(NT, MINB)
         const uint32_t n = q / kStages;
         if (n >= 1 && !wait_or_abort(&empty[st], (n - 1) & 1, &s_abort[parity]))
             return false;
-        mbar_expect_tx(&full[st], 4 * kBytes);
-        bulk_g2s(S.tile[st].x, pj.x + j, kBytes, &full[st]);
-        bulk_g2s(S.tile[st].y, pj.y + j, kBytes, &full[st]);
-        bulk_g2s(S.tile[st].z, pj.z + j, kBytes, &full[st]);
-        bulk_g2s(S.tile[st].m, pj.m + j, kBytes, &full[st]);
+        if constexpr (IPK) {
+            mbar_expect_tx(&full[st], 8 * kBytes);
+            bulk_g2s(S.tile[st].v, jd + 2 * j, 8 * kBytes, &full[st]);
+        } else {
+            mbar_expect_tx(&full[st], 4 * kBytes);
+            bulk_g2s(S.tile[st].x, pj.x + j, kBytes, &full[st]);
+            bulk_g2s(S.tile[st].y, pj.y + j, kBytes, &full[st]);
+            bulk_g2s(S.tile[st].z, pj.z + j, kBytes, &full[st]);
+            bulk_g2s(S.tile[st].m, pj.m + j, kBytes, &full[st]);
+        }
         return true;
     };
 
@@ -199,7 +294,7 @@ __global__ void __launch_bounds__(NT, MINB)
         const int64_t gt0 = item.j0 / TILE;
         const int64_t kblk = (item.i0 - c.off) / B;  // i-block index in the system
 
-        f2 xi[BI], yi[BI], zi[BI], gmi[BI];
+        f2 xi[NP], yi[NP], zi[NP], gmi[NP];
         // common G m of the i-block (> 0), else per element
         float gI = -1.f;
         if (both && tmass && item.iend_rel == B) {
@@ -208,22 +303,28 @@ __global__ void __launch_bounds__(NT, MINB)
             for (int k = 1; k < B / TILE; ++k)
                 if (tmass[it0 + k] != gI) gI = -1.f;
         }
+        float xs[BI], ys[BI], zs[BI], gs[BI];
 #pragma unroll
         for (int b = 0; b < BI; ++b) {
             const int rel = b * NT + tid;
-            float x = 0.f, y = 0.f, z = 0.f, g = 0.f;
+            xs[b] = ys[b] = zs[b] = gs[b] = 0.f;
             if (rel < item.iend_rel) {
-                x = pj.x[item.i0 + rel];
-                y = pj.y[item.i0 + rel];
-                z = pj.z[item.i0 + rel];
-                g = pj.m[item.i0 + rel];
+                xs[b] = pj.x[item.i0 + rel];
+                ys[b] = pj.y[item.i0 + rel];
+                zs[b] = pj.z[item.i0 + rel];
+                gs[b] = pj.m[item.i0 + rel];
             }
-            xi[b] = pk(x, x);
-            yi[b] = pk(y, y);
-            zi[b] = pk(z, z);
-            gmi[b] = pk(g, g);
 #pragma unroll
             for (int k = 0; k < 6; ++k) S.acc[k][b][tid] = 0.f;
+        }
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            // i-packed: slots (2p, 2p + 1); j-packed: slot p twice
+            const int b0 = IPK ? 2 * p : p, b1 = IPK ? 2 * p + 1 : p;
+            xi[p] = pk(xs[b0], xs[b1]);
+            yi[p] = pk(ys[b0], ys[b1]);
+            zi[p] = pk(zs[b0], zs[b1]);
+            gmi[p] = pk(gs[b0], gs[b1]);
         }
 
         bool prod_ok = true;
@@ -240,42 +341,80 @@ __global__ void __launch_bounds__(NT, MINB)
             got = __all_sync(0xffffffffu, got);
             if (!got) s_abort[parity] = 1;
 
-            f2 ax[BI], ay[BI], az[BI], ap[BI];
+            f2 ax[NP], ay[NP], az[NP], ap[NP];
 #pragma unroll
-            for (int b = 0; b < BI; ++b) ax[b] = ay[b] = az[b] = ap[b] = 0ull;
+            for (int p = 0; p < NP; ++p) ax[p] = ay[p] = az[p] = ap[p] = 0ull;
             const float m = tmass ? tmass[gt0 + t] : -1.f;
             float* row = &S.row[st][warp][0][0];
-            if (both) {
-                if (m > 0.f) {
-                    if (gI > 0.f)
-                        sym_tile<TILE, BI, true, true>(S.tile[st], xi, yi, zi, gmi, eps2, ax, ay,
-                                                       az, row, lane);
-                    else
-                        sym_tile<TILE, BI, true, false>(S.tile[st], xi, yi, zi, gmi, eps2, ax, ay,
-                                                        az, row, lane);
+            const auto& tj = S.tile[st];
+            if constexpr (IPK) {
+                if (both) {
+                    if (m > 0.f) {
+                        if (gI > 0.f)
+                            sym_tile_ip<TILE, NP, U, true, true>(tj, xi, yi, zi, gmi, eps2, ax, ay,
+                                                                 az, row, lane);
+                        else
+                            sym_tile_ip<TILE, NP, U, true, false>(tj, xi, yi, zi, gmi, eps2, ax,
+                                                                  ay, az, row, lane);
+                    } else {
+                        if (gI > 0.f)
+                            sym_tile_ip<TILE, NP, U, false, true>(tj, xi, yi, zi, gmi, eps2, ax,
+                                                                  ay, az, row, lane);
+                        else
+                            sym_tile_ip<TILE, NP, U, false, false>(tj, xi, yi, zi, gmi, eps2, ax,
+                                                                   ay, az, row, lane);
+                    }
+                } else if (m > 0.f) {
+                    tile_pairs_ip<TILE, NP, 0, true, false>(tj, xi, yi, zi, eps2, ax, ay, az, ap);
                 } else {
-                    if (gI > 0.f)
-                        sym_tile<TILE, BI, false, true>(S.tile[st], xi, yi, zi, gmi, eps2, ax, ay,
-                                                        az, row, lane);
-                    else
-                        sym_tile<TILE, BI, false, false>(S.tile[st], xi, yi, zi, gmi, eps2, ax,
-                                                         ay, az, row, lane);
+                    tile_pairs_ip<TILE, NP, 0, false, false>(tj, xi, yi, zi, eps2, ax, ay, az, ap);
                 }
-            } else if (m > 0.f) {
-                tile_pairs<TILE, BI, 0, 0, true, false>(S.tile[st], xi, yi, zi, eps2, ax, ay, az,
-                                                        ap);
             } else {
-                tile_pairs<TILE, BI, 0, 0, false, false>(S.tile[st], xi, yi, zi, eps2, ax, ay, az,
-                                                         ap);
+                if (both) {
+                    if (m > 0.f) {
+                        if (gI > 0.f)
+                            sym_tile<TILE, NP, U, true, true>(tj, xi, yi, zi, gmi, eps2, ax, ay, az,
+                                                              row, lane);
+                        else
+                            sym_tile<TILE, NP, U, true, false>(tj, xi, yi, zi, gmi, eps2, ax, ay,
+                                                               az, row, lane);
+                    } else {
+                        if (gI > 0.f)
+                            sym_tile<TILE, NP, U, false, true>(tj, xi, yi, zi, gmi, eps2, ax, ay,
+                                                               az, row, lane);
+                        else
+                            sym_tile<TILE, NP, U, false, false>(tj, xi, yi, zi, gmi, eps2, ax, ay,
+                                                                az, row, lane);
+                    }
+                } else if (m > 0.f) {
+                    tile_pairs<TILE, NP, 0, 0, true, false>(tj, xi, yi, zi, eps2, ax, ay, az, ap);
+                } else {
+                    tile_pairs<TILE, NP, 0, 0, false, false>(tj, xi, yi, zi, eps2, ax, ay, az, ap);
+                }
             }
             const float ms = m > 0.f ? m : 1.f;
+            // per slot: its i-side tile sum (i-packed: one half of a register;
+            // j-packed: the two halves, even and odd j)
+            float tx[BI], ty[BI], tz[BI];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                if constexpr (IPK) {
+                    upk(ax[p], tx[2 * p], tx[2 * p + 1]);
+                    upk(ay[p], ty[2 * p], ty[2 * p + 1]);
+                    upk(az[p], tz[2 * p], tz[2 * p + 1]);
+                } else {
+                    tx[p] = sum2(ax[p]);
+                    ty[p] = sum2(ay[p]);
+                    tz[p] = sum2(az[p]);
+                }
+            }
 #pragma unroll
             for (int b = 0; b < BI; ++b) {
                 float hx = S.acc[0][b][tid], hy = S.acc[1][b][tid], hz = S.acc[2][b][tid];
                 float lx = S.acc[3][b][tid], ly = S.acc[4][b][tid], lz = S.acc[5][b][tid];
-                two_sum_acc(hx, lx, ms * sum2(ax[b]));
-                two_sum_acc(hy, ly, ms * sum2(ay[b]));
-                two_sum_acc(hz, lz, ms * sum2(az[b]));
+                two_sum_acc(hx, lx, ms * tx[b]);
+                two_sum_acc(hy, ly, ms * ty[b]);
+                two_sum_acc(hz, lz, ms * tz[b]);
                 S.acc[0][b][tid] = hx;
                 S.acc[1][b][tid] = hy;
                 S.acc[2][b][tid] = hz;
@@ -350,51 +489,52 @@ __global__ void __launch_bounds__(NT, MINB)
     }
 }
 
-template <int TILE, int BI, int NT, int MINB>
+template <int TILE, int BI, int NT, int MINB, int U, bool IPK>
 cudaError_t launch_sym_t(const BatchDev& b, const float* tmass, const PairItem* items, int nitems,
                          int grid, int* counter, cudaStream_t s) {
     // the dynamic shared-memory limit was raised by occupancy_sym, which
     // every plan calls before its first launch (and outside graph capture)
-    constexpr size_t smem = sizeof(SymSmem<TILE, BI, NT>);
-    pair_sym_kernel<TILE, BI, NT, MINB><<<grid, NT, smem, s>>>(
-        b.pj, tmass, items, nitems, b.part, b.ntot, b.jpart, b.sc, b.sm, counter);
+    constexpr size_t smem = sizeof(SymSmem<TILE, BI, NT, IPK>);
+    pair_sym_kernel<TILE, BI, NT, MINB, U, IPK><<<grid, NT, smem, s>>>(
+        b.pj, b.jd, tmass, items, nitems, b.part, b.ntot, b.jpart, b.sc, b.sm, counter);
     return cudaGetLastError();
 }
 
 // raises the kernel's dynamic shared-memory limit, then asks for occupancy
-template <int TILE, int BI, int NT, int MINB>
+template <int TILE, int BI, int NT, int MINB, int U, bool IPK>
 int occupancy_sym() {
-    constexpr size_t smem = sizeof(SymSmem<TILE, BI, NT>);
-    if (cudaFuncSetAttribute(pair_sym_kernel<TILE, BI, NT, MINB>,
+    constexpr size_t smem = sizeof(SymSmem<TILE, BI, NT, IPK>);
+    if (cudaFuncSetAttribute(pair_sym_kernel<TILE, BI, NT, MINB, U, IPK>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return 0;
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_sym_kernel<TILE, BI, NT, MINB>, NT,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_sym_kernel<TILE, BI, NT, MINB, U, IPK>, NT,
                                                   smem);
     return nb;
 }
 
 }  // namespace
 
-#define NB_SYM_IS(T, B, N, M)                                                                 \
-    (c.sym == 1 && c.tile == T && c.bi == B && c.threads == N && c.minb == M && c.nr == 0 &&  \
-     c.ipk == 0 && c.shr == 0)
+#define NB_SYM_IS(T, B, N, M, U, P)                                                           \
+    (c.sym == U && c.tile == T && c.bi == B && c.threads == N && c.minb == M && c.nr == 0 &&  \
+     c.ipk == P && c.shr == 0)
 
 cudaError_t launch_pair_sym(const BatchDev& b, const float* tmass, const PairItem* items,
                             int nitems, const PairCfg& c, int* counter, cudaStream_t s) {
     if (nitems <= 0) return cudaSuccess;
     const int grid = c.grid > 0 ? c.grid : nitems;
-#define NB_LAUNCH_SYM(T, B, N, M) \
-    if (NB_SYM_IS(T, B, N, M)) return launch_sym_t<T, B, N, M>(b, tmass, items, nitems, grid, counter, s);
+#define NB_LAUNCH_SYM(T, B, N, M, U, P) \
+    if (NB_SYM_IS(T, B, N, M, U, P))    \
+        return launch_sym_t<T, B, N, M, U, P>(b, tmass, items, nitems, grid, counter, s);
     NB_PAIR_SYM_CFGS(NB_LAUNCH_SYM)
 #undef NB_LAUNCH_SYM
     return cudaErrorInvalidValue;
 }
 
 int pair_sym_occupancy(const PairCfg& c) {
-#define NB_OCC_SYM(T, B, N, M) \
-    if (NB_SYM_IS(T, B, N, M)) return occupancy_sym<T, B, N, M>();
+#define NB_OCC_SYM(T, B, N, M, U, P) \
+    if (NB_SYM_IS(T, B, N, M, U, P)) return occupancy_sym<T, B, N, M, U, P>();
     NB_PAIR_SYM_CFGS(NB_OCC_SYM)
 #undef NB_OCC_SYM
     return 0;

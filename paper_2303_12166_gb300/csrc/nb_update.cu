@@ -41,12 +41,28 @@ __device__ __forceinline__ double3 total_acc(const BatchDev& b, const SysConst& 
             ay += p.y;
             az += p.z;
         }
+        // four running sums (blocks I mod 4), added in a fixed order: the
+        // loads of four blocks are in flight at once
         const int64_t base = c.jp_off + (K * (K - 1) / 2) * B + (rel - K * B);
-        for (int64_t I = 0; I < K; ++I) {
-            ax += (double)b.jpart.x[base + I * B];
-            ay += (double)b.jpart.y[base + I * B];
-            az += (double)b.jpart.z[base + I * B];
+        double sx[4] = {0.0, 0.0, 0.0, 0.0}, sy[4] = {0.0, 0.0, 0.0, 0.0},
+               sz[4] = {0.0, 0.0, 0.0, 0.0};
+        int64_t I = 0;
+        for (; I + 4 <= K; I += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                sx[u] += (double)b.jpart.x[base + (I + u) * B];
+                sy[u] += (double)b.jpart.y[base + (I + u) * B];
+                sz[u] += (double)b.jpart.z[base + (I + u) * B];
+            }
         }
+        for (int u = 0; I < K; ++I, ++u) {
+            sx[u] += (double)b.jpart.x[base + I * B];
+            sy[u] += (double)b.jpart.y[base + I * B];
+            sz[u] += (double)b.jpart.z[base + I * B];
+        }
+        ax += (sx[0] + sx[1]) + (sx[2] + sx[3]);
+        ay += (sy[0] + sy[1]) + (sy[2] + sy[3]);
+        az += (sz[0] + sz[1]) + (sz[2] + sz[3]);
     } else {
         for (int ch = 0; ch < c.nchunks; ++ch) {
             const double4_32a p = b.part[(int64_t)ch * b.ntot + i];
