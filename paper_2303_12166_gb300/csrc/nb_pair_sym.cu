@@ -94,11 +94,12 @@ __device__ __forceinline__ float warp_reduce8(const f2 (&v)[4], int lane) {
 
 // One j-tile against the thread's BI i-elements, both sides, U groups of 8 j
 // in flight (unrolled, so one group's reduction overlaps the next group's
-// pairs).  JUNI: the
+// pairs); the first SHR slots share one reciprocal between the two halves of
+// a packed register (as in the one-sided kernel).  JUNI: the
 // tile's elements share G m_j (applied by the caller to the i-side sums);
 // IUNI: the i-block's elements share G m_i (applied to the j-side shares
 // when they are stored); otherwise the mass multiplies every pair.
-template <int TILE, int BI, int U, bool JUNI, bool IUNI>
+template <int TILE, int BI, int U, int SHR, bool JUNI, bool IUNI>
 __device__ __forceinline__ void sym_tile(const JTile<TILE>& tj, const f2 (&xi)[BI],
                                          const f2 (&yi)[BI], const f2 (&zi)[BI],
                                          const f2 (&gmi)[BI], f2 eps2, f2 (&ax)[BI],
@@ -125,7 +126,8 @@ __device__ __forceinline__ void sym_tile(const JTile<TILE>& tj, const f2 (&xi)[B
                 const f2 d2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, floor2)));
                 const f2 r = sqrt2(d2);
                 const f2 t1 = add2(r, eps2);
-                const f2 f = rcp2(mul2(mul2(t1, t1), r));
+                const f2 den = mul2(mul2(t1, t1), r);
+                const f2 f = b < SHR ? rcp2_shared(den) : rcp2(den);
                 const f2 fi = JUNI ? f : mul2(f, pm);
                 ax[b] = fma2(fi, dx, ax[b]);
                 ay[b] = fma2(fi, dy, ay[b]);
@@ -220,7 +222,31 @@ __device__ __forceinline__ void sym_tile_ip(const JTileD<TILE>& tj, const f2 (&x
     }
 }
 
-template <int TILE, int BI, int NT, int MINB, int U, bool IPK>
+// sym_tile for the tile's and the i-block's mass cases
+template <int TILE, int BI, int U, int SHR>
+__device__ __forceinline__ void sym_dispatch(const JTile<TILE>& tj, const f2 (&xi)[BI],
+                                             const f2 (&yi)[BI], const f2 (&zi)[BI],
+                                             const f2 (&gmi)[BI], f2 eps2, f2 (&ax)[BI],
+                                             f2 (&ay)[BI], f2 (&az)[BI], float* row, int lane,
+                                             bool juni, bool iuni) {
+    if (juni) {
+        if (iuni)
+            sym_tile<TILE, BI, U, SHR, true, true>(tj, xi, yi, zi, gmi, eps2, ax, ay, az, row,
+                                                   lane);
+        else
+            sym_tile<TILE, BI, U, SHR, true, false>(tj, xi, yi, zi, gmi, eps2, ax, ay, az, row,
+                                                    lane);
+    } else {
+        if (iuni)
+            sym_tile<TILE, BI, U, SHR, false, true>(tj, xi, yi, zi, gmi, eps2, ax, ay, az, row,
+                                                    lane);
+        else
+            sym_tile<TILE, BI, U, SHR, false, false>(tj, xi, yi, zi, gmi, eps2, ax, ay, az, row,
+                                                     lane);
+    }
+}
+
+template <int TILE, int BI, int NT, int MINB, int U, bool IPK, int SHR>
 __global__ void __launch_bounds__(NT, MINB)
     pair_sym_kernel(PosSoA pj, const float4* __restrict__ jd, const float* __restrict__ tmass,
                     const PairItem* __restrict__ items, int nitems,
@@ -232,6 +258,7 @@ __global__ void __launch_bounds__(NT, MINB)
     constexpr int NP = IPK ? BI / 2 : BI;  // packed i-registers per thread
     static_assert(B % TILE == 0, "a block is a whole number of tiles");
     static_assert(!IPK || BI % 2 == 0, "the i-packed form needs an even slot count");
+    static_assert(SHR >= 0 && SHR <= BI && !(IPK && SHR), "shared reciprocal: j-packed only");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     SymSmem<TILE, BI, NT, IPK>& S = *reinterpret_cast<SymSmem<TILE, BI, NT, IPK>*>(smem_raw);
     __shared__ alignas(8) uint64_t full[kStages];
@@ -371,21 +398,13 @@ __global__ void __launch_bounds__(NT, MINB)
                 }
             } else {
                 if (both) {
-                    if (m > 0.f) {
-                        if (gI > 0.f)
-                            sym_tile<TILE, NP, U, true, true>(tj, xi, yi, zi, gmi, eps2, ax, ay, az,
-                                                              row, lane);
-                        else
-                            sym_tile<TILE, NP, U, true, false>(tj, xi, yi, zi, gmi, eps2, ax, ay,
-                                                               az, row, lane);
-                    } else {
-                        if (gI > 0.f)
-                            sym_tile<TILE, NP, U, false, true>(tj, xi, yi, zi, gmi, eps2, ax, ay,
-                                                               az, row, lane);
-                        else
-                            sym_tile<TILE, NP, U, false, false>(tj, xi, yi, zi, gmi, eps2, ax, ay,
-                                                                az, row, lane);
-                    }
+                    // the shared reciprocal needs eps >= 1e-4 (see rcp2_shared)
+                    if (SHR > 0 && eps >= 1e-4f)
+                        sym_dispatch<TILE, NP, U, SHR>(tj, xi, yi, zi, gmi, eps2, ax, ay, az, row,
+                                                       lane, m > 0.f, gI > 0.f);
+                    else
+                        sym_dispatch<TILE, NP, U, 0>(tj, xi, yi, zi, gmi, eps2, ax, ay, az, row,
+                                                     lane, m > 0.f, gI > 0.f);
                 } else if (m > 0.f) {
                     tile_pairs<TILE, NP, 0, 0, true, false>(tj, xi, yi, zi, eps2, ax, ay, az, ap);
                 } else {
@@ -489,52 +508,52 @@ __global__ void __launch_bounds__(NT, MINB)
     }
 }
 
-template <int TILE, int BI, int NT, int MINB, int U, bool IPK>
+template <int TILE, int BI, int NT, int MINB, int U, bool IPK, int SHR>
 cudaError_t launch_sym_t(const BatchDev& b, const float* tmass, const PairItem* items, int nitems,
                          int grid, int* counter, cudaStream_t s) {
     // the dynamic shared-memory limit was raised by occupancy_sym, which
     // every plan calls before its first launch (and outside graph capture)
     constexpr size_t smem = sizeof(SymSmem<TILE, BI, NT, IPK>);
-    pair_sym_kernel<TILE, BI, NT, MINB, U, IPK><<<grid, NT, smem, s>>>(
+    pair_sym_kernel<TILE, BI, NT, MINB, U, IPK, SHR><<<grid, NT, smem, s>>>(
         b.pj, b.jd, tmass, items, nitems, b.part, b.ntot, b.jpart, b.sc, b.sm, counter);
     return cudaGetLastError();
 }
 
 // raises the kernel's dynamic shared-memory limit, then asks for occupancy
-template <int TILE, int BI, int NT, int MINB, int U, bool IPK>
+template <int TILE, int BI, int NT, int MINB, int U, bool IPK, int SHR>
 int occupancy_sym() {
     constexpr size_t smem = sizeof(SymSmem<TILE, BI, NT, IPK>);
-    if (cudaFuncSetAttribute(pair_sym_kernel<TILE, BI, NT, MINB, U, IPK>,
+    if (cudaFuncSetAttribute(pair_sym_kernel<TILE, BI, NT, MINB, U, IPK, SHR>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return 0;
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_sym_kernel<TILE, BI, NT, MINB, U, IPK>, NT,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_sym_kernel<TILE, BI, NT, MINB, U, IPK, SHR>, NT,
                                                   smem);
     return nb;
 }
 
 }  // namespace
 
-#define NB_SYM_IS(T, B, N, M, U, P)                                                           \
+#define NB_SYM_IS(T, B, N, M, U, P, D)                                                        \
     (c.sym == U && c.tile == T && c.bi == B && c.threads == N && c.minb == M && c.nr == 0 &&  \
-     c.ipk == P && c.shr == 0)
+     c.ipk == P && c.shr == D)
 
 cudaError_t launch_pair_sym(const BatchDev& b, const float* tmass, const PairItem* items,
                             int nitems, const PairCfg& c, int* counter, cudaStream_t s) {
     if (nitems <= 0) return cudaSuccess;
     const int grid = c.grid > 0 ? c.grid : nitems;
-#define NB_LAUNCH_SYM(T, B, N, M, U, P) \
-    if (NB_SYM_IS(T, B, N, M, U, P))    \
-        return launch_sym_t<T, B, N, M, U, P>(b, tmass, items, nitems, grid, counter, s);
+#define NB_LAUNCH_SYM(T, B, N, M, U, P, D) \
+    if (NB_SYM_IS(T, B, N, M, U, P, D))    \
+        return launch_sym_t<T, B, N, M, U, P, D>(b, tmass, items, nitems, grid, counter, s);
     NB_PAIR_SYM_CFGS(NB_LAUNCH_SYM)
 #undef NB_LAUNCH_SYM
     return cudaErrorInvalidValue;
 }
 
 int pair_sym_occupancy(const PairCfg& c) {
-#define NB_OCC_SYM(T, B, N, M, U, P) \
-    if (NB_SYM_IS(T, B, N, M, U, P)) return occupancy_sym<T, B, N, M, U, P>();
+#define NB_OCC_SYM(T, B, N, M, U, P, D) \
+    if (NB_SYM_IS(T, B, N, M, U, P, D)) return occupancy_sym<T, B, N, M, U, P, D>();
     NB_PAIR_SYM_CFGS(NB_OCC_SYM)
 #undef NB_OCC_SYM
     return 0;

@@ -56,7 +56,7 @@ def test_pair_variant_table(lib_path):
     """The variant table is readable without a GPU and every entry respects
     the slot split: Newton-Raphson plus shared-reciprocal slots <= i per
     thread, the shared reciprocal only on the j-packed kernel, and the
-    symmetric kernel without Newton-Raphson or shared reciprocals and with
+    symmetric kernel without Newton-Raphson reciprocals and with
     whole tiles per block."""
     from paper_2303_12166_gb300 import nbody as nbm
     v = nbm.nb_pair_cfg_variants()
@@ -67,7 +67,7 @@ def test_pair_variant_table(lib_path):
         assert nr >= 0 and shr >= 0 and (nr * (2 if ipk else 1) + shr) <= bi
         assert not (ipk and shr)
         if sym:
-            assert nr == shr == 0 and (nt * bi) % tile == 0
+            assert nr == 0 and not (ipk and shr) and (nt * bi) % tile == 0
     with pytest.raises(nbm.NbError) as ei:
         nbm._check(nbm._lib.nb_pair_cfg_variants(None, 1, ctypes.byref(nbm._I32())), "x")
     assert ei.value.status == nbm.NB_EINVAL

@@ -371,7 +371,8 @@ def test_bounded_device_wait_times_out_cleanly(nbm, orc):
     test_forces_binary_1k(nbm, orc, 32, 1e-5)
 
 
-@pytest.mark.parametrize("cfg", [(128, 8, 128, 2, 0, 0, 8), (256, 8, 128, 2, 0, 0, 6)])
+@pytest.mark.parametrize("cfg", [(128, 8, 128, 2, 0, 0, 8), (256, 8, 128, 2, 0, 0, 6),
+                                 (256, 8, 128, 2, 0, 0, 2, 1)])
 def test_shared_reciprocal_falls_back_without_softening(nbm, orc, cfg):
     """With eps < 1e-4 the shared-reciprocal variants use the plain
     reciprocal (the product of two denominators could underflow); the
