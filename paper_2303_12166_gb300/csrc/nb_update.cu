@@ -26,6 +26,16 @@ __device__ __forceinline__ double kick1(double v, double hdt, double a) {
     return __dadd_rn(v, __dmul_rn(hdt, a));
 }
 
+// TwoSum (Knuth) in FP32: hi + lo accumulates x with the rounding error of
+// every addition kept in lo.
+__device__ __forceinline__ void two_sum_f(float& hi, float& lo, float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bp = __fsub_rn(s, hi);
+    const float ap = __fsub_rn(s, bp);
+    lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, ap), __fsub_rn(x, bp)));
+    hi = s;
+}
+
 __device__ __forceinline__ double3 total_acc(const BatchDev& b, const SysConst& c, int64_t i) {
     double ax = 0.0, ay = 0.0, az = 0.0;
     if (c.sym) {
@@ -41,28 +51,39 @@ __device__ __forceinline__ double3 total_acc(const BatchDev& b, const SysConst& 
             ay += p.y;
             az += p.z;
         }
-        // four running sums (blocks I mod 4), added in a fixed order: the
-        // loads of four blocks are in flight at once
+        // Up to ~1,000 FP32 shares per element: summed on the FP32 pipe with
+        // TwoSum (Knuth; the sum carries its exact rounding error in a low
+        // part), four running sums (blocks I mod 4) so that four blocks'
+        // loads are in flight, combined in FP64 in a fixed order.  (FP64
+        // additions here would bound the kernel by GB300's FP64 rate.)
         const int64_t base = c.jp_off + (K * (K - 1) / 2) * B + (rel - K * B);
-        double sx[4] = {0.0, 0.0, 0.0, 0.0}, sy[4] = {0.0, 0.0, 0.0, 0.0},
-               sz[4] = {0.0, 0.0, 0.0, 0.0};
+        float hx[4] = {0.f, 0.f, 0.f, 0.f}, lx[4] = {0.f, 0.f, 0.f, 0.f};
+        float hy[4] = {0.f, 0.f, 0.f, 0.f}, ly[4] = {0.f, 0.f, 0.f, 0.f};
+        float hz[4] = {0.f, 0.f, 0.f, 0.f}, lz[4] = {0.f, 0.f, 0.f, 0.f};
         int64_t I = 0;
         for (; I + 4 <= K; I += 4) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                sx[u] += (double)b.jpart.x[base + (I + u) * B];
-                sy[u] += (double)b.jpart.y[base + (I + u) * B];
-                sz[u] += (double)b.jpart.z[base + (I + u) * B];
+                two_sum_f(hx[u], lx[u], b.jpart.x[base + (I + u) * B]);
+                two_sum_f(hy[u], ly[u], b.jpart.y[base + (I + u) * B]);
+                two_sum_f(hz[u], lz[u], b.jpart.z[base + (I + u) * B]);
             }
         }
         for (int u = 0; I < K; ++I, ++u) {
-            sx[u] += (double)b.jpart.x[base + I * B];
-            sy[u] += (double)b.jpart.y[base + I * B];
-            sz[u] += (double)b.jpart.z[base + I * B];
+            two_sum_f(hx[u], lx[u], b.jpart.x[base + I * B]);
+            two_sum_f(hy[u], ly[u], b.jpart.y[base + I * B]);
+            two_sum_f(hz[u], lz[u], b.jpart.z[base + I * B]);
         }
-        ax += (sx[0] + sx[1]) + (sx[2] + sx[3]);
-        ay += (sy[0] + sy[1]) + (sy[2] + sy[3]);
-        az += (sz[0] + sz[1]) + (sz[2] + sz[3]);
+        double sx = 0.0, sy = 0.0, sz = 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            sx += (double)hx[u] + (double)lx[u];
+            sy += (double)hy[u] + (double)ly[u];
+            sz += (double)hz[u] + (double)lz[u];
+        }
+        ax += sx;
+        ay += sy;
+        az += sz;
     } else {
         for (int ch = 0; ch < c.nchunks; ++ch) {
             const double4_32a p = b.part[(int64_t)ch * b.ntot + i];
