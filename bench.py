@@ -388,6 +388,7 @@ def measure_served(nbm, stream, args):
     srv = nbm.nb_server_create(int(150e9), 64, 262144, 32, stream)
     try:
         info = nbm.nb_server_info(srv)
+        scfg = nbm.nb_server_pair_cfg(srv)
         t0 = time.perf_counter()
         tickets = []
         for r in trace:
@@ -409,6 +410,7 @@ def measure_served(nbm, stream, args):
             "n_range": [4096, 262144],
             "steps_range": [1000 // args.served_steps_div, 20000 // args.served_steps_div],
             "slots": info["nslots"], "failed": len(bad),
+            "pair_cfg": {k: scfg[k] for k in PAIR_CFG_KEYS},
             "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)),
             "makespan_s": span, "value": pairs / span, "unit": "pairs/s",

@@ -360,6 +360,11 @@ nb_status nb_server_create(size_t hbm_budget_bytes, int32_t max_slots, int64_t m
                            int32_t prec, void* stream, nb_server_t* out);
 nb_status nb_server_info(nb_server_t srv, int32_t* nslots, int64_t* slot_n,
                          int64_t* device_bytes);
+/* The pair-kernel configuration the server runs every request with: the
+ * symmetric kernel for slots of at least 16,384 elements (FP32), else the
+ * library's default.  A request's result equals running it alone with this
+ * configuration. */
+nb_status nb_server_pair_cfg(nb_server_t srv, nb_pair_cfg* cfg);
 /* Queue a run of nsteps steps; *ticket identifies it.  The arrays of desc are
  * copied.  NB_EBUDGET if the system is larger than a slot. */
 nb_status nb_submit(nb_server_t srv, const nb_desc* desc, const nb_params* params,

@@ -611,14 +611,18 @@ nb_status Batch::plan_pairs_() {
         const int64_t tpb = B / tile;
         constexpr int64_t kItemsPerSlot = 24;
         constexpr int64_t kMinChunkTiles = 16;
+        constexpr int64_t kMaxRowItems = 16;
         for (int s : act) {
             SysConst& c = sc_[s];
             const int64_t nbk = (c.n + B - 1) / B;
             const int64_t ntiles = (c.n + tile - 1) / tile;
             int64_t toff = 0;
             for (int64_t K = 0; K < nbk; ++K) toff += std::max<int64_t>(0, ntiles - (K + 1) * tpb);
+            // at most kMaxRowItems items per row (partial slots per element)
             const int64_t C = std::max<int64_t>(
-                kMinChunkTiles, (toff + slots * kItemsPerSlot - 1) / (slots * kItemsPerSlot));
+                std::max<int64_t>(kMinChunkTiles,
+                                  (toff + slots * kItemsPerSlot - 1) / (slots * kItemsPerSlot)),
+                (ntiles - tpb + kMaxRowItems - 1) / kMaxRowItems);
             c.sym = 1;
             c.sym_blk = (int32_t)B;
             c.sym_tpb = (int32_t)tpb;

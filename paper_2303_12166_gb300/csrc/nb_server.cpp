@@ -50,17 +50,45 @@ struct Active {
     double t_start = 0;
 };
 
-// Device bytes one element occupies in a slot (arrays of nb_internal.h with
-// `chunks` partial sums, the FP32 copy, the grid arrays at two buckets per
-// element), used to size the slots from the budget.
-size_t bytes_per_element(int chunks) {
+// Device bytes one element occupies in a slot (arrays of nb_internal.h: the
+// FP64 state, the FP32 copies, the grid arrays at two buckets per element)
+// without the pair sums.
+size_t bytes_per_element_base() {
     return 4 * 32      // X, V, A, contact
            + 16        // E
-           + 16        // FP32 copy
+           + 16 + 32   // FP32 copy, duplicated copy
            + 4 + 4 + 8 // owner, key, cell id
-           + 4 + 8 + 16  // sorted index, cell, position
+           + 4 + 8 + 16 + 16 + 16  // sorted index, cell, position, low parts, velocity
            + 2 * 12    // bucket counts, fills, starts
-           + (size_t)32 * chunks;
+           + 24;       // FP32 low parts and velocity copy
+}
+
+// Device bytes of one slot of npad elements with pair configuration c: the
+// base arrays, the partial sums (at most 17 slots per element with the
+// symmetric kernel, a few with the one-sided one) and the symmetric kernel's
+// shares (one FP32 triple per (earlier block, element)).
+size_t slot_bytes(int64_t npad, const nb::PairCfg& c) {
+    size_t bytes = bytes_per_element_base() * (size_t)npad;
+    if (c.sym) {
+        const int64_t B = (int64_t)c.threads * c.bi;
+        const int64_t nbk = (npad + B - 1) / B;
+        bytes += (size_t)17 * 32 * (size_t)npad + (size_t)(nbk * (nbk - 1) / 2) * B * 12;
+    } else {
+        bytes += (size_t)4 * 32 * (size_t)npad;
+    }
+    return bytes;
+}
+
+// The server's pair kernel: the symmetric one (each unordered pair once)
+// for slots of at least 16,384 elements, where it is the faster; otherwise
+// the library's default.  Fixed for the server's life, so a run's result
+// does not depend on the other runs in the batch.
+nb::PairCfg server_pair_cfg(int64_t slot_n, int prec, const nb::PairCfg& dflt) {
+    if (prec == 32 && slot_n >= 16384) {
+        const nb::PairCfg sym{256, 8, 128, 0, 2, 0, 0, 2, 1};
+        if (nb::pair_cfg_supported(sym)) return sym;
+    }
+    return dflt;
 }
 
 }  // namespace
@@ -203,7 +231,8 @@ nb_status nb_server_create(size_t hbm_budget_bytes, int32_t max_slots, int64_t m
                              "nb_server_create: need max_slots >= 1, max_n >= 1, prec 32 or 64");
         *out = nullptr;
         const int64_t npad = (max_n + nb::NB_PAD - 1) / nb::NB_PAD * nb::NB_PAD;
-        const size_t per_slot = bytes_per_element(4) * (size_t)npad;
+        const nb::PairCfg cfg = server_pair_cfg(npad, prec, nb::Batch().pair_cfg());
+        const size_t per_slot = slot_bytes(npad, cfg);
         const int64_t fit = (int64_t)(hbm_budget_bytes / std::max<size_t>(per_slot, 1));
         const int nslots = (int)std::min<int64_t>(max_slots, fit);
         if (nslots < 1)
@@ -220,6 +249,7 @@ nb_status nb_server_create(size_t hbm_budget_bytes, int32_t max_slots, int64_t m
         srv->batch.set_use_graph(true);
         nb_status st = srv->batch.init(std::vector<int64_t>(nslots, npad), prec,
                                        static_cast<cudaStream_t>(stream));
+        if (st == NB_OK) st = srv->batch.set_pair_cfg(cfg);
         if (st != NB_OK) {
             delete srv;
             return st;
@@ -237,6 +267,21 @@ nb_status nb_server_info(nb_server_t srv, int32_t* nslots, int64_t* slot_n, int6
     if (nslots) *nslots = srv->nslots;
     if (slot_n) *slot_n = srv->slot_n;
     if (device_bytes) *device_bytes = srv->batch.device_bytes();
+    return NB_OK;
+}
+
+nb_status nb_server_pair_cfg(nb_server_t srv, nb_pair_cfg* cfg) {
+    if (!srv || !cfg) return set_error(NB_EINVAL, "null argument");
+    const nb::PairCfg& c = srv->batch.pair_cfg();
+    std::memset(cfg, 0, sizeof *cfg);
+    cfg->tile = c.tile;
+    cfg->i_per_thread = c.bi;
+    cfg->threads = c.threads;
+    cfg->min_blocks = c.minb;
+    cfg->nr_slots = c.nr;
+    cfg->i_packed = c.ipk;
+    cfg->shared_rcp = c.shr;
+    cfg->symmetric = c.sym;
     return NB_OK;
 }
 

@@ -136,6 +136,7 @@ _sig("nb_submit", ctypes.c_int, [_P, ctypes.POINTER(nb_desc), ctypes.POINTER(nb_
 _sig("nb_poll", ctypes.c_int, [_P, _U64, ctypes.POINTER(nb_result)])
 _sig("nb_server_drain", ctypes.c_int, [_P, _D])
 _sig("nb_server_clock", _D, [_P])
+_sig("nb_server_pair_cfg", ctypes.c_int, [_P, ctypes.POINTER(nb_pair_cfg)])
 _sig("nb_server_destroy", None, [_P])
 _sig("nb_set_pair_cfg", ctypes.c_int, [_P, ctypes.POINTER(nb_pair_cfg)])
 _sig("nb_get_pair_cfg", ctypes.c_int, [_P, ctypes.POINTER(nb_pair_cfg)])
@@ -531,6 +532,12 @@ def nb_server_info(h) -> dict:
     _check(_lib.nb_server_info(_P(h), ctypes.byref(ns), ctypes.byref(sn), ctypes.byref(db)),
            "nb_server_info")
     return {"nslots": ns.value, "slot_n": sn.value, "device_bytes": db.value}
+
+
+def nb_server_pair_cfg(h) -> dict:
+    c = nb_pair_cfg()
+    _check(_lib.nb_server_pair_cfg(_P(h), ctypes.byref(c)), "nb_server_pair_cfg")
+    return _cfg_dict(c)
 
 
 def nb_submit(h, desc: nb_desc, params: nb_params, nsteps: int, xv_in=None, mrg_in=None) -> int:

@@ -157,3 +157,42 @@ def test_server_budget_and_errors(nbm):
         assert r1["diag"]["e_kin"] == r2["diag"]["e_kin"]
     finally:
         nbm.nb_server_destroy(srv)
+
+
+def test_server_large_slots_use_symmetric_kernel(nbm):
+    """Slots of >= 16,384 elements run the symmetric pair kernel; a run's
+    result equals the run alone with the server's configuration."""
+    import torch
+    stream = torch.cuda.Stream()
+    big = [
+        dict(desc=dict(n_donor=12000, n_accretor=5000, q=0.4, f_donor=0.9, f_accretor=0.5,
+                       sigma_v=1e-3, seed=7), params=dict(eps=0.005, dt=5e-4, beta=0.5)),
+        dict(desc=dict(n_donor=3000, n_accretor=2000, q=0.7, f_donor=0.8, f_accretor=0.5,
+                       expand_rate=1e-3, expand_steps=-1, sigma_v=1e-3, seed=8),
+             params=dict(eps=0.008, dt=5e-4, beta=0.4)),
+    ]
+    srv = nbm.nb_server_create(8 << 30, 2, 17000, 32, stream)
+    try:
+        cfg = nbm.nb_server_pair_cfg(srv)
+        assert cfg["symmetric"] >= 1
+        tickets = [nbm.nb_submit(srv, nbm.nb_desc_default(**b["desc"]),
+                                 nbm.nb_params_default(**b["params"]), 7 + 5 * k)
+                   for k, b in enumerate(big)]
+        nbm.nb_server_drain(srv, 120.0)
+        results = [nbm.nb_poll(srv, t) for t in tickets]
+    finally:
+        nbm.nb_server_destroy(srv)
+    fields = ("tile", "i_per_thread", "threads", "min_blocks", "nr_slots", "i_packed",
+              "shared_rcp", "symmetric")
+    for k, (b, r) in enumerate(zip(big, results)):
+        assert r["status"] == nbm.NB_OK
+        with nbm.System(nbm.nb_desc_default(**b["desc"]), nbm.nb_params_default(**b["params"])) as s:
+            s.set_pair_cfg(*[cfg[f] for f in fields])
+            # a^0 re-evaluated with the server's configuration
+            xv, _, meta = s.get_state()
+            s.set_state(xv, None, meta)
+            s.step(7 + 5 * k)
+            s.sync()
+            d = s.diagnostics()
+        assert r["diag"]["e_kin"] == d["e_kin"]
+        assert np.array_equal(r["diag"]["p"], d["p"]) and np.array_equal(r["diag"]["com"], d["com"])
