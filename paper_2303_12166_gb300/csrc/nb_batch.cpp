@@ -1079,38 +1079,43 @@ nb_status Batch::diagnostics(int s, nb_diag* out, bool energy) {
     return NB_OK;
 }
 
+// Device staging for checkpoints: 9 doubles per element and one check word.
+nb_status Batch::stage_(int64_t n) {
+    if (n <= stage_cap_) return NB_OK;
+    if (stage_d_) {
+        NB_CU(cudaStreamSynchronize(stream_));
+        auto itp = std::find(allocs_.begin(), allocs_.end(), (void*)stage_d_);
+        if (itp != allocs_.end()) allocs_.erase(itp);
+        NB_CU(cudaFreeAsync(stage_d_, stream_));
+        bytes_ -= stage_cap_ * 9 * (int64_t)sizeof(double) + 256;
+    }
+    NB_TRY(alloc_((void**)&stage_d_, (size_t)n * 9 * sizeof(double) + 256));
+    stage_cap_ = n;
+    return NB_OK;
+}
+
+// The state goes through a device staging array in the caller's layout, so
+// the host side is two plain copies (at full link bandwidth when the
+// caller's arrays are page-locked) and no host loop.
 nb_status Batch::get_state(int s, double* xv, double* a, nb_ckpt_meta* meta) {
     if (s < 0 || s >= nslots() || !sc_[s].active) return set_error(NB_ENOTFOUND, "no system %d", s);
     const SysConst& c = sc_[s];
     const int64_t n = c.n;
-    std::vector<double4_32a> X(n), V(n), A(n);
     SysMut m{};
-    NB_CU(cudaMemcpyAsync(X.data(), d_.X + c.off, n * sizeof(double4_32a), cudaMemcpyDeviceToHost,
-                          stream_));
-    NB_CU(cudaMemcpyAsync(V.data(), d_.V + c.off, n * sizeof(double4_32a), cudaMemcpyDeviceToHost,
-                          stream_));
-    if (a)
-        NB_CU(cudaMemcpyAsync(A.data(), d_.A + c.off, n * sizeof(double4_32a),
-                              cudaMemcpyDeviceToHost, stream_));
+    if (xv || a) {
+        NB_TRY(stage_(n));
+        double* sxv = stage_d_;
+        double* sa = stage_d_ + 6 * n;
+        NB_CU(launch_state_pack(d_, c.off, n, sxv, a ? sa : nullptr, stream_));
+        if (xv)
+            NB_CU(cudaMemcpyAsync(xv, sxv, (size_t)n * 6 * sizeof(double),
+                                  cudaMemcpyDeviceToHost, stream_));
+        if (a)
+            NB_CU(cudaMemcpyAsync(a, sa, (size_t)n * 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                                  stream_));
+    }
     NB_CU(cudaMemcpyAsync(&m, d_.sm + s, sizeof m, cudaMemcpyDeviceToHost, stream_));
     NB_CU(cudaStreamSynchronize(stream_));
-    if (xv) {
-        for (int64_t i = 0; i < n; ++i) {
-            xv[6 * i + 0] = X[i].x;
-            xv[6 * i + 1] = X[i].y;
-            xv[6 * i + 2] = X[i].z;
-            xv[6 * i + 3] = V[i].x;
-            xv[6 * i + 4] = V[i].y;
-            xv[6 * i + 5] = V[i].z;
-        }
-    }
-    if (a) {
-        for (int64_t i = 0; i < n; ++i) {
-            a[3 * i + 0] = A[i].x;
-            a[3 * i + 1] = A[i].y;
-            a[3 * i + 2] = A[i].z;
-        }
-    }
     if (meta) {
         meta->n = n;
         meta->step = m.k;
@@ -1127,20 +1132,24 @@ nb_status Batch::set_state(int s, const double* xv, const double* a, const nb_ck
     if (meta->n != n) return set_error(NB_EINVAL, "checkpoint has %lld elements, system %lld",
                                        (long long)meta->n, (long long)n);
     if (meta->step < 0) return set_error(NB_EINVAL, "checkpoint step must be >= 0");
-    std::vector<double4_32a> X(n), V(n), A(a ? n : 0);
-    for (int64_t i = 0; i < n; ++i) {
-        for (int d = 0; d < 6; ++d)
-            if (!std::isfinite(xv[6 * i + d]))
-                return set_error(NB_EINVAL, "xv_in[%lld] is not finite", (long long)i);
-        X[i] = make_double4_32a(xv[6 * i], xv[6 * i + 1], xv[6 * i + 2], mass_[s][i]);
-        V[i] = make_double4_32a(xv[6 * i + 3], xv[6 * i + 4], xv[6 * i + 5], 0.0);
-        if (a) A[i] = make_double4_32a(a[3 * i], a[3 * i + 1], a[3 * i + 2], 0.0);
-    }
+    NB_TRY(stage_(n));
+    double* sxv = stage_d_;
+    double* sa = stage_d_ + 6 * n;
+    unsigned long long* bad = reinterpret_cast<unsigned long long*>(stage_d_ + 9 * n);
+    const unsigned long long none = (unsigned long long)n;
+    NB_CU(cudaMemcpyAsync(sxv, xv, (size_t)n * 6 * sizeof(double), cudaMemcpyHostToDevice,
+                          stream_));
+    if (a)
+        NB_CU(cudaMemcpyAsync(sa, a, (size_t)n * 3 * sizeof(double), cudaMemcpyHostToDevice,
+                              stream_));
+    NB_CU(cudaMemcpyAsync(bad, &none, sizeof none, cudaMemcpyHostToDevice, stream_));
+    NB_CU(launch_state_check(sxv, n, bad, stream_));
+    unsigned long long first_bad = none;
+    NB_CU(cudaMemcpyAsync(&first_bad, bad, sizeof first_bad, cudaMemcpyDeviceToHost, stream_));
     NB_CU(cudaStreamSynchronize(stream_));
-    NB_CU(cudaMemcpyAsync(d_.X + c.off, X.data(), n * sizeof(double4_32a), cudaMemcpyHostToDevice,
-                          stream_));
-    NB_CU(cudaMemcpyAsync(d_.V + c.off, V.data(), n * sizeof(double4_32a), cudaMemcpyHostToDevice,
-                          stream_));
+    if (first_bad < none)
+        return set_error(NB_EINVAL, "xv_in[%llu] is not finite", first_bad);
+    NB_CU(launch_state_unpack(d_, c.off, n, sxv, a ? sa : nullptr, stream_));
     SysMut m{};
     m.k = meta->step;
     NB_CU(cudaMemcpyAsync(d_.sm + s, &m, sizeof m, cudaMemcpyHostToDevice, stream_));
@@ -1149,12 +1158,7 @@ nb_status Batch::set_state(int s, const double* xv, const double* a, const nb_ck
     consts_dirty_ = true;
     NB_TRY(push_consts_());
     NB_CU(launch_shadow(d_, stream_));
-    if (a) {
-        NB_CU(cudaMemcpyAsync(d_.A + c.off, A.data(), n * sizeof(double4_32a),
-                              cudaMemcpyHostToDevice, stream_));
-    } else {
-        NB_TRY(init_acc(s));
-    }
+    if (!a) NB_TRY(init_acc(s));
     NB_CU(cudaStreamSynchronize(stream_));
     return NB_OK;
 }

@@ -139,6 +139,9 @@ private:
     int64_t graph_n_ = -1;
     double* fout_d_ = nullptr;  // staging for forces_out to host
     int64_t fout_cap_ = 0;
+    double* stage_d_ = nullptr;  // checkpoint staging (9 doubles per element) + check word
+    int64_t stage_cap_ = 0;
+    nb_status stage_(int64_t n);
     // profiling
     enum Phase { PH_PAIR = 0, PH_CONTACT = 1, PH_UPDATE = 2 };
     struct ProfMark { cudaEvent_t a, b; int phase; };

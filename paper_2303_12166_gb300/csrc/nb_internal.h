@@ -182,6 +182,15 @@ cudaError_t launch_kick(const BatchDev& b, KickMode mode, bool build_keys, cudaS
 cudaError_t launch_advance(const BatchDev& b, cudaStream_t s);
 // out3: n x 3 doubles, the summed acceleration of system `sys` (n real elements)
 cudaError_t launch_sum_forces(const BatchDev& b, int sys, int64_t n, double* out3, cudaStream_t s);
+// Checkpoint staging of one system (elements [off, off + n)): xv n x 6 and a
+// n x 3 (a may be null), FP64 in caller order, device memory.
+cudaError_t launch_state_pack(const BatchDev& b, int64_t off, int64_t n, double* xv, double* a,
+                              cudaStream_t s);
+// *bad = min(*bad, first index whose xv row is not finite)
+cudaError_t launch_state_check(const double* xv, int64_t n, unsigned long long* bad,
+                               cudaStream_t s);
+cudaError_t launch_state_unpack(const BatchDev& b, int64_t off, int64_t n, const double* xv,
+                                const double* a, cudaStream_t s);
 // A = pair term + contact term for system `only` (-1: all), velocities untouched
 cudaError_t launch_store_acc(const BatchDev& b, int only, cudaStream_t s);
 

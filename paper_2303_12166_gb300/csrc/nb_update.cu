@@ -396,6 +396,77 @@ cudaError_t kick_t(const BatchDev& b, cudaStream_t s, int only = -1) {
 
 }  // namespace
 
+// Checkpoint staging: xv (n x 6) and a (n x 3) in caller order, FP64.
+__global__ void state_pack_kernel(BatchDev b, int64_t off, int64_t n, double* xv, double* a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double4_32a x = b.X[off + i], v = b.V[off + i];
+    double* o = xv + 6 * i;
+    o[0] = x.x;
+    o[1] = x.y;
+    o[2] = x.z;
+    o[3] = v.x;
+    o[4] = v.y;
+    o[5] = v.z;
+    if (a) {
+        const double4_32a q = b.A[off + i];
+        a[3 * i + 0] = q.x;
+        a[3 * i + 1] = q.y;
+        a[3 * i + 2] = q.z;
+    }
+}
+
+// Smallest index of a non-finite value in xv (n x 6), into *bad (set to n
+// beforehand).
+__global__ void state_check_kernel(const double* xv, int64_t n, unsigned long long* bad) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    bool ok = true;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) ok = ok && isfinite(xv[6 * i + d]);
+    if (!ok) atomicMin(bad, (unsigned long long)i);
+}
+
+// Positions, velocities (and a, if given) from the staging arrays; the
+// masses in X.w stay.
+__global__ void state_unpack_kernel(BatchDev b, int64_t off, int64_t n, const double* xv,
+                                    const double* a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double* p = xv + 6 * i;
+    double4_32a x = b.X[off + i];
+    x.x = p[0];
+    x.y = p[1];
+    x.z = p[2];
+    b.X[off + i] = x;
+    b.V[off + i] = make_double4_32a(p[3], p[4], p[5], 0.0);
+    if (a) b.A[off + i] = make_double4_32a(a[3 * i], a[3 * i + 1], a[3 * i + 2], 0.0);
+}
+
+cudaError_t launch_state_pack(const BatchDev& b, int64_t off, int64_t n, double* xv, double* a,
+                              cudaStream_t s) {
+    const int nt = 256;
+    const unsigned ng = (unsigned)((n + nt - 1) / nt);
+    if (ng) state_pack_kernel<<<ng, nt, 0, s>>>(b, off, n, xv, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_state_check(const double* xv, int64_t n, unsigned long long* bad,
+                               cudaStream_t s) {
+    const int nt = 256;
+    const unsigned ng = (unsigned)((n + nt - 1) / nt);
+    if (ng) state_check_kernel<<<ng, nt, 0, s>>>(xv, n, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_state_unpack(const BatchDev& b, int64_t off, int64_t n, const double* xv,
+                                const double* a, cudaStream_t s) {
+    const int nt = 256;
+    const unsigned ng = (unsigned)((n + nt - 1) / nt);
+    if (ng) state_unpack_kernel<<<ng, nt, 0, s>>>(b, off, n, xv, a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_shadow(const BatchDev& b, cudaStream_t s) {
     const int nt = 256;
     const unsigned ng = (unsigned)((b.ntot + nt - 1) / nt);

@@ -297,11 +297,21 @@ def nb_diagnostics(h) -> dict:
     return _diag_dict(d)
 
 
-def nb_get_state(h, with_acc: bool = True):
-    """Returns (xv (n,6), a (n,3) or None, meta)."""
+def nb_get_state(h, with_acc: bool = True, out=None):
+    """Returns (xv (n,6), a (n,3) or None, meta).  ``out`` = (xv, a): caller
+    arrays (C-contiguous float64, e.g. views of page-locked memory) to fill
+    instead of new ones."""
     n = nb_get_info(h).n
-    xv = np.empty((n, 6), dtype=np.float64)
-    a = np.empty((n, 3), dtype=np.float64) if with_acc else None
+    if out is not None:
+        xv, a = out
+        if xv.shape != (n, 6) or xv.dtype != np.float64 or not xv.flags.c_contiguous:
+            raise ValueError("out xv must be a C-contiguous float64 (n, 6) array")
+        if a is not None and (a.shape != (n, 3) or a.dtype != np.float64 or
+                              not a.flags.c_contiguous):
+            raise ValueError("out a must be a C-contiguous float64 (n, 3) array")
+    else:
+        xv = np.empty((n, 6), dtype=np.float64)
+        a = np.empty((n, 3), dtype=np.float64) if with_acc else None
     meta = nb_ckpt_meta()
     _check(_lib.nb_get_state(_P(h), xv.ctypes.data_as(_P),
                              a.ctypes.data_as(_P) if a is not None else None,
@@ -610,8 +620,8 @@ class System:
     def diagnostics(self) -> dict:
         return nb_diagnostics(self.h)
 
-    def get_state(self, with_acc: bool = True):
-        return nb_get_state(self.h, with_acc)
+    def get_state(self, with_acc: bool = True, out=None):
+        return nb_get_state(self.h, with_acc, out)
 
     def set_state(self, xv, a, meta):
         nb_set_state(self.h, xv, a, meta)

@@ -256,6 +256,29 @@ def test_checkpoint_resume_bitwise(nbm):
     assert np.array_equal(x_ref, x2) and np.array_equal(v_ref, v2) and np.array_equal(a_ref, a2)
 
 
+def test_set_state_rejects_nonfinite_and_keeps_state(nbm):
+    """A checkpoint with a non-finite value is refused (NB_EINVAL naming the
+    first bad row) and the system's state is left as it was; page-locked
+    output arrays are filled in place."""
+    import torch
+    desc, params = workload_kwargs("binary_1k")
+    with _make(nbm, desc, params) as s:
+        s.step(3)
+        xv, a, meta = s.get_state()
+        bad = xv.copy()
+        bad[700, 4] = np.nan
+        bad[900, 0] = np.inf
+        with pytest.raises(nbm.NbError) as ei:
+            s.set_state(bad, a, meta)
+        assert ei.value.status == nbm.NB_EINVAL and "xv_in[700]" in str(ei.value)
+        n = s.n
+        pxv = torch.empty((n, 6), dtype=torch.float64, pin_memory=True).numpy()
+        pa = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+        _, _, meta2 = s.get_state(out=(pxv, pa))
+        assert meta2.step == 3
+        assert np.array_equal(pxv, xv) and np.array_equal(pa, a)
+
+
 def test_steps_split_across_calls_bitwise(nbm):
     desc, params = workload_kwargs("binary_1k")
     with _make(nbm, desc, params) as s:
