@@ -284,7 +284,7 @@ void Batch::release_() {
     }
     if (!allocs_.empty()) {
         cudaStreamSynchronize(stream_);
-        for (void* p : allocs_) cudaFreeAsync(p, stream_);
+        for (auto& a : allocs_) cudaFreeAsync(a.first, stream_);
         cudaStreamSynchronize(stream_);
         allocs_.clear();
     }
@@ -296,8 +296,24 @@ nb_status Batch::alloc_(void** p, size_t bytes) {
     bytes = (bytes + 255) & ~size_t(255);
     NB_CU(cudaMallocAsync(p, bytes, stream_));
     NB_CU(cudaMemsetAsync(*p, 0, bytes, stream_));
-    allocs_.push_back(*p);
+    allocs_.emplace_back(*p, bytes);
     bytes_ += (int64_t)bytes;
+    return NB_OK;
+}
+
+nb_status Batch::free_(void** p) {
+    if (!*p) return NB_OK;
+    NB_CU(cudaStreamSynchronize(stream_));
+    for (auto it = allocs_.begin(); it != allocs_.end(); ++it) {
+        if (it->first == *p) {
+            bytes_ -= (int64_t)it->second;
+            allocs_.erase(it);
+            break;
+        }
+    }
+    const cudaError_t e = cudaFreeAsync(*p, stream_);
+    *p = nullptr;
+    NB_CU(e);
     return NB_OK;
 }
 
@@ -580,12 +596,8 @@ nb_status Batch::plan_pairs_() {
             }
         }
         if (ntiles_all > tmass_cap_) {
-            if (tmass_d_) {
-                NB_CU(cudaStreamSynchronize(stream_));
-                auto itp = std::find(allocs_.begin(), allocs_.end(), (void*)tmass_d_);
-                if (itp != allocs_.end()) allocs_.erase(itp);
-                NB_CU(cudaFreeAsync(tmass_d_, stream_));
-            }
+            tmass_cap_ = 0;
+            NB_TRY(free_((void**)&tmass_d_));
             NB_TRY(alloc_((void**)&tmass_d_, (size_t)ntiles_all * sizeof(float)));
             tmass_cap_ = ntiles_all;
         }
@@ -657,27 +669,32 @@ nb_status Batch::plan_pairs_() {
         if (maxslots > NB_MAX_CHUNKS * 4)
             return set_error(NB_EINVAL, "symmetric pair plan needs %d partial slots", maxslots);
     }
+    {
+        // room for the buffers this plan grows (checked before anything is
+        // freed, so a plan that does not fit leaves the batch as it was)
+        size_t need = 0, have = 0;
+        if (maxslots > d_.nchunk_alloc)
+            need += (size_t)(maxslots - d_.nchunk_alloc) * d_.ntot * sizeof(double4_32a);
+        if (jp_total > jpart_cap_) need += 3 * (size_t)(jp_total - jpart_cap_) * sizeof(float);
+        size_t total = 0;
+        if (need > 0 && cudaMemGetInfo(&have, &total) == cudaSuccess && need + (64u << 20) > have)
+            return set_error(NB_ENOMEM,
+                             "pair plan needs %.2f GB more device memory, %.2f GB free",
+                             need / 1e9, have / 1e9);
+    }
     if (maxslots > d_.nchunk_alloc) {
         // grow the partial-sum buffer (chunk-major)
-        if (d_.part) {
-            NB_CU(cudaStreamSynchronize(stream_));
-            auto itp = std::find(allocs_.begin(), allocs_.end(), (void*)d_.part);
-            if (itp != allocs_.end()) allocs_.erase(itp);
-            NB_CU(cudaFreeAsync(d_.part, stream_));
-            bytes_ -= (int64_t)d_.nchunk_alloc * d_.ntot * (int64_t)sizeof(double4_32a);
-        }
+        d_.nchunk_alloc = 0;
+        NB_TRY(free_((void**)&d_.part));
         NB_TRY(alloc_((void**)&d_.part, (size_t)maxslots * d_.ntot * sizeof(double4_32a)));
         d_.nchunk_alloc = maxslots;
     }
     if (jp_total > jpart_cap_) {
         // j-side shares of the symmetric plan: three component arrays
-        if (d_.jpart.x) {
-            NB_CU(cudaStreamSynchronize(stream_));
-            auto itp = std::find(allocs_.begin(), allocs_.end(), (void*)d_.jpart.x);
-            if (itp != allocs_.end()) allocs_.erase(itp);
-            NB_CU(cudaFreeAsync(d_.jpart.x, stream_));
-            bytes_ -= 3 * jpart_cap_ * (int64_t)sizeof(float);
-        }
+        jpart_cap_ = 0;
+        float* old = d_.jpart.x;
+        d_.jpart = Vec3SoA{};
+        NB_TRY(free_((void**)&old));
         float* base = nullptr;
         NB_TRY(alloc_((void**)&base, 3 * (size_t)jp_total * sizeof(float)));
         d_.jpart = Vec3SoA{base, base + jp_total, base + 2 * jp_total};
@@ -685,14 +702,11 @@ nb_status Batch::plan_pairs_() {
     }
     auto upload = [&](const std::vector<PairItem>& v, PairItem*& dptr, int& cap) -> nb_status {
         if ((int)v.size() > cap) {
-            if (dptr) {
-                NB_CU(cudaStreamSynchronize(stream_));
-                auto itp = std::find(allocs_.begin(), allocs_.end(), (void*)dptr);
-                if (itp != allocs_.end()) allocs_.erase(itp);
-                NB_CU(cudaFreeAsync(dptr, stream_));
-            }
-            cap = std::max<int>(64, (int)v.size());
-            NB_TRY(alloc_((void**)&dptr, (size_t)cap * sizeof(PairItem)));
+            cap = 0;
+            NB_TRY(free_((void**)&dptr));
+            const int want = std::max<int>(64, (int)v.size());
+            NB_TRY(alloc_((void**)&dptr, (size_t)want * sizeof(PairItem)));
+            cap = want;
         }
         if (!v.empty())
             NB_CU(cudaMemcpyAsync(dptr, v.data(), v.size() * sizeof(PairItem),
@@ -825,7 +839,14 @@ nb_status Batch::autotune(int reps, PairCfg* best, double* best_ms) {
         if (pair_occupancy(c) < 1) continue;
         cfg_ = c;
         planned_ = false;
-        if ((st = plan_pairs_()) != NB_OK) break;
+        if ((st = plan_pairs_()) != NB_OK) {
+            // a variant whose buffers do not fit is skipped
+            if (st == NB_ENOMEM) {
+                st = NB_OK;
+                continue;
+            }
+            break;
+        }
         // time about two waves of the persistent grid (items are equal-sized
         // within a system), normalised per pair interaction
         const std::vector<PairItem>& list = cfg_.sym ? sitems_ : items_;
@@ -1018,12 +1039,8 @@ nb_status Batch::forces_out(int s, double* out, bool out_on_device) {
         return sync();
     }
     if (fout_cap_ < n) {
-        if (fout_d_) {
-            NB_CU(cudaStreamSynchronize(stream_));
-            auto itp = std::find(allocs_.begin(), allocs_.end(), (void*)fout_d_);
-            if (itp != allocs_.end()) allocs_.erase(itp);
-            NB_CU(cudaFreeAsync(fout_d_, stream_));
-        }
+        fout_cap_ = 0;
+        NB_TRY(free_((void**)&fout_d_));
         NB_TRY(alloc_((void**)&fout_d_, (size_t)n * 3 * sizeof(double)));
         fout_cap_ = n;
     }
@@ -1082,13 +1099,8 @@ nb_status Batch::diagnostics(int s, nb_diag* out, bool energy) {
 // Device staging for checkpoints: 9 doubles per element and one check word.
 nb_status Batch::stage_(int64_t n) {
     if (n <= stage_cap_) return NB_OK;
-    if (stage_d_) {
-        NB_CU(cudaStreamSynchronize(stream_));
-        auto itp = std::find(allocs_.begin(), allocs_.end(), (void*)stage_d_);
-        if (itp != allocs_.end()) allocs_.erase(itp);
-        NB_CU(cudaFreeAsync(stage_d_, stream_));
-        bytes_ -= stage_cap_ * 9 * (int64_t)sizeof(double) + 256;
-    }
+    stage_cap_ = 0;
+    NB_TRY(free_((void**)&stage_d_));
     NB_TRY(alloc_((void**)&stage_d_, (size_t)n * 9 * sizeof(double) + 256));
     stage_cap_ = n;
     return NB_OK;

@@ -6,6 +6,7 @@
 #pragma once
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "nb_internal.h"
@@ -102,6 +103,8 @@ public:
 
 private:
     nb_status alloc_(void** p, size_t bytes);
+    // free one allocation made by alloc_ (after the stream drains); p = null
+    nb_status free_(void** p);
     nb_status push_consts_();
     nb_status plan_pairs_();
     nb_status launch_pairs_(bool pot, int nitems_limit = -1);
@@ -133,7 +136,7 @@ private:
     bool planned_ = false;
     bool consts_dirty_ = true;
     int64_t bytes_ = 0;
-    std::vector<void*> allocs_;
+    std::vector<std::pair<void*, size_t>> allocs_;  // live device allocations and sizes
     bool use_graph_ = false;
     cudaGraphExec_t graph_exec_ = nullptr;
     int64_t graph_n_ = -1;
