@@ -334,6 +334,7 @@ nb_status Batch::init(const std::vector<int64_t>& n_per_slot, int prec, cudaStre
     sc_.assign(nsys, SysConst{});
     k_.assign(nsys, 0);
     mass_.assign(nsys, {});
+    runs_.assign(nsys, {});
     rmax_d0_.assign(nsys, 0.0);
     rmax_a_.assign(nsys, 0.0);
     int64_t off = 0;
@@ -445,6 +446,14 @@ nb_status Batch::load(int s, const SystemInit& si, bool defer_forces) {
     if (!(rd > 0 || ra > 0)) c.contacts = 0;  // no element has a radius
     k_[s] = 0;
     mass_[s] = si.m;
+    runs_[s].clear();
+    for (int64_t i = 0; i < si.n;) {
+        const float g = (float)(si.G * si.m[i]);
+        int64_t j = i + 1;
+        while (j < si.n && (float)(si.G * si.m[j]) == g) ++j;
+        if (g > 0.f) runs_[s].push_back(MassRun{i, j, g});
+        i = j;
+    }
 
     // host staging (pageable: cudaMemcpyAsync returns after the copy-out)
     const int64_t n = si.n, npad = c.npad;
@@ -585,14 +594,12 @@ nb_status Batch::plan_pairs_() {
         std::vector<float> tm(ntiles_all, -1.f);
         for (int s : act) {
             const SysConst& c = sc_[s];
-            const std::vector<double>& m = mass_[s];
-            for (int64_t t0 = 0; t0 < c.n; t0 += tile) {
-                if (t0 + tile > c.n) break;  // padded last tile
-                const float g0 = (float)(c.G * m[t0]);
-                bool same = g0 > 0.f;
-                for (int64_t j = t0 + 1; same && j < t0 + tile; ++j)
-                    same = (float)(c.G * m[j]) == g0;
-                if (same) tm[(c.off + t0) / tile] = g0;
+            const std::vector<MassRun>& runs = runs_[s];
+            size_t r = 0;
+            for (int64_t t0 = 0; t0 + tile <= c.n; t0 += tile) {  // padded last tile: per pair
+                while (r < runs.size() && runs[r].end <= t0) ++r;
+                if (r < runs.size() && runs[r].begin <= t0 && t0 + tile <= runs[r].end)
+                    tm[(c.off + t0) / tile] = runs[r].g;
             }
         }
         if (ntiles_all > tmass_cap_) {
@@ -939,6 +946,24 @@ nb_status Batch::init_acc_subset(const std::vector<int>& slots) {
     planned_ = false;
     consts_dirty_ = true;
     nb_status st = init_acc(-1);
+    for (int s = 0; s < nslots(); ++s) sc_[s].active = was[s];
+    planned_ = false;
+    consts_dirty_ = true;
+    if (st != NB_OK) return st;
+    return push_consts_();
+}
+
+nb_status Batch::step_subset(const std::vector<int>& slots, int64_t n) {
+    std::vector<int32_t> was(nslots());
+    for (int s = 0; s < nslots(); ++s) {
+        was[s] = sc_[s].active;
+        sc_[s].active = 0;
+    }
+    for (int s : slots)
+        if (s >= 0 && s < nslots()) sc_[s].active = was[s];
+    planned_ = false;
+    consts_dirty_ = true;
+    nb_status st = step(n);
     for (int s = 0; s < nslots(); ++s) sc_[s].active = was[s];
     planned_ = false;
     consts_dirty_ = true;

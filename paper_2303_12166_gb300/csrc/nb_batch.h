@@ -71,6 +71,9 @@ public:
     // a^k of the listed (active) systems only: the others sit out the force
     // evaluation and keep their state
     nb_status init_acc_subset(const std::vector<int>& slots);
+    // n steps of the listed (active) systems only; the others keep their
+    // state and step count
+    nb_status step_subset(const std::vector<int>& slots, int64_t n);
 
     nb_status sync();                 // wait + report device-side flags
     nb_status forces_out(int s, double* out, bool out_on_device);
@@ -119,6 +122,13 @@ private:
     std::vector<SysConst> sc_;
     std::vector<int64_t> k_;
     std::vector<std::vector<double>> mass_;  // host copy of element masses
+    // maximal runs of elements with the same FP32 G m (> 0), per slot: the
+    // plan's per-tile common mass in O(runs + tiles)
+    struct MassRun {
+        int64_t begin, end;
+        float g;
+    };
+    std::vector<std::vector<MassRun>> runs_;
     std::vector<double> rmax_d0_, rmax_a_;
     PairCfg cfg_{128, 4, 256, 0, 2, 1, 0, 0, 0};
     float* tmass_d_ = nullptr;   // per j-tile common G m (see launch_pair_f32)

@@ -4,14 +4,17 @@
 // memory budget allows).  Requests (a system description, parameters and a
 // step count) queue in arrival order; whenever slots are free the thread
 // admits queued requests -- builds their initial state, loads it into free
-// slots and evaluates their initial acceleration -- and then advances every
-// active system together by a chunk of steps: one persistent pair-kernel
+// slots and evaluates their initial acceleration -- and then advances a set
+// of active systems together by a chunk of steps: one persistent pair-kernel
 // launch, one contact pass and one update per step for all of them, replayed
-// from a CUDA graph while the set of active systems is unchanged.  The chunk
-// ends at the next completion, so a finished run is retired (its final
-// diagnostics recorded, its slot freed) without waiting for the others, and
-// requests that arrived meanwhile are admitted at once.  State stays on the
-// device for the whole run.
+// from a CUDA graph.  The set is chosen shortest remaining work first (n^2 x
+// steps left), adding runs until a step holds enough pair interactions to
+// fill the GPU: short requests do not wait on every step of long ones, and
+// the device stays busy.  The chunk ends at the next completion in the set,
+// so a finished run is retired (its final diagnostics recorded, its slot
+// freed) without waiting for the others, and requests that arrived
+// meanwhile are admitted at once.  State stays on the device for the whole
+// run.
 //
 // A system's trajectory does not depend on what else shares the batch or on
 // how its steps are chunked (see nb_batch.cpp), so each result equals the
@@ -83,6 +86,10 @@ size_t slot_bytes(int64_t npad, const nb::PairCfg& c) {
 // for slots of at least 16,384 elements, where it is the faster; otherwise
 // the library's default.  Fixed for the server's life, so a run's result
 // does not depend on the other runs in the batch.
+// Pair interactions per step the server gathers before it stops adding runs
+// to a step (about a millisecond of the pair kernel on one GB300).
+constexpr double kMinPairsPerStep = 4e9;
+
 nb::PairCfg server_pair_cfg(int64_t slot_n, int prec, const nb::PairCfg& dflt) {
     if (prec == 32 && slot_n >= 16384) {
         const nb::PairCfg sym{256, 8, 128, 0, 2, 0, 0, 2, 1};
@@ -175,16 +182,34 @@ void nb_server::run() {
                 return;
             }
         }
-        // ---- step every active system to the next completion (or a tick)
-        int64_t chunk = tick_steps;
-        bool any = false;
+        // ---- advance the runs with the least remaining work (n^2 x steps
+        // left) first, taking runs in that order until one step holds at
+        // least kMinPairsPerStep pair interactions (enough to fill the GPU),
+        // to the next completion among them (or a tick): shortest remaining
+        // work first keeps short requests from waiting on every step of the
+        // long ones, the minimum keeps the device busy
+        std::vector<int> act;
         for (int s = 0; s < nslots; ++s)
-            if (slot_used[s] && batch.active(s)) {
-                any = true;
-                chunk = std::min(chunk, active[s].req.nsteps - active[s].done);
-            }
-        if (!any) continue;
-        nb_status st = chunk > 0 ? batch.step(chunk) : NB_OK;
+            if (slot_used[s] && batch.active(s)) act.push_back(s);
+        if (act.empty()) continue;
+        auto work_left = [&](int s) {
+            const double n = (double)batch.n_of(s);
+            return n * n * (double)(active[s].req.nsteps - active[s].done);
+        };
+        std::stable_sort(act.begin(), act.end(),
+                         [&](int a, int b) { return work_left(a) < work_left(b); });
+        std::vector<int> run;
+        double pairs_per_step = 0;
+        for (int s : act) {
+            run.push_back(s);
+            pairs_per_step += (double)batch.n_of(s) * (double)batch.n_of(s);
+            if (pairs_per_step >= kMinPairsPerStep) break;
+        }
+        int64_t chunk = tick_steps;
+        for (int s : run) chunk = std::min(chunk, active[s].req.nsteps - active[s].done);
+        nb_status st = NB_OK;
+        if (chunk > 0)
+            st = run.size() == act.size() ? batch.step(chunk) : batch.step_subset(run, chunk);
         std::vector<nb::SysMut> flags;
         if (st == NB_OK) st = batch.read_flags(flags);
         if (st != NB_OK) {
@@ -193,9 +218,11 @@ void nb_server::run() {
             fatal_msg = nb::last_error();
             return;
         }
+        std::vector<char> stepped(nslots, 0);
+        for (int s : run) stepped[s] = 1;
         // ---- retire finished (or failed) runs
         for (int s = 0; s < nslots; ++s) {
-            if (!slot_used[s] || !batch.active(s)) continue;
+            if (!slot_used[s] || !batch.active(s) || !stepped[s]) continue;
             Active& a = active[s];
             a.done += chunk;
             nb_status rs = NB_OK;

@@ -196,3 +196,39 @@ def test_server_large_slots_use_symmetric_kernel(nbm):
             d = s.diagnostics()
         assert r["diag"]["e_kin"] == d["e_kin"]
         assert np.array_equal(r["diag"]["p"], d["p"]) and np.array_equal(r["diag"]["com"], d["com"])
+
+
+def test_server_shortest_work_first_keeps_results(nbm):
+    """Two runs large enough to fill a step each: once both are admitted the
+    one with less work left runs alone and the other waits; both results
+    equal the runs alone (paused and resumed steps are bitwise invisible)."""
+    import torch
+    stream = torch.cuda.Stream()
+    big = dict(n_donor=50000, n_accretor=16000, q=0.3, f_donor=0.9, f_accretor=0.5,
+               sigma_v=1e-3, seed=11)
+    p = dict(eps=0.005, dt=5e-4, beta=0.5)
+    srv = nbm.nb_server_create(16 << 30, 2, 66000, 32, stream)
+    try:
+        cfg = nbm.nb_server_pair_cfg(srv)
+        t_long = nbm.nb_submit(srv, nbm.nb_desc_default(**big), nbm.nb_params_default(**p), 150)
+        t_short = nbm.nb_submit(srv, nbm.nb_desc_default(**dict(big, seed=12)),
+                                nbm.nb_params_default(**p), 6)
+        nbm.nb_server_drain(srv, 300.0)
+        r_long, r_short = nbm.nb_poll(srv, t_long), nbm.nb_poll(srv, t_short)
+    finally:
+        nbm.nb_server_destroy(srv)
+    assert r_long["status"] == r_short["status"] == nbm.NB_OK
+    assert r_short["t_finish"] < r_long["t_finish"]
+    fields = ("tile", "i_per_thread", "threads", "min_blocks", "nr_slots", "i_packed",
+              "shared_rcp", "symmetric")
+    for desc, steps, r in [(big, 150, r_long), (dict(big, seed=12), 6, r_short)]:
+        with nbm.System(nbm.nb_desc_default(**desc), nbm.nb_params_default(**p)) as s:
+            s.set_pair_cfg(*[cfg[f] for f in fields])
+            xv, _, meta = s.get_state()
+            s.set_state(xv, None, meta)
+            s.step(steps)
+            s.sync()
+            d = s.diagnostics()
+        assert r["steps"] == steps and r["diag"]["step"] == steps
+        assert r["diag"]["e_kin"] == d["e_kin"]
+        assert np.array_equal(r["diag"]["com"], d["com"])
