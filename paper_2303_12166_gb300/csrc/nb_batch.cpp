@@ -935,7 +935,8 @@ nb_status Batch::store_acc(int only) {
     return NB_OK;
 }
 
-nb_status Batch::init_acc_subset(const std::vector<int>& slots) {
+template <class F>
+nb_status Batch::with_subset_(const std::vector<int>& slots, F f) {
     std::vector<int32_t> was(nslots());
     for (int s = 0; s < nslots(); ++s) {
         was[s] = sc_[s].active;
@@ -945,30 +946,21 @@ nb_status Batch::init_acc_subset(const std::vector<int>& slots) {
         if (s >= 0 && s < nslots()) sc_[s].active = was[s];
     planned_ = false;
     consts_dirty_ = true;
-    nb_status st = init_acc(-1);
+    nb_status st = f();
     for (int s = 0; s < nslots(); ++s) sc_[s].active = was[s];
     planned_ = false;
     consts_dirty_ = true;
-    if (st != NB_OK) return st;
-    return push_consts_();
+    // the restored flags are copied after the launches above (stream order)
+    nb_status st2 = push_consts_();
+    return st != NB_OK ? st : st2;
+}
+
+nb_status Batch::init_acc_subset(const std::vector<int>& slots) {
+    return with_subset_(slots, [&] { return init_acc(-1); });
 }
 
 nb_status Batch::step_subset(const std::vector<int>& slots, int64_t n) {
-    std::vector<int32_t> was(nslots());
-    for (int s = 0; s < nslots(); ++s) {
-        was[s] = sc_[s].active;
-        sc_[s].active = 0;
-    }
-    for (int s : slots)
-        if (s >= 0 && s < nslots()) sc_[s].active = was[s];
-    planned_ = false;
-    consts_dirty_ = true;
-    nb_status st = step(n);
-    for (int s = 0; s < nslots(); ++s) sc_[s].active = was[s];
-    planned_ = false;
-    consts_dirty_ = true;
-    if (st != NB_OK) return st;
-    return push_consts_();
+    return with_subset_(slots, [&] { return step(n); });
 }
 
 nb_status Batch::init_acc(int only) {

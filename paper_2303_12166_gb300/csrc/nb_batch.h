@@ -119,7 +119,7 @@ private:
     int prec_ = 32;
     cudaStream_t stream_ = nullptr;
     BatchDev d_{};
-    std::vector<SysConst> sc_;
+    std::vector<SysConst> sc_;       // sc_[s].active: stepped by the next launches
     std::vector<int64_t> k_;
     std::vector<std::vector<double>> mass_;  // host copy of element masses
     // maximal runs of elements with the same FP32 G m (> 0), per slot: the
@@ -170,6 +170,10 @@ private:
     nb_status prof_collect_();
     bool any_contacts_() const;
     nb_status contact_pass_(int kofs, bool energy, bool with_keys);
+    // run f with only the listed slots active (flags restored afterwards;
+    // the work plan is rebuilt for the subset and again after it)
+    template <class F>
+    nb_status with_subset_(const std::vector<int>& slots, F f);
 };
 
 }  // namespace nb

@@ -87,8 +87,8 @@ size_t slot_bytes(int64_t npad, const nb::PairCfg& c) {
 // the library's default.  Fixed for the server's life, so a run's result
 // does not depend on the other runs in the batch.
 // Pair interactions per step the server gathers before it stops adding runs
-// to a step (about a millisecond of the pair kernel on one GB300).
-constexpr double kMinPairsPerStep = 4e9;
+// to a step (about 3 ms of the pair kernel on one GB300).
+constexpr double kMinPairsPerStep = 1e10;
 
 nb::PairCfg server_pair_cfg(int64_t slot_n, int prec, const nb::PairCfg& dflt) {
     if (prec == 32 && slot_n >= 16384) {

@@ -204,10 +204,10 @@ def test_server_shortest_work_first_keeps_results(nbm):
     equal the runs alone (paused and resumed steps are bitwise invisible)."""
     import torch
     stream = torch.cuda.Stream()
-    big = dict(n_donor=50000, n_accretor=16000, q=0.3, f_donor=0.9, f_accretor=0.5,
+    big = dict(n_donor=82000, n_accretor=28000, q=0.3, f_donor=0.9, f_accretor=0.5,
                sigma_v=1e-3, seed=11)
     p = dict(eps=0.005, dt=5e-4, beta=0.5)
-    srv = nbm.nb_server_create(16 << 30, 2, 66000, 32, stream)
+    srv = nbm.nb_server_create(16 << 30, 2, 110000, 32, stream)
     try:
         cfg = nbm.nb_server_pair_cfg(srv)
         t_long = nbm.nb_submit(srv, nbm.nb_desc_default(**big), nbm.nb_params_default(**p), 150)
