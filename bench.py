@@ -85,12 +85,17 @@ PAIR_SOURCES = ("nb_pair_common.cuh", "nb_pair.cu", "nb_pair_sym.cu")
 
 
 def pair_sources_sha():
-    """Hash of the pair kernels' sources (the traffic record is void once it changes)."""
+    """Hash of the pair kernels' sources with comments and whitespace
+    removed (the traffic record is void once the code changes)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in PAIR_SOURCES:
-        with open(os.path.join(ROOT, "paper_2303_12166_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2303_12166_gb300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -95,10 +95,10 @@ __device__ __forceinline__ float warp_reduce8(const f2 (&v)[4], int lane) {
 // One j-tile against the thread's BI i-elements, both sides, U groups of 8 j
 // in flight (unrolled, so one group's reduction overlaps the next group's
 // pairs); the first SHR slots share one reciprocal between the two halves of
-// a packed register (as in the one-sided kernel).  JUNI: the
-// tile's elements share G m_j (applied by the caller to the i-side sums);
-// IUNI: the i-block's elements share G m_i (applied to the j-side shares
-// when they are stored); otherwise the mass multiplies every pair.
+// a packed register (as in the one-sided kernel).  JUNI: the tile's elements
+// share G m_j (applied by the caller to the i-side sums); IUNI: the i-block's
+// elements share G m_i (applied to the j-side shares when they are stored);
+// otherwise the mass multiplies every pair.
 template <int TILE, int BI, int U, int SHR, bool JUNI, bool IUNI>
 __device__ __forceinline__ void sym_tile(const JTile<TILE>& tj, const f2 (&xi)[BI],
                                          const f2 (&yi)[BI], const f2 (&zi)[BI],
