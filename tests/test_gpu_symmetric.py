@@ -203,3 +203,51 @@ def test_symmetric_full_size_sampled(nbm, orc, name, nrows):
     ref = orc.forces_rows(rows, ox, ov, om, oR, og, G=1.0, eps=params["eps"],
                           beta=params["beta"])
     assert rms_rel(a[rows], ref) <= 1e-5
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 1023, 1024, 1025, 2047, 2048, 2049, 3071, 3073])
+def test_symmetric_block_boundaries(nbm, orc, n):
+    """Sizes around whole blocks of 1,024 (ragged last block, one element
+    past a block, a single block), per-element masses and contacts."""
+    s, (x, v, m, R, gam) = _cloud_system(nbm, n, 500 + n, contacts=True)
+    with s:
+        s.set_pair_cfg(256, 8, 128, 2, 0, 0, 2, 1)
+        a = s.forces()
+    if n == 1:
+        assert np.all(a == 0.0)
+        return
+    ref = orc.forces(x, v, m, R, gam, G=1.0, eps=0.003, beta=0.35)
+    assert rms_rel(a, ref) <= 1e-5
+    assert np.abs(a - ref).max() <= 5e-4 * np.abs(ref).max()
+
+
+def test_symmetric_tiny_and_large_systems_in_one_batch(nbm):
+    """Systems of 1, 3, 257 and 5,000 elements with the symmetric kernel:
+    each bitwise equal to itself alone."""
+    import torch
+    systems = [
+        (dict(n_donor=1, n_accretor=0, q=0.5, f_donor=0.8, f_accretor=0.5, seed=21),
+         dict(eps=0.01, dt=1e-3, beta=0.5)),
+        (dict(n_donor=2, n_accretor=1, q=0.5, f_donor=0.8, f_accretor=0.5, seed=22),
+         dict(eps=0.01, dt=1e-3, beta=0.5)),
+        (dict(n_donor=200, n_accretor=57, q=0.6, f_donor=0.8, f_accretor=0.5, seed=23),
+         dict(eps=0.006, dt=5e-4, beta=0.4)),
+        (dict(n_donor=3600, n_accretor=1400, q=0.3, f_donor=0.9, f_accretor=0.5, seed=24),
+         dict(eps=0.005, dt=5e-4, beta=0.5)),
+    ]
+    cfg = (256, 8, 128, 2, 0, 0, 2, 1)
+    descs = [nbm.nb_desc_default(**d) for d, _ in systems]
+    params = [nbm.nb_params_default(**p) for _, p in systems]
+    with nbm.Batch(descs, params, stream=torch.cuda.Stream()) as b:
+        b.set_pair_cfg(*cfg)
+        b.step(4)
+        b.sync()
+        mixed = [b.get_state(s) for s in range(len(systems))]
+    for s, (d, p) in enumerate(systems):
+        with _make(nbm, d, p) as one:
+            one.set_pair_cfg(*cfg)
+            one.step(4)
+            one.sync()
+            xv, a, _ = one.get_state()
+        assert np.array_equal(mixed[s][0], xv), f"system {s}: state differs"
+        assert np.array_equal(mixed[s][1], a), f"system {s}: accelerations differ"
