@@ -251,3 +251,23 @@ def test_symmetric_tiny_and_large_systems_in_one_batch(nbm):
             xv, a, _ = one.get_state()
         assert np.array_equal(mixed[s][0], xv), f"system {s}: state differs"
         assert np.array_equal(mixed[s][1], a), f"system {s}: accelerations differ"
+
+
+@pytest.mark.parametrize("name,nrows", [("binary_64k", 256), ("binary_1m", 128)])
+def test_full_size_in_the_tuned_configuration(nbm, orc, name, nrows):
+    """At the benchmark's sizes, in the pair configuration the tuner picks
+    (the launch configuration the benchmark times): sampled rows against
+    the oracle."""
+    desc, params = workload_kwargs(name)
+    with _make(nbm, desc, params) as s:
+        best = s.autotune(2)
+        a = s.forces()
+        n = s.n
+    ox, ov, om, oR, og = oracle_ic(orc, desc, params)
+    nd = desc["n_donor"]
+    rows = np.unique(np.concatenate([
+        [0, 1, 1023, 1024, nd - 1, nd, nd + 1, n - 1],
+        (synth.u01(13, 9, nrows) * n).astype(np.int64)]))
+    ref = orc.forces_rows(rows, ox, ov, om, oR, og, G=1.0, eps=params["eps"],
+                          beta=params["beta"])
+    assert rms_rel(a[rows], ref) <= 1e-5, f"tuned configuration {best}"
