@@ -38,6 +38,14 @@
 // The i-side TwoSum accumulators live in shared memory (touched once per
 // tile), which leaves the registers to the pair arithmetic.
 //
+// Rotating form (symmetric configuration value 3): instead of a reduction,
+// the warp walks the tile in groups of 64 j; lane l starts on j-pair l of the
+// group and at step s evaluates j-pair (l + s) mod 32 (positions read from
+// shared memory at that index), then takes the j-side sums that lane l + 1
+// holds -- those of the pair it evaluates next.  A pair's sums visit every
+// lane once, so after 32 steps each lane holds the warp's sums of one
+// j-pair: 6 shuffles per lane per step instead of a reduction tree.
+//
 // i-packed form (IPK): a packed register holds two i-elements of the thread
 // against one j (the duplicated j-stream ((x,x,y,y),(z,z,Gm,Gm)) of the
 // one-sided i-packed kernel), which halves the registers that hold the
@@ -222,27 +230,99 @@ __device__ __forceinline__ void sym_tile_ip(const JTileD<TILE>& tj, const f2 (&x
     }
 }
 
-// sym_tile for the tile's and the i-block's mass cases
+// The rotating form of sym_tile (see the header).
+template <int TILE, int BI, int SHR, bool JUNI, bool IUNI>
+__device__ __forceinline__ void sym_tile_rot(const JTile<TILE>& tj, const f2 (&xi)[BI],
+                                             const f2 (&yi)[BI], const f2 (&zi)[BI],
+                                             const f2 (&gmi)[BI], f2 eps2, f2 (&ax)[BI],
+                                             f2 (&ay)[BI], f2 (&az)[BI], float* row, int lane) {
+    static_assert(TILE % 64 == 0, "the rotating form walks groups of 64 j");
+    const f2 floor2 = pk(kD2Floor, kD2Floor);
+    const int next = (lane + 1) & 31;
+#pragma unroll 1
+    for (int g = 0; g < TILE; g += 64) {
+        f2 sx = 0ull, sy = 0ull, sz = 0ull;  // j-side sums of the pair this lane holds
+#pragma unroll 4
+        for (int s = 0; s < 32; ++s) {
+            const int j = g + 2 * ((lane + s) & 31);
+            const f2 px = *reinterpret_cast<const f2*>(&tj.x[j]);
+            const f2 py = *reinterpret_cast<const f2*>(&tj.y[j]);
+            const f2 pz = *reinterpret_cast<const f2*>(&tj.z[j]);
+            f2 pm = 0;
+            if (!JUNI) pm = *reinterpret_cast<const f2*>(&tj.m[j]);
+#pragma unroll
+            for (int b = 0; b < BI; ++b) {
+                const f2 dx = sub2(px, xi[b]);
+                const f2 dy = sub2(py, yi[b]);
+                const f2 dz = sub2(pz, zi[b]);
+                const f2 d2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, floor2)));
+                const f2 r = sqrt2(d2);
+                const f2 t1 = add2(r, eps2);
+                const f2 den = mul2(mul2(t1, t1), r);
+                const f2 f = b < SHR ? rcp2_shared(den) : rcp2(den);
+                const f2 fi = JUNI ? f : mul2(f, pm);
+                ax[b] = fma2(fi, dx, ax[b]);
+                ay[b] = fma2(fi, dy, ay[b]);
+                az[b] = fma2(fi, dz, az[b]);
+                const f2 fj = IUNI ? f : mul2(f, gmi[b]);
+                sx = fma2(fj, dx, sx);
+                sy = fma2(fj, dy, sy);
+                sz = fma2(fj, dz, sz);
+            }
+            if (s < 31) {  // take the sums of the pair evaluated next
+                sx = __shfl_sync(0xffffffffu, sx, next);
+                sy = __shfl_sync(0xffffffffu, sy, next);
+                sz = __shfl_sync(0xffffffffu, sz, next);
+            }
+        }
+        // the sums now held are those of j-pair (lane + 31) mod 32
+        const int j = g + 2 * ((lane + 31) & 31);
+        *reinterpret_cast<f2*>(&row[0 * (TILE + kRowPad) + j]) = sx;
+        *reinterpret_cast<f2*>(&row[1 * (TILE + kRowPad) + j]) = sy;
+        *reinterpret_cast<f2*>(&row[2 * (TILE + kRowPad) + j]) = sz;
+    }
+}
+
+// sym_tile (U = 1, 2) or sym_tile_rot (U = 3) for the tile's and the
+// i-block's mass cases
 template <int TILE, int BI, int U, int SHR>
 __device__ __forceinline__ void sym_dispatch(const JTile<TILE>& tj, const f2 (&xi)[BI],
                                              const f2 (&yi)[BI], const f2 (&zi)[BI],
                                              const f2 (&gmi)[BI], f2 eps2, f2 (&ax)[BI],
                                              f2 (&ay)[BI], f2 (&az)[BI], float* row, int lane,
                                              bool juni, bool iuni) {
-    if (juni) {
-        if (iuni)
-            sym_tile<TILE, BI, U, SHR, true, true>(tj, xi, yi, zi, gmi, eps2, ax, ay, az, row,
-                                                   lane);
-        else
-            sym_tile<TILE, BI, U, SHR, true, false>(tj, xi, yi, zi, gmi, eps2, ax, ay, az, row,
-                                                    lane);
+    if constexpr (U == 3) {
+        if (juni) {
+            if (iuni)
+                sym_tile_rot<TILE, BI, SHR, true, true>(tj, xi, yi, zi, gmi, eps2, ax, ay, az,
+                                                        row, lane);
+            else
+                sym_tile_rot<TILE, BI, SHR, true, false>(tj, xi, yi, zi, gmi, eps2, ax, ay, az,
+                                                         row, lane);
+        } else {
+            if (iuni)
+                sym_tile_rot<TILE, BI, SHR, false, true>(tj, xi, yi, zi, gmi, eps2, ax, ay, az,
+                                                         row, lane);
+            else
+                sym_tile_rot<TILE, BI, SHR, false, false>(tj, xi, yi, zi, gmi, eps2, ax, ay,
+                                                          az, row, lane);
+        }
     } else {
-        if (iuni)
-            sym_tile<TILE, BI, U, SHR, false, true>(tj, xi, yi, zi, gmi, eps2, ax, ay, az, row,
-                                                    lane);
-        else
-            sym_tile<TILE, BI, U, SHR, false, false>(tj, xi, yi, zi, gmi, eps2, ax, ay, az, row,
-                                                     lane);
+        if (juni) {
+            if (iuni)
+                sym_tile<TILE, BI, U, SHR, true, true>(tj, xi, yi, zi, gmi, eps2, ax, ay, az,
+                                                       row, lane);
+            else
+                sym_tile<TILE, BI, U, SHR, true, false>(tj, xi, yi, zi, gmi, eps2, ax, ay, az,
+                                                        row, lane);
+        } else {
+            if (iuni)
+                sym_tile<TILE, BI, U, SHR, false, true>(tj, xi, yi, zi, gmi, eps2, ax, ay, az,
+                                                        row, lane);
+            else
+                sym_tile<TILE, BI, U, SHR, false, false>(tj, xi, yi, zi, gmi, eps2, ax, ay, az,
+                                                         row, lane);
+        }
     }
 }
 
