@@ -92,7 +92,7 @@ constexpr double kMinPairsPerStep = 1e10;
 
 nb::PairCfg server_pair_cfg(int64_t slot_n, int prec, const nb::PairCfg& dflt) {
     if (prec == 32 && slot_n >= 16384) {
-        const nb::PairCfg sym{256, 8, 128, 0, 2, 0, 0, 2, 1};
+        const nb::PairCfg sym{256, 12, 128, 0, 2, 0, 0, 2, 3};
         if (nb::pair_cfg_supported(sym)) return sym;
     }
     return dflt;
