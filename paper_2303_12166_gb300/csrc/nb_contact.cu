@@ -296,13 +296,16 @@ __global__ void __launch_bounds__(128) contact_kernel(BatchDev b, int kofs, uint
                 const uint32_t beg = b.start[key];
                 const uint32_t end = beg + b.cnt[key];
                 for (uint32_t slot = beg; slot < end; ++slot) {
-                    if (b.scell[slot] != cell) continue;  // hash collision
                     const float4 pj = b.spos[slot];
                     const float dxh = pj.x - pi4.x, dyh = pj.y - pi4.y, dzh = pj.z - pi4.z;
                     // pre-test on the hi parts; the margin covers their rounding
                     // (2^-24 relative per coordinate) and that of the radii
                     const float tol = (Rif + pj.w) * 1.0001f + 2.5e-7f * (mi + max_abs3(pj));
                     if (dxh * dxh + dyh * dyh + dzh * dzh > tol * tol) continue;
+                    // another cell hashed to this bucket (checked after the distance
+                    // test, which rejects most candidates: a colliding cell's
+                    // elements would otherwise be visited twice)
+                    if (b.scell[slot] != cell) continue;
                     const float4 vj4 = b.svel[slot];
                     if (__float_as_int(vj4.w) != s) continue;  // another system
                     const uint32_t j = b.sorted[slot];
