@@ -61,17 +61,25 @@ PAIR_CFG_KEYS = ("tile", "i_per_thread", "threads", "min_blocks", "nr_slots", "i
                  "shared_rcp", "symmetric")
 
 
-def pairs_per_sm_clk(symmetric: bool = False):
+def pairs_per_sm_clk(symmetric: bool = False, rates=None):
     """Pair interactions per clock per SM at the best split x of shared
-    reciprocals: max over x in [0, 1] of min(FP32 rate / FP32 ops, MUFU rate /
-    MUFU ops) per evaluation, times the interactions one evaluation serves."""
+    reciprocals: max over x in [0, 1] of 1 / max(FP32 time, MUFU time) per
+    evaluation, times the interactions one evaluation serves.  rates: issue
+    rates per clock per SM (measured: unit_rates_per_clk), else the nominal
+    128 FP32 lanes and 16 MUFU results."""
+    fp32_rate = rates["fp32_lanes_per_clk_sm"] if rates else FP32_PER_SM_CLK
+    sqrt_rate = rates["mufu_sqrt_per_clk_sm"] if rates else MUFU_PER_SM_CLK
+    rcp_rate = rates["mufu_rcp_per_clk_sm"] if rates else MUFU_PER_SM_CLK
     fp32 = FP32_PER_PAIR_SYM if symmetric else FP32_PER_PAIR
-    x = (MUFU_PER_PAIR * FP32_PER_SM_CLK / MUFU_PER_SM_CLK - fp32) / (
-        SHARED_RCP_FP32 + SHARED_RCP_MUFU * FP32_PER_SM_CLK / MUFU_PER_SM_CLK)
-    x = min(max(x, 0.0), 1.0)
-    per_eval = min(FP32_PER_SM_CLK / (fp32 + SHARED_RCP_FP32 * x),
-                   MUFU_PER_SM_CLK / (MUFU_PER_PAIR - SHARED_RCP_MUFU * x))
-    return (2.0 if symmetric else 1.0) * per_eval, x
+    best, x_best = 0.0, 0.0
+    for k in range(1001):
+        x = k / 1000.0
+        t_fp32 = (fp32 + SHARED_RCP_FP32 * x) / fp32_rate
+        t_mufu = 1.0 / sqrt_rate + (1.0 - SHARED_RCP_MUFU * x) / rcp_rate
+        per_eval = 1.0 / max(t_fp32, t_mufu)
+        if per_eval > best:
+            best, x_best = per_eval, x
+    return (2.0 if symmetric else 1.0) * best, x_best
 
 
 def _dist():
@@ -493,7 +501,21 @@ def run_ours(args):
     peaks, peak_src = _measured_peaks()
     sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     sym = bool(tuned.get("symmetric", 0)) and not args.fp64
-    ppc, x_opt = pairs_per_sm_clk(sym)
+    clocks = clk.summary()
+    rates = None
+    try:
+        # the pipes' issue rates, measured on this device now (per second per
+        # SM), per clock at the SM clock sampled during the timed steps
+        r = nbm.nb_measure_unit_rates(stream)
+        mhz = clocks["sm_mhz"] if clocks and clocks.get("sm_mhz") == clocks.get("sm_mhz") \
+            else sm_max_mhz
+        rates = {"sm_mhz": mhz,
+                 "fp32_lanes_per_clk_sm": r["fp32_lanes_per_s_sm"] / (mhz * 1e6),
+                 "mufu_sqrt_per_clk_sm": r["mufu_sqrt_per_s_sm"] / (mhz * 1e6),
+                 "mufu_rcp_per_clk_sm": r["mufu_rcp_per_s_sm"] / (mhz * 1e6)}
+    except nbm.NbError:
+        rates = None
+    ppc, x_opt = pairs_per_sm_clk(sym, rates)
     peak_pairs = props.multi_processor_count * sm_max_mhz * 1e6 * ppc
     pair_ms = prof["pair_ms"] / max(prof["pair_launches"], 1)
     achieved = pairs_step / (pair_ms * 1e-3)
@@ -549,12 +571,18 @@ def run_ours(args):
                          "traffic": None if args.fp64 else _pair_traffic(args.workload, tuned),
                          "peak_basis": f"{props.multi_processor_count} SMs x {sm_max_mhz:.0f} MHz "
                                        f"({peak_src} sm_max_mhz) x {ppc:.3f} pairs/clk/SM: "
-                                       f"{FP32_PER_SM_CLK} FP32 lanes and {MUFU_PER_SM_CLK} MUFU "
-                                       f"per clk per SM, "
-                                       f"{FP32_PER_PAIR_SYM if sym else FP32_PER_PAIR:g} FP32 + "
+                                       + (f"{rates['fp32_lanes_per_clk_sm']:.1f} FP32 lanes, "
+                                          f"{rates['mufu_sqrt_per_clk_sm']:.2f} MUFU sqrt and "
+                                          f"{rates['mufu_rcp_per_clk_sm']:.2f} MUFU rcp per clk "
+                                          f"per SM measured in this run"
+                                          if rates else
+                                          f"{FP32_PER_SM_CLK} FP32 lanes and {MUFU_PER_SM_CLK} MUFU "
+                                          f"per clk per SM (nominal)")
+                                       + f"; {FP32_PER_PAIR_SYM if sym else FP32_PER_PAIR:g} FP32 + "
                                        f"{MUFU_PER_PAIR:g} MUFU per evaluation, "
                                        f"{'2 interactions (i and j sides)' if sym else '1 interaction'}"
                                        f" per evaluation, a fraction {x_opt:.3f} of reciprocals shared",
+                         "unit_rates": rates,
                          "kernel": "pair_sym_kernel" if sym else "pair_f32_kernel",
                          "kernel_ms": pair_ms},
             "cpu_baseline": cpu,
@@ -562,7 +590,7 @@ def run_ours(args):
             "gpu_launches": int(prof["kernels"]),
             "phase_ms": {"pair": prof["pair_ms"], "contact": prof["contact_ms"],
                          "update": prof["update_ms"]},
-            "clocks": clk.summary(),
+            "clocks": clocks,
             "batched": batched,
             "served": served,
             "fp64_path": fp64_path,

@@ -277,6 +277,21 @@ nb_status nb_set_state(nb_system_t sys, const double* xv_in, const double* a_in,
  * NULL) receives it.  Results are cached per element count and precision
  * for the life of the process.  The state is not changed. */
 nb_status nb_autotune(nb_system_t sys, int reps, nb_pair_cfg* best);
+/* Issue rates of the pipes that bound the pair kernels, measured on the
+ * current device at the clock it runs at (an implementation aid of this
+ * library; the paper has no counterpart): MUFU square roots and
+ * reciprocals, and FP32 lanes of packed FMA, per second per SM (one wave of
+ * resident blocks timed with CUDA events, best of three).  Divide by the SM
+ * clock for per-clock rates.  Runs for ~20 ms on `stream`, blocks until
+ * done. */
+typedef struct {
+    int32_t sm_count;
+    double mufu_sqrt_per_s_sm;
+    double mufu_rcp_per_s_sm;
+    double fp32_lanes_per_s_sm;
+} nb_unit_rates;
+nb_status nb_measure_unit_rates(nb_unit_rates* out, void* stream);
+
 /* Select a pair-kernel variant; it must be one of nb_pair_cfg_variants'
  * (NB_EINVAL otherwise).  The field ms is ignored. */
 nb_status nb_set_pair_cfg(nb_system_t sys, const nb_pair_cfg* cfg);

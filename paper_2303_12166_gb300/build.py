@@ -19,7 +19,8 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libnbody.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["nb_pair.cu", "nb_pair_sym.cu", "nb_contact.cu", "nb_update.cu", "nb_noalloc.cu"]
+CU_SOURCES = ["nb_pair.cu", "nb_pair_sym.cu", "nb_contact.cu", "nb_update.cu", "nb_noalloc.cu",
+              "nb_probe.cu"]
 CPP_SOURCES = ["nb_batch.cpp", "nb_api.cpp", "nb_server.cpp"]
 
 

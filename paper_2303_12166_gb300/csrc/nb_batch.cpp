@@ -26,21 +26,6 @@ nb_status set_error(nb_status s, const char* fmt, ...) {
 
 const char* last_error() { return t_err.c_str(); }
 
-#define NB_CU(call)                                                                          \
-    do {                                                                                     \
-        cudaError_t e_ = (call);                                                             \
-        if (e_ != cudaSuccess)                                                               \
-            return set_error(e_ == cudaErrorMemoryAllocation ? NB_ENOMEM : NB_ECUDA,         \
-                             "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
-                             __LINE__);                                                      \
-    } while (0)
-
-#define NB_TRY(call)                     \
-    do {                                 \
-        nb_status s_ = (call);           \
-        if (s_ != NB_OK) return s_;      \
-    } while (0)
-
 // ------------------------------------------------------------------ model setup
 namespace {
 

@@ -18,6 +18,24 @@ namespace nb {
 nb_status set_error(nb_status s, const char* fmt, ...);
 const char* last_error();
 
+// Return the library status of a failed CUDA call (with its text), or of a
+// failed library call, from the enclosing function.
+#define NB_CU(call)                                                                          \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return set_error(e_ == cudaErrorMemoryAllocation ? NB_ENOMEM : NB_ECUDA,         \
+                             "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                             __LINE__);                                                      \
+    } while (0)
+
+#define NB_TRY(call)                     \
+    do {                                 \
+        nb_status s_ = (call);           \
+        if (s_ != NB_OK) return s_;      \
+    } while (0)
+
+
 // Host description of one system, ready for upload.
 struct SystemInit {
     int64_t n = 0, n_donor = 0;

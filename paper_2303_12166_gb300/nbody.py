@@ -79,6 +79,11 @@ class nb_result(ctypes.Structure):
                 ("t_submit", _D), ("t_start", _D), ("t_finish", _D), ("diag", nb_diag)]
 
 
+class nb_unit_rates(ctypes.Structure):
+    _fields_ = [("sm_count", _I32), ("mufu_sqrt_per_s_sm", _D), ("mufu_rcp_per_s_sm", _D),
+                ("fp32_lanes_per_s_sm", _D)]
+
+
 class nb_info(ctypes.Structure):
     _fields_ = [("n", _I64), ("n_donor", _I64), ("n_accretor", _I64), ("m_donor", _D),
                 ("m_accretor", _D), ("r_donor0", _D), ("r_accretor", _D),
@@ -137,6 +142,7 @@ _sig("nb_poll", ctypes.c_int, [_P, _U64, ctypes.POINTER(nb_result)])
 _sig("nb_server_drain", ctypes.c_int, [_P, _D])
 _sig("nb_server_clock", _D, [_P])
 _sig("nb_server_pair_cfg", ctypes.c_int, [_P, ctypes.POINTER(nb_pair_cfg)])
+_sig("nb_measure_unit_rates", ctypes.c_int, [ctypes.POINTER(nb_unit_rates), _P])
 _sig("nb_server_destroy", None, [_P])
 _sig("nb_set_pair_cfg", ctypes.c_int, [_P, ctypes.POINTER(nb_pair_cfg)])
 _sig("nb_get_pair_cfg", ctypes.c_int, [_P, ctypes.POINTER(nb_pair_cfg)])
@@ -349,6 +355,14 @@ def nb_get_pair_cfg(h) -> dict:
     c = nb_pair_cfg()
     _check(_lib.nb_get_pair_cfg(_P(h), ctypes.byref(c)), "nb_get_pair_cfg")
     return _cfg_dict(c)
+
+
+def nb_measure_unit_rates(stream=None) -> dict:
+    """MUFU and FP32 issue rates per SM per second on the current device."""
+    r = nb_unit_rates()
+    _check(_lib.nb_measure_unit_rates(ctypes.byref(r), _stream_ptr(stream)),
+           "nb_measure_unit_rates")
+    return {name: getattr(r, name) for name, _ in nb_unit_rates._fields_}
 
 
 PAIR_CFG_FIELDS = ("tile", "i_per_thread", "threads", "min_blocks", "nr_slots", "i_packed",

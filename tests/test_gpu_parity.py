@@ -411,3 +411,18 @@ def test_shared_reciprocal_falls_back_without_softening(nbm, orc, cfg):
         a = s.forces()
     ref = orc.forces(x, v, m, np.zeros(n), np.zeros(n), G=1.0, eps=0.0)
     assert rms_rel(a, ref) <= 1e-5
+
+
+def test_unit_rate_probe(nbm):
+    """The measured issue rates behind the roofline are those of a
+    Blackwell SM at its clock: 16 MUFU results and 128 FP32 lanes per clock
+    (per second here, so bounded with the clock range of the part)."""
+    import torch
+    r = nbm.nb_measure_unit_rates(torch.cuda.Stream())
+    assert r["sm_count"] == torch.cuda.get_device_properties(0).multi_processor_count
+    for k in ("mufu_sqrt_per_s_sm", "mufu_rcp_per_s_sm"):
+        assert 12.0 * 1.0e9 <= r[k] <= 17.0 * 2.2e9, r
+    assert 96.0 * 1.0e9 <= r["fp32_lanes_per_s_sm"] <= 130.0 * 2.2e9, r
+    # the two MUFU operations and the FP32 lanes keep the SM's 1 : 8 ratio
+    ratio = r["fp32_lanes_per_s_sm"] / r["mufu_rcp_per_s_sm"]
+    assert 7.0 <= ratio <= 9.0, r
