@@ -13,7 +13,7 @@
  * force sum for particle i runs over j = 0..n-1 in that fixed order, so the
  * result does not depend on the OpenMP thread count.
  *
- * Readings of the paper that this file takes (each is listed in the design doc):
+ * Readings of the paper that this file takes (the library takes the same):
  *   - Eq. 3 is used with the coefficient as a parameter; the printed value
  *     is 0.69 (Eggleton's published fit uses 0.6).
  *   - Eq. 2 is garbled in the text; the normalised Roche potential used here

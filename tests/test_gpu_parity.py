@@ -1,6 +1,8 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI.
 
-Tolerances (from the arithmetic):
+Tolerances (from the arithmetic: FP32 coordinates relative to the system's
+reference point carry ~3e-8 relative rounding, the MUFU square root and
+reciprocal ~1 ulp, tile sums of <= 256 terms are compensated across tiles):
   * FP32 pair term: per-step accelerations within 1e-5 RMS-relative.
   * FP64 pair term: within 1e-12 RMS-relative (summation order only).
   * 100 steps of the 1,024-element binary: positions within 1e-4 (max abs).
