@@ -614,8 +614,8 @@ nb_status Batch::plan_pairs_() {
         const int64_t B = I;
         const int64_t tpb = B / tile;
         constexpr int64_t kItemsPerSlot = 24;
-        constexpr int64_t kMinChunkTiles = 16;
-        constexpr int64_t kMaxRowItems = 16;
+        constexpr int64_t kMinChunkTiles = 4;
+        constexpr int64_t kMaxRowItems = 64;
         for (int s : act) {
             SysConst& c = sc_[s];
             const int64_t nbk = (c.n + B - 1) / B;

@@ -67,7 +67,7 @@ size_t bytes_per_element_base() {
 }
 
 // Device bytes of one slot of npad elements with pair configuration c: the
-// base arrays, the partial sums (at most 17 slots per element with the
+// base arrays, the partial sums (at most 65 slots per element with the
 // symmetric kernel, a few with the one-sided one) and the symmetric kernel's
 // shares (one FP32 triple per (earlier block, element)).
 size_t slot_bytes(int64_t npad, const nb::PairCfg& c) {
@@ -75,7 +75,7 @@ size_t slot_bytes(int64_t npad, const nb::PairCfg& c) {
     if (c.sym) {
         const int64_t B = (int64_t)c.threads * c.bi;
         const int64_t nbk = (npad + B - 1) / B;
-        bytes += (size_t)17 * 32 * (size_t)npad + (size_t)(nbk * (nbk - 1) / 2) * B * 12;
+        bytes += (size_t)65 * 32 * (size_t)npad + (size_t)(nbk * (nbk - 1) / 2) * B * 12;
     } else {
         bytes += (size_t)4 * 32 * (size_t)npad;
     }
