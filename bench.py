@@ -89,7 +89,8 @@ def _dist():
     return ws, rank, local
 
 
-PAIR_SOURCES = ("nb_pair_common.cuh", "nb_pair.cu", "nb_pair_sym.cu")
+# the pair kernels and the plan that cuts their work into items
+PAIR_SOURCES = ("nb_pair_common.cuh", "nb_pair.cu", "nb_pair_sym.cu", "nb_batch.cpp")
 
 
 def pair_sources_sha():
