@@ -293,7 +293,12 @@ typedef struct {
 nb_status nb_measure_unit_rates(nb_unit_rates* out, void* stream);
 
 /* Select a pair-kernel variant; it must be one of nb_pair_cfg_variants'
- * (NB_EINVAL otherwise).  The field ms is ignored. */
+ * (NB_EINVAL otherwise).  The field ms is ignored.  Until a variant is
+ * selected (or tuned), a system runs the symmetric kernel with rotating
+ * shares (tile 256, 12 i-elements per thread, 2 shared-reciprocal slots),
+ * or the one-sided kernel (tile 256, 8 i-elements, 6 shared-reciprocal
+ * slots) when the symmetric kernel's O(N^2 / 1536) share buffers do not
+ * fit in device memory. */
 nb_status nb_set_pair_cfg(nb_system_t sys, const nb_pair_cfg* cfg);
 nb_status nb_get_pair_cfg(nb_system_t sys, nb_pair_cfg* cfg);
 /* The built pair-kernel variants (an implementation detail of this library;
@@ -376,9 +381,10 @@ nb_status nb_server_create(size_t hbm_budget_bytes, int32_t max_slots, int64_t m
 nb_status nb_server_info(nb_server_t srv, int32_t* nslots, int64_t* slot_n,
                          int64_t* device_bytes);
 /* The pair-kernel configuration the server runs every request with: the
- * symmetric kernel for slots of at least 16,384 elements (FP32), else the
- * library's default.  A request's result equals running it alone with this
- * configuration. */
+ * symmetric kernel (rotating shares, 12 i-elements per thread) for slots of
+ * at least 16,384 elements (FP32), else the one-sided kernel (tile 256, 8
+ * i-elements per thread, 6 shared-reciprocal slots).  A request's result
+ * equals running it alone with this configuration. */
 nb_status nb_server_pair_cfg(nb_server_t srv, nb_pair_cfg* cfg);
 /* Queue a run of nsteps steps; *ticket identifies it.  The arrays of desc are
  * copied.  NB_EBUDGET if the system is larger than a slot. */

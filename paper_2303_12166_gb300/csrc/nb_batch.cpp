@@ -497,6 +497,7 @@ nb_status Batch::set_pair_cfg(const PairCfg& c) {
                          "pair configuration tile=%d bi=%d threads=%d minb=%d nr=%d not built",
                          c.tile, c.bi, c.threads, c.minb, c.nr);
     cfg_ = c;
+    cfg_explicit_ = true;
     planned_ = false;
     return NB_OK;
 }
@@ -669,10 +670,16 @@ nb_status Batch::plan_pairs_() {
             need += (size_t)(maxslots - d_.nchunk_alloc) * d_.ntot * sizeof(double4_32a);
         if (jp_total > jpart_cap_) need += 3 * (size_t)(jp_total - jpart_cap_) * sizeof(float);
         size_t total = 0;
-        if (need > 0 && cudaMemGetInfo(&have, &total) == cudaSuccess && need + (64u << 20) > have)
+        if (need > 0 && cudaMemGetInfo(&have, &total) == cudaSuccess && need + (64u << 20) > have) {
+            if (f32 && cfg_.sym && !cfg_explicit_) {
+                // the default symmetric plan does not fit: one-sided instead
+                cfg_ = kOneSided;
+                return plan_pairs_();
+            }
             return set_error(NB_ENOMEM,
                              "pair plan needs %.2f GB more device memory, %.2f GB free",
                              need / 1e9, have / 1e9);
+        }
     }
     if (maxslots > d_.nchunk_alloc) {
         // grow the partial-sum buffer (chunk-major)
@@ -868,6 +875,7 @@ nb_status Batch::autotune(int reps, PairCfg* best, double* best_ms) {
     kernels_ = 0;
     pairs_done_ = 0;
     cfg_ = st == NB_OK ? best_c : keep;
+    if (st == NB_OK) cfg_explicit_ = true;
     planned_ = false;
     if (st != NB_OK) return st;
     NB_TRY(plan_pairs_());

@@ -14,6 +14,10 @@
 
 namespace nb {
 
+// The one-sided configuration used where the symmetric kernel's buffers do
+// not fit (best one-sided variant: 6 of 8 slots share a reciprocal).
+constexpr PairCfg kOneSided{256, 8, 128, 0, 2, 0, 0, 6, 0};
+
 // Thread-local error text behind nb_last_error().
 nb_status set_error(nb_status s, const char* fmt, ...);
 const char* last_error();
@@ -148,7 +152,12 @@ private:
     };
     std::vector<std::vector<MassRun>> runs_;
     std::vector<double> rmax_d0_, rmax_a_;
-    PairCfg cfg_{128, 4, 256, 0, 2, 1, 0, 0, 0};
+    // default: the symmetric kernel with rotating shares (12 i-elements per
+    // thread, 2 shared-reciprocal slots); while the caller has not chosen a
+    // configuration, a plan whose share buffers do not fit falls back to the
+    // one-sided kOneSided (O(N) memory)
+    PairCfg cfg_{256, 12, 128, 0, 2, 0, 0, 2, 3};
+    bool cfg_explicit_ = false;
     float* tmass_d_ = nullptr;   // per j-tile common G m (see launch_pair_f32)
     int64_t tmass_cap_ = 0;
     std::vector<PairItem> items_;      // one-sided work list (also the potential pass)

@@ -67,15 +67,21 @@ size_t bytes_per_element_base() {
 }
 
 // Device bytes of one slot of npad elements with pair configuration c: the
-// base arrays, the partial sums (at most 65 slots per element with the
-// symmetric kernel, a few with the one-sided one) and the symmetric kernel's
-// shares (one FP32 triple per (earlier block, element)).
+// base arrays, the partial sums (with the symmetric kernel at most 1 +
+// ceil(later tiles of block 0 / smallest item) slots per element, the plan
+// cutting items of at least 4 tiles and at most 64 per row; a few with the
+// one-sided one) and the symmetric kernel's shares (one FP32 triple per
+// (earlier block, element)).
 size_t slot_bytes(int64_t npad, const nb::PairCfg& c) {
     size_t bytes = bytes_per_element_base() * (size_t)npad;
     if (c.sym) {
         const int64_t B = (int64_t)c.threads * c.bi;
         const int64_t nbk = (npad + B - 1) / B;
-        bytes += (size_t)65 * 32 * (size_t)npad + (size_t)(nbk * (nbk - 1) / 2) * B * 12;
+        const int64_t ntiles = (npad + c.tile - 1) / c.tile;
+        const int64_t later = std::max<int64_t>(0, ntiles - B / c.tile);
+        const int64_t cmin = std::max<int64_t>(4, (later + 63) / 64);
+        const int64_t slots = 1 + (later + cmin - 1) / cmin;
+        bytes += (size_t)slots * 32 * (size_t)npad + (size_t)(nbk * (nbk - 1) / 2) * B * 12;
     } else {
         bytes += (size_t)4 * 32 * (size_t)npad;
     }
@@ -84,18 +90,18 @@ size_t slot_bytes(int64_t npad, const nb::PairCfg& c) {
 
 // The server's pair kernel: the symmetric one (each unordered pair once)
 // for slots of at least 16,384 elements, where it is the faster; otherwise
-// the library's default.  Fixed for the server's life, so a run's result
-// does not depend on the other runs in the batch.
+// the one-sided one.  Fixed for the server's life, so a run's result does
+// not depend on the other runs in the batch.
 // Pair interactions per step the server gathers before it stops adding runs
 // to a step (about 3 ms of the pair kernel on one GB300).
 constexpr double kMinPairsPerStep = 1e10;
 
-nb::PairCfg server_pair_cfg(int64_t slot_n, int prec, const nb::PairCfg& dflt) {
+nb::PairCfg server_pair_cfg(int64_t slot_n, int prec) {
     if (prec == 32 && slot_n >= 16384) {
         const nb::PairCfg sym{256, 12, 128, 0, 2, 0, 0, 2, 3};
         if (nb::pair_cfg_supported(sym)) return sym;
     }
-    return dflt;
+    return nb::kOneSided;
 }
 
 }  // namespace
@@ -258,7 +264,7 @@ nb_status nb_server_create(size_t hbm_budget_bytes, int32_t max_slots, int64_t m
                              "nb_server_create: need max_slots >= 1, max_n >= 1, prec 32 or 64");
         *out = nullptr;
         const int64_t npad = (max_n + nb::NB_PAD - 1) / nb::NB_PAD * nb::NB_PAD;
-        const nb::PairCfg cfg = server_pair_cfg(npad, prec, nb::Batch().pair_cfg());
+        const nb::PairCfg cfg = server_pair_cfg(npad, prec);
         const size_t per_slot = slot_bytes(npad, cfg);
         const int64_t fit = (int64_t)(hbm_budget_bytes / std::max<size_t>(per_slot, 1));
         const int nslots = (int)std::min<int64_t>(max_slots, fit);

@@ -39,9 +39,19 @@ def _descs(nbm, systems):
             [nbm.nb_params_default(**s["params"]) for s in systems])
 
 
-def _alone(nbm, s, nsteps, stream=None):
+CFG_FIELDS = ("tile", "i_per_thread", "threads", "min_blocks", "nr_slots", "i_packed",
+              "shared_rcp", "symmetric")
+
+
+def _alone(nbm, s, nsteps, stream=None, cfg=None):
+    """The run alone; with cfg (a pair configuration as a dict), a^0 is
+    re-evaluated with it before stepping, as a server does at admission."""
     with nbm.System(nbm.nb_desc_default(**s["desc"]), nbm.nb_params_default(**s["params"]),
                     stream=stream) as sysm:
+        if cfg is not None:
+            sysm.set_pair_cfg(*[cfg[f] for f in CFG_FIELDS])
+            xv, _, meta = sysm.get_state()
+            sysm.set_state(xv, None, meta)
         sysm.step(nsteps)
         sysm.sync()
         xv, a, meta = sysm.get_state()
@@ -104,6 +114,7 @@ def test_server_results_equal_alone(nbm):
     stream = torch.cuda.Stream()
     srv = nbm.nb_server_create(4 << 30, 3, 4096, 32, stream)
     try:
+        cfg = nbm.nb_server_pair_cfg(srv)
         info = nbm.nb_server_info(srv)
         assert info["nslots"] == 3 and info["slot_n"] >= 4096
         tickets = []
@@ -119,7 +130,7 @@ def test_server_results_equal_alone(nbm):
         assert r["status"] == nbm.NB_OK
         assert r["steps"] == nsteps
         assert r["t_submit"] <= r["t_start"] <= r["t_finish"]
-        _, _, _, ref = _alone(nbm, s, nsteps)
+        _, _, _, ref = _alone(nbm, s, nsteps, cfg=cfg)
         d = r["diag"]
         assert d["step"] == nsteps
         assert d["e_kin"] == ref["e_kin"]
