@@ -127,8 +127,11 @@ __device__ __forceinline__ void write_vel32(const BatchDev& b, int64_t i, const 
 
 template <int MODE, bool KEYS>
 __global__ void kick_kernel(BatchDev b, int only) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= b.ntot) return;
+    // elements in reverse order: with the symmetric pair sums an element of
+    // block K adds K blocks' shares, so the longest threads run first
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= b.ntot) return;
+    const int64_t i = b.ntot - 1 - t;
     const int s = b.sys_of[i];
     // every element gets a fresh grid key (none for padding / idle systems)
     if (s < 0 || !b.sc[s].active) {
