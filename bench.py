@@ -302,7 +302,7 @@ def measure_batched(nbm, torch, dev, stream, args, ws, rank):
     descs = [nbm.nb_desc_default(**systems[s]) for s in mine]
     params = [nbm.nb_params_default(**SWEEP_PARAMS) for _ in mine]
     b = nbm.Batch(descs, params, stream=stream)
-    tuned = b.autotune(1)
+    tuned = b.autotune(3)
     b.step(3)
     b.sync()
     b.profile(True)

@@ -242,7 +242,7 @@ __device__ __forceinline__ void sym_tile_rot(const JTile<TILE>& tj, const f2 (&x
 #pragma unroll 1
     for (int g = 0; g < TILE; g += 64) {
         f2 sx = 0ull, sy = 0ull, sz = 0ull;  // j-side sums of the pair this lane holds
-#pragma unroll 4
+#pragma unroll 8
         for (int s = 0; s < 32; ++s) {
             const int j = g + 2 * ((lane + s) & 31);
             const f2 px = *reinterpret_cast<const f2*>(&tj.x[j]);
