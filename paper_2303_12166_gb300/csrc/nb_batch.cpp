@@ -846,10 +846,14 @@ nb_status Batch::autotune(int reps, PairCfg* best, double* best_ms) {
             }
             break;
         }
-        // time about two waves of the persistent grid (items are equal-sized
-        // within a system), normalised per pair interaction
+        // time the whole pass when it is short (a batch of many systems: the
+        // largest items first would not represent the rest), else about two
+        // waves of the persistent grid; normalised per pair interaction
         const std::vector<PairItem>& list = cfg_.sym ? sitems_ : items_;
-        const int nlim = std::min<int>((int)list.size(), 2 * std::max(cfg_.grid, 1));
+        constexpr double kWholePassPairs = 2e11;
+        const int nlim = pairs_per_step() <= kWholePassPairs
+                             ? (int)list.size()
+                             : std::min<int>((int)list.size(), 2 * std::max(cfg_.grid, 1));
         double pairs = 0;
         for (int q = 0; q < nlim; ++q) pairs += item_pairs(list[q], cfg_.sym != 0);
         if ((st = launch_pairs_(false, nlim)) != NB_OK) break;  // warm-up
