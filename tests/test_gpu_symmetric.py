@@ -271,3 +271,30 @@ def test_full_size_in_the_tuned_configuration(nbm, orc, name, nrows):
     ref = orc.forces_rows(rows, ox, ov, om, oR, og, G=1.0, eps=params["eps"],
                           beta=params["beta"])
     assert rms_rel(a[rows], ref) <= 1e-5, f"tuned configuration {best}"
+
+
+def test_energy_drift_long_run(nbm, orc):
+    """1,000 elastic steps (beta = 1) of a 4,096-element binary on the
+    default (symmetric) path: the total energy's drift stays within a small
+    multiple of the FP64 oracle's own drift on the same problem (the two
+    trajectories separate chaotically, so energies are compared in size,
+    not value by value)."""
+    desc = dict(n_donor=3072, n_accretor=1024, q=0.4, f_donor=0.85, f_accretor=0.5,
+                sigma_v=1e-3, seed=9, stream=0)
+    params = dict(eps=0.005, dt=2e-4, beta=1.0)
+    nsteps = 1000
+    with _make(nbm, desc, params) as s:
+        d0 = s.diagnostics()
+        s.step(nsteps)
+        s.sync()
+        d1 = s.diagnostics()
+    p = dict(params, G=1.0, kappa_gamma=8.0, rl_coeff=0.69)
+    ox, ov, om, oR, og = oracle_ic(orc, desc, p)
+    e0 = orc.diagnostics(ox, ov, om, oR, og, G=1.0, eps=0.005)["E_tot"]
+    rx, rv, _ = orc.run(ox, ov, om, oR, og, G=1.0, eps=0.005, beta=1.0, dt=2e-4, nsteps=nsteps,
+                        n_donor=3072)
+    e1 = orc.diagnostics(rx, rv, om, oR, og, G=1.0, eps=0.005)["E_tot"]
+    assert d0["e_tot"] == pytest.approx(e0, rel=1e-6)
+    drift_gpu = abs(d1["e_tot"] - d0["e_tot"]) / abs(e0)
+    drift_orc = abs(e1 - e0) / abs(e0)
+    assert drift_gpu <= 3.0 * max(drift_orc, 1e-5), (drift_gpu, drift_orc)
