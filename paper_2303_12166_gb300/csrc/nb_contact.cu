@@ -255,7 +255,7 @@ __device__ __forceinline__ void contact_fp64(const BatchDev& b, const SysConst& 
 // FULL64: every candidate through contact_fp64 in FP64 (the FP64 force path
 // and the diagnostics); ENERGY: also the repulsion energy (implies FULL64).
 template <bool FULL64, bool ENERGY>
-__global__ void __launch_bounds__(128) contact_kernel(BatchDev b, int kofs, uint32_t total_idx) {
+__global__ void __launch_bounds__(128, 8) contact_kernel(BatchDev b, int kofs, uint32_t total_idx) {
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= b.blocksum[total_idx]) return;
     const uint32_t i = b.sorted[t];
