@@ -125,8 +125,10 @@ __device__ __forceinline__ void write_vel32(const BatchDev& b, int64_t i, const 
     b.v32.z[i] = (float)v.z;
 }
 
+// 4 blocks of 256 per SM (64 registers): the share sums are latency-bound
+// and gain more from resident warps than they lose to a small spill
 template <int MODE, bool KEYS>
-__global__ void kick_kernel(BatchDev b, int only) {
+__global__ void __launch_bounds__(256, 4) kick_kernel(BatchDev b, int only) {
     // elements in reverse order: with the symmetric pair sums an element of
     // block K adds K blocks' shares, so the longest threads run first
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
