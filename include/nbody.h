@@ -345,6 +345,11 @@ nb_status nb_batch_forces(nb_batch_t b, int32_t sys, double* acc_out, int out_on
 nb_status nb_batch_diagnostics(nb_batch_t b, int32_t sys, nb_diag* out);
 nb_status nb_batch_get_state(nb_batch_t b, int32_t sys, double* xv_out, double* a_out,
                              nb_ckpt_meta* meta);
+/* Replace system sys's state from a checkpoint, as nb_set_state does for a
+ * single system (the other systems keep theirs; with a_in NULL the batch
+ * re-evaluates forces and stores a^k for sys only). */
+nb_status nb_batch_set_state(nb_batch_t b, int32_t sys, const double* xv_in, const double* a_in,
+                             const nb_ckpt_meta* meta);
 nb_status nb_batch_set_pair_cfg(nb_batch_t b, const nb_pair_cfg* cfg);
 nb_status nb_batch_autotune(nb_batch_t b, int reps, nb_pair_cfg* best);
 nb_status nb_batch_profile(nb_batch_t b, int enable);

@@ -393,6 +393,13 @@ nb_status nb_batch_get_state(nb_batch_t b, int32_t sys, double* xv_out, double* 
     return guarded([&] { return b->batch.get_state(sys, xv_out, a_out, meta); });
 }
 
+nb_status nb_batch_set_state(nb_batch_t b, int32_t sys, const double* xv_in, const double* a_in,
+                             const nb_ckpt_meta* meta) {
+    nb_status st = check_sys(b, sys);
+    if (st != NB_OK) return st;
+    return guarded([&] { return b->batch.set_state(sys, xv_in, a_in, meta); });
+}
+
 nb_status nb_batch_set_pair_cfg(nb_batch_t b, const nb_pair_cfg* cfg) {
     if (!b || !cfg) return set_error(NB_EINVAL, "null argument");
     return guarded([&] {

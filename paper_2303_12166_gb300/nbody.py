@@ -130,6 +130,7 @@ _sig("nb_batch_forces", ctypes.c_int, [_P, _I32, _P, ctypes.c_int])
 _sig("nb_batch_diagnostics", ctypes.c_int, [_P, _I32, ctypes.POINTER(nb_diag)])
 _sig("nb_batch_get_state", ctypes.c_int, [_P, _I32, _P, _P, ctypes.POINTER(nb_ckpt_meta)])
 _sig("nb_batch_set_pair_cfg", ctypes.c_int, [_P, ctypes.POINTER(nb_pair_cfg)])
+_sig("nb_batch_set_state", ctypes.c_int, [_P, _I32, _P, _P, ctypes.POINTER(nb_ckpt_meta)])
 _sig("nb_batch_autotune", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(nb_pair_cfg)])
 _sig("nb_batch_profile", ctypes.c_int, [_P, ctypes.c_int])
 _sig("nb_batch_profile_read", ctypes.c_int, [_P, ctypes.POINTER(nb_prof), ctypes.c_int])
@@ -463,6 +464,14 @@ def nb_batch_get_state(h, sys: int, with_acc: bool = True):
     return xv, a, meta
 
 
+def nb_batch_set_state(h, sys: int, xv, a, meta: nb_ckpt_meta) -> None:
+    xv = np.ascontiguousarray(xv, dtype=np.float64)
+    a = None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+    _check(_lib.nb_batch_set_state(_P(h), int(sys), xv.ctypes.data_as(_P),
+                                   a.ctypes.data_as(_P) if a is not None else None,
+                                   ctypes.byref(meta)), "nb_batch_set_state")
+
+
 def nb_batch_set_pair_cfg(h, tile, i_per_thread, threads, min_blocks, nr_slots=0,
                           i_packed=0, shared_rcp=0, symmetric=0) -> None:
     c = nb_pair_cfg(tile, i_per_thread, threads, min_blocks, nr_slots, i_packed, shared_rcp,
@@ -511,6 +520,9 @@ class Batch:
 
     def get_state(self, s, with_acc=True):
         return nb_batch_get_state(self.h, s, with_acc)
+
+    def set_state(self, s, xv, a, meta):
+        nb_batch_set_state(self.h, s, xv, a, meta)
 
     def set_pair_cfg(self, *cfg):
         nb_batch_set_pair_cfg(self.h, *cfg)

@@ -243,3 +243,53 @@ def test_server_shortest_work_first_keeps_results(nbm):
         assert r["steps"] == steps and r["diag"]["step"] == steps
         assert r["diag"]["e_kin"] == d["e_kin"]
         assert np.array_equal(r["diag"]["com"], d["com"])
+
+
+def test_batch_set_state_one_system(nbm):
+    """A checkpoint restored into one system of a batch rewinds that system
+    only; each system then matches its own run alone, bitwise."""
+    import torch
+    descs, params = _descs(nbm, SYSTEMS)
+    stream = torch.cuda.Stream()
+    with nbm.Batch(descs, params, stream=stream) as b:
+        b.step(4)
+        b.sync()
+        saved = b.get_state(1)
+        b.step(3)
+        b.sync()
+        b.set_state(1, *saved)           # system 1 back to step 4, the others at 7
+        b.step(5)
+        b.sync()
+        got = [b.get_state(s) for s in range(len(SYSTEMS))]
+    for s, steps in [(0, 12), (1, 9), (2, 12)]:
+        xv, a, meta, _ = _alone(nbm, SYSTEMS[s], steps)
+        assert got[s][2].step == steps
+        assert np.array_equal(got[s][0], xv) and np.array_equal(got[s][1], a), s
+
+
+def test_server_fp64(nbm):
+    """A server running the FP64 pair path returns, per run, the result of
+    the run alone with the FP64 path."""
+    srv = nbm.nb_server_create(1 << 30, 2, 4096, 64)
+    try:
+        reqs = [(SYSTEMS[0], 6), (SYSTEMS[2], 9)]
+        tickets = [nbm.nb_submit(srv, nbm.nb_desc_default(**s["desc"]),
+                                 nbm.nb_params_default(**dict(s["params"], force_prec=64)), n)
+                   for s, n in reqs]
+        nbm.nb_server_drain(srv, 120.0)
+        res = [nbm.nb_poll(srv, t) for t in tickets]
+        with pytest.raises(nbm.NbError):   # a run of the other precision is refused
+            t = nbm.nb_submit(srv, nbm.nb_desc_default(**SYSTEMS[0]["desc"]),
+                              nbm.nb_params_default(**SYSTEMS[0]["params"]), 2)
+            nbm.nb_server_drain(srv, 60.0)
+            r = nbm.nb_poll(srv, t)
+            if r["status"] != nbm.NB_OK:
+                raise nbm.NbError(r["status"], "refused")
+    finally:
+        nbm.nb_server_destroy(srv)
+    for (s, n), r in zip(reqs, res):
+        assert r["status"] == nbm.NB_OK
+        one = dict(s, params=dict(s["params"], force_prec=64))
+        _, _, _, ref = _alone(nbm, one, n)
+        assert r["diag"]["e_kin"] == ref["e_kin"]
+        assert np.array_equal(r["diag"]["com"], ref["com"])
