@@ -171,6 +171,7 @@ void nb_server::run() {
                 done[r.ticket] = res;
                 where.erase(r.ticket);
                 slot_used[s] = 0;
+                cv.notify_all();  // a drain may be waiting for this ticket
                 continue;
             }
             active[s].req = std::move(r);
@@ -373,7 +374,8 @@ nb_status nb_server_drain(nb_server_t srv, double timeout_s) {
     std::unique_lock<std::mutex> lk(srv->mu);
     const auto deadline = Clock::now() + std::chrono::duration<double>(timeout_s);
     while (!srv->where.empty() && srv->fatal == NB_OK) {
-        if (srv->cv.wait_until(lk, deadline) == std::cv_status::timeout && Clock::now() >= deadline)
+        if (srv->cv.wait_until(lk, deadline) == std::cv_status::timeout &&
+            Clock::now() >= deadline && !srv->where.empty() && srv->fatal == NB_OK)
             return set_error(NB_ETIMEOUT, "nb_server_drain: %zu requests still open",
                              srv->where.size());
     }

@@ -278,13 +278,13 @@ def test_server_fp64(nbm):
                    for s, n in reqs]
         nbm.nb_server_drain(srv, 120.0)
         res = [nbm.nb_poll(srv, t) for t in tickets]
-        with pytest.raises(nbm.NbError):   # a run of the other precision is refused
-            t = nbm.nb_submit(srv, nbm.nb_desc_default(**SYSTEMS[0]["desc"]),
-                              nbm.nb_params_default(**SYSTEMS[0]["params"]), 2)
-            nbm.nb_server_drain(srv, 60.0)
-            r = nbm.nb_poll(srv, t)
-            if r["status"] != nbm.NB_OK:
-                raise nbm.NbError(r["status"], "refused")
+        # a run of the other precision is refused at admission, promptly
+        t = nbm.nb_submit(srv, nbm.nb_desc_default(**SYSTEMS[0]["desc"]),
+                          nbm.nb_params_default(**SYSTEMS[0]["params"]), 2)
+        t0 = nbm.nb_server_clock(srv)
+        nbm.nb_server_drain(srv, 60.0)
+        assert nbm.nb_server_clock(srv) - t0 < 10.0
+        assert nbm.nb_poll(srv, t)["status"] == nbm.NB_EINVAL
     finally:
         nbm.nb_server_destroy(srv)
     for (s, n), r in zip(reqs, res):
