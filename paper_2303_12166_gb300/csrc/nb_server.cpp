@@ -186,6 +186,7 @@ void nb_server::run() {
                 std::lock_guard<std::mutex> lk(mu);
                 fatal = st;
                 fatal_msg = nb::last_error();
+                cv.notify_all();  // wake drains: the server has stopped
                 return;
             }
         }
@@ -223,6 +224,7 @@ void nb_server::run() {
             std::lock_guard<std::mutex> lk(mu);
             fatal = st;
             fatal_msg = nb::last_error();
+            cv.notify_all();  // wake drains: the server has stopped
             return;
         }
         std::vector<char> stepped(nslots, 0);
