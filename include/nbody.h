@@ -398,7 +398,9 @@ nb_status nb_submit(nb_server_t srv, const nb_desc* desc, const nb_params* param
 /* NB_OK with *out filled once the run has finished, NB_PENDING before,
  * NB_ENOTFOUND for an unknown ticket. */
 nb_status nb_poll(nb_server_t srv, uint64_t ticket, nb_result* out);
-/* Wait until every submitted run has finished (NB_ETIMEOUT after timeout_s). */
+/* Wait until every submitted run has finished (NB_ETIMEOUT after timeout_s
+ * seconds; NB_EINVAL for a negative or NaN timeout, an infinite one waits
+ * without limit). */
 nb_status nb_server_drain(nb_server_t srv, double timeout_s);
 /* Seconds since the server was created (the clock of nb_result's times). */
 double nb_server_clock(nb_server_t srv);

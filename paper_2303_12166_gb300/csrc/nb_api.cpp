@@ -5,6 +5,7 @@
 #include <cstring>
 #include <exception>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <utility>
@@ -166,18 +167,16 @@ nb_status nb_create_system(const nb_desc* desc, const nb_params* params, void* s
         nb::SystemInit si;
         nb_status st = nb::build_system(*desc, *params, si);
         if (st != NB_OK) return st;
-        nb_system* sys = new nb_system();
+        // freed on every early return and on an exception below
+        std::unique_ptr<nb_system> sys(new nb_system());
         // multi-step calls replay a captured CUDA graph (needs a non-default stream)
         sys->batch.set_use_graph(true);
         st = sys->batch.init({si.n}, params->force_prec, static_cast<cudaStream_t>(stream));
         if (st == NB_OK) st = sys->batch.load(0, si);
         if (st == NB_OK) st = sys->batch.sync();
-        if (st != NB_OK) {
-            delete sys;
-            return st;
-        }
+        if (st != NB_OK) return st;
         sys->info = si.info;
-        *out = sys;
+        *out = sys.release();
         return NB_OK;
     });
 }
@@ -325,18 +324,15 @@ nb_status nb_batch_create(const nb_desc* descs, const nb_params* params, int32_t
             if (st != NB_OK) return st;
             sizes[s] = si[s].n;
         }
-        nb_batch* b = new nb_batch();
+        std::unique_ptr<nb_batch> b(new nb_batch());
         b->batch.set_use_graph(true);
         nb_status st = b->batch.init(sizes, params[0].force_prec, static_cast<cudaStream_t>(stream));
         for (int32_t s = 0; st == NB_OK && s < nsys; ++s) st = b->batch.load(s, si[s], true);
         if (st == NB_OK) st = b->batch.init_acc(-1);
         if (st == NB_OK) st = b->batch.sync();
-        if (st != NB_OK) {
-            delete b;
-            return st;
-        }
+        if (st != NB_OK) return st;
         for (auto& x : si) b->info.push_back(x.info);
-        *out = b;
+        *out = b.release();
         return NB_OK;
     });
 }

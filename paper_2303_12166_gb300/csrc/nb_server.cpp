@@ -26,6 +26,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <thread>
 
@@ -276,7 +277,8 @@ nb_status nb_server_create(size_t hbm_budget_bytes, int32_t max_slots, int64_t m
                              "nb_server_create: one slot of %lld elements needs ~%zu bytes, over "
                              "the budget of %zu",
                              (long long)max_n, per_slot, hbm_budget_bytes);
-        nb_server* srv = new nb_server();
+        std::unique_ptr<nb_server> owner(new nb_server());
+        nb_server* srv = owner.get();
         srv->slot_n = npad;
         srv->nslots = nslots;
         srv->t0 = Clock::now();
@@ -286,12 +288,9 @@ nb_status nb_server_create(size_t hbm_budget_bytes, int32_t max_slots, int64_t m
         nb_status st = srv->batch.init(std::vector<int64_t>(nslots, npad), prec,
                                        static_cast<cudaStream_t>(stream));
         if (st == NB_OK) st = srv->batch.set_pair_cfg(cfg);
-        if (st != NB_OK) {
-            delete srv;
-            return st;
-        }
+        if (st != NB_OK) return st;
         srv->worker = std::thread([srv] { srv->run(); });
-        *out = srv;
+        *out = owner.release();
         return NB_OK;
     } catch (const std::exception& e) {
         return set_error(NB_EINVAL, "nb_server_create: %s", e.what());
@@ -373,8 +372,12 @@ nb_status nb_poll(nb_server_t srv, uint64_t ticket, nb_result* out) {
 
 nb_status nb_server_drain(nb_server_t srv, double timeout_s) {
     if (!srv) return set_error(NB_EINVAL, "null server");
+    if (!(timeout_s >= 0)) return set_error(NB_EINVAL, "nb_server_drain: timeout must be >= 0");
+    // a year stands for "no limit" (keeps the deadline representable)
+    timeout_s = std::min(timeout_s, 3.2e7);
     std::unique_lock<std::mutex> lk(srv->mu);
-    const auto deadline = Clock::now() + std::chrono::duration<double>(timeout_s);
+    const auto deadline =
+        Clock::now() + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(timeout_s));
     while (!srv->where.empty() && srv->fatal == NB_OK) {
         if (srv->cv.wait_until(lk, deadline) == std::cv_status::timeout &&
             Clock::now() >= deadline && !srv->where.empty() && srv->fatal == NB_OK)

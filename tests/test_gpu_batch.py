@@ -161,7 +161,11 @@ def test_server_budget_and_errors(nbm):
         with pytest.raises(nbm.NbError) as ei:
             nbm.nb_poll(srv, 999999)
         assert ei.value.status == nbm.NB_ENOTFOUND
-        nbm.nb_server_drain(srv, 60.0)
+        for bad in (-1.0, float("nan")):
+            with pytest.raises(nbm.NbError) as ei:
+                nbm.nb_server_drain(srv, bad)
+            assert ei.value.status == nbm.NB_EINVAL
+        nbm.nb_server_drain(srv, float("inf"))  # no limit: returns when both are done
         r1, r2 = nbm.nb_poll(srv, t1), nbm.nb_poll(srv, t2)
         assert r1["status"] == r2["status"] == nbm.NB_OK
         assert r2["t_start"] >= r1["t_finish"]
