@@ -362,7 +362,7 @@ nb_status Batch::init(const std::vector<int64_t>& n_per_slot, int prec, cudaStre
     NB_TRY(alloc_((void**)&d_.cellid, nt * sizeof(uint64_t)));
     NB_TRY(alloc_((void**)&d_.cnt, d_.nbucket * sizeof(uint32_t)));
     NB_TRY(alloc_((void**)&d_.fill, d_.nbucket * sizeof(uint32_t)));
-    NB_TRY(alloc_((void**)&d_.start, d_.nbucket * sizeof(uint32_t)));
+    NB_TRY(alloc_((void**)&d_.start, (d_.nbucket + 1) * sizeof(uint32_t)));  // + the total
     NB_TRY(alloc_((void**)&d_.blocksum, (d_.nbucket / 4096 + 2) * sizeof(uint32_t)));
     NB_TRY(alloc_((void**)&d_.sorted, nt * sizeof(uint32_t)));
     NB_TRY(alloc_((void**)&d_.scell, nt * sizeof(uint64_t)));

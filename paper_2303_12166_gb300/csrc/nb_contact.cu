@@ -130,11 +130,13 @@ __global__ void __launch_bounds__(kScanThreads) scan_top_kernel(uint32_t* __rest
     if (threadIdx.x == kScanThreads - 1) blocksum[nblocks] = total;
 }
 
-// Phase 3: add the block offsets.
+// Phase 3: add the block offsets; start[n] = the grand total, so bucket k
+// spans [start[k], start[k + 1]).
 __global__ void scan_add_kernel(uint32_t* __restrict__ start, const uint32_t* __restrict__ blocksum,
                                 uint32_t n) {
     const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx < n) start[idx] += blocksum[idx / kScanBlock];
+    else if (idx == n) start[n] = blocksum[(n + kScanBlock - 1) / kScanBlock];
 }
 
 // current radius of element i (donor radii grow with the step index)
@@ -258,19 +260,26 @@ template <bool FULL64, bool ENERGY>
 __global__ void __launch_bounds__(128, 8) contact_kernel(BatchDev b, int kofs, uint32_t total_idx) {
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= b.blocksum[total_idx]) return;
+    // the element's own payload (in bucket order); of its FP64 state only
+    // the mass unless a pair needs the FP64 decision (rare, loaded there)
     const uint32_t i = b.sorted[t];
-    const int s = b.sys_of[i];
+    const float4 pi4 = b.spos[t];  // hi position, current radius
+    const float4 li4 = b.slo[t];   // lo position, gamma
+    const float4 vi4 = b.svel[t];  // FP32 velocity, system
+    const int s = __float_as_int(vi4.w);
     const SysConst& c = b.sc[s];
     const int64_t k = b.sm[s].k + kofs;
     const double scale = donor_scale(c, k);
     const int64_t dend = c.off + c.n_donor;
     const double4_32a xi = b.X[i];
-    const double4_32a vi = b.V[i];
-    const double2 ei = b.E[i];
-    const double Ri = ei.x * ((int64_t)i < dend ? scale : 1.0);
-    const float4 pi4 = b.spos[t];  // hi position, current radius
-    const float4 li4 = b.slo[t];   // lo position, gamma
-    const float4 vi4 = b.svel[t];  // FP32 velocity
+    double4_32a vi{};
+    double2 ei{};
+    double Ri = 0.0;
+    if (FULL64) {
+        vi = b.V[i];
+        ei = b.E[i];
+        Ri = ei.x * ((int64_t)i < dend ? scale : 1.0);
+    }
     const float Rif = pi4.w;
     const float gif = li4.w;
     const float mi = max_abs3(pi4);
@@ -294,7 +303,7 @@ __global__ void __launch_bounds__(128, 8) contact_kernel(BatchDev b, int kofs, u
                 const uint64_t cell = pack_cell(nx, ny, nz);
                 const uint32_t key = bucket_of(s, cell, mask);
                 const uint32_t beg = b.start[key];
-                const uint32_t end = beg + b.cnt[key];
+                const uint32_t end = b.start[key + 1];
                 for (uint32_t slot = beg; slot < end; ++slot) {
                     const float4 pj = b.spos[slot];
                     const float dxh = pj.x - pi4.x, dyh = pj.y - pi4.y, dzh = pj.z - pi4.z;
@@ -334,7 +343,10 @@ __global__ void __launch_bounds__(128, 8) contact_kernel(BatchDev b, int kofs, u
                                      (vmi + max_abs3(vj4) + 1e-30f);
                     if (gap2 <= 1e-3f * Rs2 || !(d2 > 0.f) || fabsf(closing) <= cb) {
                         // ambiguous, very shallow or coincident: from the FP64 state
-                        contact_fp64<false, false>(b, c, i, j, dend, scale, xi, vi, ei, Ri,
+                        const double4_32a vi64 = b.V[i];
+                        const double2 ei64 = b.E[i];
+                        const double Ri64 = ei64.x * ((int64_t)i < dend ? scale : 1.0);
+                        contact_fp64<false, false>(b, c, i, j, dend, scale, xi, vi64, ei64, Ri64,
                                                    inv_m, ax, ay, az, eax, eay, eaz, er);
                         continue;
                     }
@@ -370,7 +382,7 @@ cudaError_t launch_contact(const BatchDev& b, int kofs, bool with_energy, bool f
     const uint32_t nblk = (b.nbucket + kScanBlock - 1) / kScanBlock;
     scan_blocks_kernel<<<nblk, kScanThreads, 0, s>>>(b.cnt, b.start, b.blocksum, b.nbucket);
     scan_top_kernel<<<1, kScanThreads, 0, s>>>(b.blocksum, nblk);
-    scan_add_kernel<<<(b.nbucket + 255) / 256, 256, 0, s>>>(b.start, b.blocksum, b.nbucket);
+    scan_add_kernel<<<(b.nbucket + 1 + 255) / 256, 256, 0, s>>>(b.start, b.blocksum, b.nbucket);
     cudaError_t e = cudaMemsetAsync(b.fill, 0, sizeof(uint32_t) * b.nbucket, s);
     if (e != cudaSuccess) return e;
     const unsigned ng = (unsigned)((b.ntot + 255) / 256);
