@@ -476,7 +476,7 @@ nb_status Batch::load(int s, const SystemInit& si, bool defer_forces) {
     consts_dirty_ = true;
     planned_ = false;
     NB_TRY(push_consts_());
-    NB_CU(launch_shadow(d_, stream_));
+    NB_CU(launch_shadow(d_, c.off, c.npad, stream_));
     if (!defer_forces) NB_TRY(init_acc(s));
     // the staging vectors go out of scope: make sure pageable copies are done
     NB_CU(cudaStreamSynchronize(stream_));
@@ -1183,7 +1183,7 @@ nb_status Batch::set_state(int s, const double* xv, const double* a, const nb_ck
     for (int d = 0; d < 3; ++d) c.origin[d] = meta->origin[d];
     consts_dirty_ = true;
     NB_TRY(push_consts_());
-    NB_CU(launch_shadow(d_, stream_));
+    NB_CU(launch_shadow(d_, c.off, c.npad, stream_));
     if (!a) NB_TRY(init_acc(s));
     NB_CU(cudaStreamSynchronize(stream_));
     return NB_OK;

@@ -176,7 +176,8 @@ cudaError_t launch_wait_selftest(long long budget, unsigned int* timed_out, cuda
 // Update kernels.  With build_keys the drift kernel also bins the new
 // positions into the contact grid of step k+1 (b.cnt must be zeroed).
 enum KickMode { KICK_START = 0, KICK_FINISH = 1, KICK_FINISH_START = 2 };
-cudaError_t launch_shadow(const BatchDev& b, cudaStream_t s);
+// FP32 copies of elements [off, off + n) (one system's slot) from the FP64 state
+cudaError_t launch_shadow(const BatchDev& b, int64_t off, int64_t n, cudaStream_t s);
 cudaError_t launch_kick(const BatchDev& b, KickMode mode, bool build_keys, cudaStream_t s);
 // k += 1 for every active system (the last kernel of a step)
 cudaError_t launch_advance(const BatchDev& b, cudaStream_t s);

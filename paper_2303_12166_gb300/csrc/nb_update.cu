@@ -192,9 +192,9 @@ __global__ void advance_kernel(BatchDev b) {
     if (s < b.nsys && b.sc[s].active) b.sm[s].k += 1;
 }
 
-__global__ void shadow_kernel(BatchDev b) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= b.ntot) return;
+__global__ void shadow_kernel(BatchDev b, int64_t off, int64_t n) {
+    const int64_t i = off + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= off + n) return;
     const int s = b.sys_of[i];
     if (s < 0) return;
     const SysConst& c = b.sc[s];
@@ -472,10 +472,10 @@ cudaError_t launch_state_unpack(const BatchDev& b, int64_t off, int64_t n, const
     return cudaGetLastError();
 }
 
-cudaError_t launch_shadow(const BatchDev& b, cudaStream_t s) {
+cudaError_t launch_shadow(const BatchDev& b, int64_t off, int64_t n, cudaStream_t s) {
     const int nt = 256;
-    const unsigned ng = (unsigned)((b.ntot + nt - 1) / nt);
-    if (ng) shadow_kernel<<<ng, nt, 0, s>>>(b);
+    const unsigned ng = (unsigned)((n + nt - 1) / nt);
+    if (ng) shadow_kernel<<<ng, nt, 0, s>>>(b, off, n);
     return cudaGetLastError();
 }
 
