@@ -298,3 +298,33 @@ def test_energy_drift_long_run(nbm, orc):
     drift_gpu = abs(d1["e_tot"] - d0["e_tot"]) / abs(e0)
     drift_orc = abs(e1 - e0) / abs(e0)
     assert drift_gpu <= 3.0 * max(drift_orc, 1e-5), (drift_gpu, drift_orc)
+
+
+def test_default_plan_falls_back_to_one_sided_when_shares_do_not_fit(nbm, orc):
+    """With ~2.5 GB of device memory left, a 1,048,576-element system cannot
+    hold the symmetric plan's shares (4.3 GB) and partial slots: the default
+    configuration falls back to the one-sided kernel by itself (no error)
+    and the forces still match the oracle on sampled rows."""
+    import torch
+    desc, params = workload_kwargs("binary_1m")
+    free, _ = torch.cuda.mem_get_info()
+    leave = 2560 << 20
+    if free < leave + (1 << 30):
+        pytest.skip("not enough device memory to set the case up")
+    hold = torch.empty(free - leave, dtype=torch.uint8, device="cuda")
+    try:
+        with _make(nbm, desc, params) as s:
+            cfg = s.pair_cfg()
+            a = s.forces()
+            n = s.n
+    finally:
+        del hold
+        torch.cuda.empty_cache()
+    assert cfg["symmetric"] == 0
+    ox, ov, om, oR, og = oracle_ic(orc, desc, params)
+    nd = desc["n_donor"]
+    rows = np.unique(np.concatenate([[0, nd - 1, nd, n - 1],
+                                     (synth.u01(5, 19, 96) * n).astype(np.int64)]))
+    ref = orc.forces_rows(rows, ox, ov, om, oR, og, G=1.0, eps=params["eps"],
+                          beta=params["beta"])
+    assert rms_rel(a[rows], ref) <= 1e-5
