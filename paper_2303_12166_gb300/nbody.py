@@ -235,21 +235,31 @@ def dump_state(system, path: str) -> None:
              **{f"diag_{k}": np.asarray(v) for k, v in d.items()})
 
 
+def _host_rows(arr, n: int, k: int, name: str) -> np.ndarray:
+    """`arr` as a flat C-contiguous float64 array of n rows of k values; the
+    library reads exactly n * k doubles through the pointer, so the size is
+    checked here."""
+    a = np.ascontiguousarray(arr, dtype=np.float64).reshape(-1)
+    if a.size != n * k:
+        raise ValueError(f"{name} must hold {n} x {k} values, got {a.size}")
+    return a
+
+
+def _desc_n(desc: nb_desc) -> int:
+    return int(desc.n_donor) + int(desc.n_accretor)
+
+
 # ------------------------------------------------------------------ single system
 def nb_create_system(desc: nb_desc, params: nb_params, stream=None, xv_in=None, mrg_in=None):
     """Returns an opaque handle (int).  xv_in (n,6) / mrg_in (n,3) are optional
     host arrays copied during the call."""
-    keep = []
-    if xv_in is not None:
-        a = np.ascontiguousarray(xv_in, dtype=np.float64).reshape(-1)
-        keep.append(a)
-        desc.xv_in = _dptr(a)
-    if mrg_in is not None:
-        a = np.ascontiguousarray(mrg_in, dtype=np.float64).reshape(-1)
-        keep.append(a)
-        desc.mrg_in = _dptr(a)
+    # both arrays checked before the descriptor points at either
+    xv = None if xv_in is None else _host_rows(xv_in, _desc_n(desc), 6, "xv_in")
+    mrg = None if mrg_in is None else _host_rows(mrg_in, _desc_n(desc), 3, "mrg_in")
     h = _P()
     try:
+        desc.xv_in = None if xv is None else _dptr(xv)
+        desc.mrg_in = None if mrg is None else _dptr(mrg)
         _check(_lib.nb_create_system(ctypes.byref(desc), ctypes.byref(params),
                                      _P(_stream_ptr(stream)), ctypes.byref(h)),
                "nb_create_system")
@@ -273,10 +283,17 @@ def nb_forces(h, out=None):
     """Accelerations (n,3) FP64 at the current state.  With ``out`` a CUDA
     tensor of n*3 float64 the result is written there (device pointer);
     otherwise a new numpy array is returned."""
+    n = nb_get_info(h).n
     if out is not None and hasattr(out, "data_ptr"):
+        import torch
+        if (out.dtype != torch.float64 or out.numel() != 3 * n or not out.is_cuda or
+                not out.is_contiguous()):
+            raise ValueError(f"out must be a contiguous CUDA float64 tensor of {3 * n} values")
         _check(_lib.nb_forces(_P(h), _P(out.data_ptr()), 1), "nb_forces")
         return out
-    n = nb_get_info(h).n
+    if out is not None and (out.shape != (n, 3) or out.dtype != np.float64 or
+                            not out.flags.c_contiguous):
+        raise ValueError("out must be a C-contiguous float64 (n, 3) array")
     a = np.empty((n, 3), dtype=np.float64) if out is None else out
     _check(_lib.nb_forces(_P(h), a.ctypes.data_as(_P), 0), "nb_forces")
     return a
@@ -327,8 +344,9 @@ def nb_get_state(h, with_acc: bool = True, out=None):
 
 
 def nb_set_state(h, xv, a, meta: nb_ckpt_meta) -> None:
-    xv = np.ascontiguousarray(xv, dtype=np.float64)
-    a = None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+    n = nb_get_info(h).n
+    xv = _host_rows(xv, n, 6, "xv")
+    a = None if a is None else _host_rows(a, n, 3, "a")
     _check(_lib.nb_set_state(_P(h), xv.ctypes.data_as(_P),
                              a.ctypes.data_as(_P) if a is not None else None,
                              ctypes.byref(meta)), "nb_set_state")
@@ -465,8 +483,9 @@ def nb_batch_get_state(h, sys: int, with_acc: bool = True):
 
 
 def nb_batch_set_state(h, sys: int, xv, a, meta: nb_ckpt_meta) -> None:
-    xv = np.ascontiguousarray(xv, dtype=np.float64)
-    a = None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+    n = nb_batch_info(h, sys).n
+    xv = _host_rows(xv, n, 6, "xv")
+    a = None if a is None else _host_rows(a, n, 3, "a")
     _check(_lib.nb_batch_set_state(_P(h), int(sys), xv.ctypes.data_as(_P),
                                    a.ctypes.data_as(_P) if a is not None else None,
                                    ctypes.byref(meta)), "nb_batch_set_state")
@@ -577,17 +596,13 @@ def nb_server_pair_cfg(h) -> dict:
 
 
 def nb_submit(h, desc: nb_desc, params: nb_params, nsteps: int, xv_in=None, mrg_in=None) -> int:
-    keep = []
-    if xv_in is not None:
-        a = np.ascontiguousarray(xv_in, dtype=np.float64).reshape(-1)
-        keep.append(a)
-        desc.xv_in = _dptr(a)
-    if mrg_in is not None:
-        a = np.ascontiguousarray(mrg_in, dtype=np.float64).reshape(-1)
-        keep.append(a)
-        desc.mrg_in = _dptr(a)
+    # both arrays checked before the descriptor points at either
+    xv = None if xv_in is None else _host_rows(xv_in, _desc_n(desc), 6, "xv_in")
+    mrg = None if mrg_in is None else _host_rows(mrg_in, _desc_n(desc), 3, "mrg_in")
     t = _U64()
     try:
+        desc.xv_in = None if xv is None else _dptr(xv)
+        desc.mrg_in = None if mrg is None else _dptr(mrg)
         _check(_lib.nb_submit(_P(h), ctypes.byref(desc), ctypes.byref(params), int(nsteps),
                               ctypes.byref(t)), "nb_submit")
     finally:

@@ -95,3 +95,22 @@ def test_no_gpu_fails_loudly(lib_path):
     with pytest.raises(nbm.NbError) as ei:
         nbm.nb_create_system(nbm.nb_desc_default(n_donor=8, n_accretor=8), nbm.nb_params_default())
     assert ei.value.status in (nbm.NB_ECUDA, nbm.NB_ENOMEM)
+
+
+def test_caller_arrays_are_size_checked_before_the_call():
+    """Arrays handed to the library by pointer must hold exactly n rows: the
+    binding refuses other sizes before calling (no handle or GPU needed)."""
+    import numpy as np
+    from paper_2303_12166_gb300 import nbody as nbm
+    desc = nbm.nb_desc_default(n_donor=40, n_accretor=24)
+    params = nbm.nb_params_default()
+    with pytest.raises(ValueError):
+        nbm.nb_create_system(desc, params, xv_in=np.zeros((63, 6)))
+    with pytest.raises(ValueError):
+        nbm.nb_create_system(desc, params, mrg_in=np.zeros((64, 2)))
+    with pytest.raises(ValueError):
+        nbm.nb_submit(None, desc, params, 1, xv_in=np.zeros(64 * 6 + 1))
+    with pytest.raises(ValueError):  # a valid xv_in with a bad mrg_in
+        nbm.nb_create_system(desc, params, xv_in=np.zeros((64, 6)), mrg_in=np.zeros(5))
+    # the descriptor keeps no pointer after a refused call
+    assert not desc.xv_in and not desc.mrg_in

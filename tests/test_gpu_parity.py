@@ -281,6 +281,31 @@ def test_set_state_rejects_nonfinite_and_keeps_state(nbm):
         assert np.array_equal(pxv, xv) and np.array_equal(pa, a)
 
 
+def test_caller_arrays_of_the_wrong_size_are_refused(nbm):
+    """The library reads and writes exactly n rows through caller pointers;
+    the binding refuses arrays of another size before any call (the state is
+    left as it was)."""
+    import torch
+    desc, params = workload_kwargs("binary_1k")
+    with _make(nbm, desc, params) as s:
+        xv, a, meta = s.get_state()
+        with pytest.raises(ValueError):
+            s.set_state(xv[:-1], None, meta)
+        with pytest.raises(ValueError):
+            s.set_state(xv, a[:, :2], meta)
+        with pytest.raises(ValueError):
+            s.forces(out=np.empty((s.n, 2)))
+        with pytest.raises(ValueError):
+            s.forces(out=torch.empty(3 * s.n - 3, dtype=torch.float64, device="cuda"))
+        with pytest.raises(ValueError):
+            s.forces(out=torch.empty(3 * s.n, dtype=torch.float32, device="cuda"))
+        xv2, a2, _ = s.get_state()
+        assert np.array_equal(xv, xv2) and np.array_equal(a, a2)
+        dev = torch.empty(3 * s.n, dtype=torch.float64, device="cuda")
+        s.forces(out=dev)
+        assert np.array_equal(dev.cpu().numpy().reshape(-1, 3), s.forces())
+
+
 def test_steps_split_across_calls_bitwise(nbm):
     desc, params = workload_kwargs("binary_1k")
     with _make(nbm, desc, params) as s:
