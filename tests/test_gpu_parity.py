@@ -453,3 +453,23 @@ def test_unit_rate_probe(nbm):
     # the two MUFU operations and the FP32 lanes keep the SM's 1 : 8 ratio
     ratio = r["fp32_lanes_per_s_sm"] / r["mufu_rcp_per_s_sm"]
     assert 7.0 <= ratio <= 9.0, r
+
+
+# ---------------------------------------------------------------- stored values
+@pytest.mark.parametrize("prec,ftol,xtol", [(32, 1e-5, 1e-5), (64, 1e-12, 1e-11)])
+def test_stored_binary_64(nbm, prec, ftol, xtol):
+    """The 64-element binary of tests/golden/binary_64.txt (written from the
+    FP64 oracle): the library's forces at the start and its state after the
+    stored number of steps, against the stored values."""
+    from test_golden import load_binary_64
+    desc, p, steps, a0, x, v, a = load_binary_64()
+    params = dict(eps=p["eps"], dt=p["dt"], beta=p["beta"], G=p["G"], force_prec=prec)
+    with _make(nbm, dict(desc), params) as s:
+        got0 = s.forces()
+        s.step(steps)
+        s.sync()
+        xv, _, meta = s.get_state()
+    assert meta.step == steps
+    assert rms_rel(got0, a0) <= ftol
+    assert np.abs(xv[:, :3] - x).max() <= xtol
+    assert rms_rel(xv[:, 3:], v) <= 100 * ftol
