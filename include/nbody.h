@@ -19,7 +19,10 @@
  *     are never retained.  Output arrays are allocated by the caller.
  *   - "stream" arguments are cudaStream_t values passed as void*; 0 means the
  *     legacy default stream.  All device work of a handle runs on its stream,
- *     in stream order.
+ *     in stream order, on the CUDA device that was current when the handle
+ *     was created: a call on a handle may come from any thread, and the
+ *     library makes that device current for the call and then restores the
+ *     caller's (a server's own thread runs on its device throughout).
  *   - The library allocates the device memory of a handle itself
  *     (cudaMallocAsync on the handle's stream) and frees it on destroy.
  *   - Units: any consistent set; the defaults use G = 1, total mass 1 and

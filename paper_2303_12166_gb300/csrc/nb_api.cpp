@@ -182,7 +182,9 @@ nb_status nb_create_system(const nb_desc* desc, const nb_params* params, void* s
 }
 
 void nb_destroy(nb_system_t sys) {
+    if (!sys) return;
     try {
+        nb::DeviceScope ds(sys->batch.device());  // its memory is freed there
         delete sys;
     } catch (...) {
     }
@@ -197,38 +199,57 @@ nb_status nb_get_info(nb_system_t sys, nb_info* out) {
 
 nb_status nb_forces(nb_system_t sys, double* acc_out, int out_on_device) {
     if (!sys) return set_error(NB_EINVAL, "null system");
-    return guarded([&] { return sys->batch.forces_out(0, acc_out, out_on_device != 0); });
+    return guarded([&] {
+        nb::DeviceScope ds(sys->batch.device());
+        return sys->batch.forces_out(0, acc_out, out_on_device != 0);
+    });
 }
 
 nb_status nb_step(nb_system_t sys, int64_t nsteps) {
     if (!sys) return set_error(NB_EINVAL, "null system");
-    return guarded([&] { return sys->batch.step(nsteps); });
+    return guarded([&] {
+        nb::DeviceScope ds(sys->batch.device());
+        return sys->batch.step(nsteps);
+    });
 }
 
 nb_status nb_sync(nb_system_t sys) {
     if (!sys) return set_error(NB_EINVAL, "null system");
-    return guarded([&] { return sys->batch.sync(); });
+    return guarded([&] {
+        nb::DeviceScope ds(sys->batch.device());
+        return sys->batch.sync();
+    });
 }
 
 nb_status nb_diagnostics(nb_system_t sys, nb_diag* out) {
     if (!sys) return set_error(NB_EINVAL, "null system");
-    return guarded([&] { return sys->batch.diagnostics(0, out); });
+    return guarded([&] {
+        nb::DeviceScope ds(sys->batch.device());
+        return sys->batch.diagnostics(0, out);
+    });
 }
 
 nb_status nb_get_state(nb_system_t sys, double* xv_out, double* a_out, nb_ckpt_meta* meta) {
     if (!sys) return set_error(NB_EINVAL, "null system");
-    return guarded([&] { return sys->batch.get_state(0, xv_out, a_out, meta); });
+    return guarded([&] {
+        nb::DeviceScope ds(sys->batch.device());
+        return sys->batch.get_state(0, xv_out, a_out, meta);
+    });
 }
 
 nb_status nb_set_state(nb_system_t sys, const double* xv_in, const double* a_in,
                        const nb_ckpt_meta* meta) {
     if (!sys) return set_error(NB_EINVAL, "null system");
-    return guarded([&] { return sys->batch.set_state(0, xv_in, a_in, meta); });
+    return guarded([&] {
+        nb::DeviceScope ds(sys->batch.device());
+        return sys->batch.set_state(0, xv_in, a_in, meta);
+    });
 }
 
 nb_status nb_autotune(nb_system_t sys, int reps, nb_pair_cfg* best) {
     if (!sys) return set_error(NB_EINVAL, "null system");
     return guarded([&]() -> nb_status {
+        nb::DeviceScope ds(sys->batch.device());
         const auto key = std::make_pair(sys->info.n, sys->batch.prec());
         {
             std::lock_guard<std::mutex> g(g_tune_mu);
@@ -300,12 +321,18 @@ nb_status nb_selftest_device_wait(int64_t budget_clocks, void* stream) {
 
 nb_status nb_profile(nb_system_t sys, int enable) {
     if (!sys) return set_error(NB_EINVAL, "null system");
-    return guarded([&] { return sys->batch.set_profile(enable != 0); });
+    return guarded([&] {
+        nb::DeviceScope ds(sys->batch.device());
+        return sys->batch.set_profile(enable != 0);
+    });
 }
 
 nb_status nb_profile_read(nb_system_t sys, nb_prof* out, int reset) {
     if (!sys) return set_error(NB_EINVAL, "null system");
-    return guarded([&] { return sys->batch.read_profile(out, reset != 0); });
+    return guarded([&] {
+        nb::DeviceScope ds(sys->batch.device());
+        return sys->batch.read_profile(out, reset != 0);
+    });
 }
 
 // ------------------------------------------------------------------ batches
@@ -338,7 +365,9 @@ nb_status nb_batch_create(const nb_desc* descs, const nb_params* params, int32_t
 }
 
 void nb_batch_destroy(nb_batch_t b) {
+    if (!b) return;
     try {
+        nb::DeviceScope ds(b->batch.device());
         delete b;
     } catch (...) {
     }
@@ -362,38 +391,56 @@ nb_status nb_batch_info(nb_batch_t b, int32_t sys, nb_info* out) {
 
 nb_status nb_batch_step(nb_batch_t b, int64_t nsteps) {
     if (!b) return set_error(NB_EINVAL, "null batch");
-    return guarded([&] { return b->batch.step(nsteps); });
+    return guarded([&] {
+        nb::DeviceScope ds(b->batch.device());
+        return b->batch.step(nsteps);
+    });
 }
 
 nb_status nb_batch_sync(nb_batch_t b) {
     if (!b) return set_error(NB_EINVAL, "null batch");
-    return guarded([&] { return b->batch.sync(); });
+    return guarded([&] {
+        nb::DeviceScope ds(b->batch.device());
+        return b->batch.sync();
+    });
 }
 
 nb_status nb_batch_forces(nb_batch_t b, int32_t sys, double* acc_out, int out_on_device) {
     nb_status st = check_sys(b, sys);
     if (st != NB_OK) return st;
-    return guarded([&] { return b->batch.forces_out(sys, acc_out, out_on_device != 0); });
+    return guarded([&] {
+        nb::DeviceScope ds(b->batch.device());
+        return b->batch.forces_out(sys, acc_out, out_on_device != 0);
+    });
 }
 
 nb_status nb_batch_diagnostics(nb_batch_t b, int32_t sys, nb_diag* out) {
     nb_status st = check_sys(b, sys);
     if (st != NB_OK) return st;
-    return guarded([&] { return b->batch.diagnostics(sys, out); });
+    return guarded([&] {
+        nb::DeviceScope ds(b->batch.device());
+        return b->batch.diagnostics(sys, out);
+    });
 }
 
 nb_status nb_batch_get_state(nb_batch_t b, int32_t sys, double* xv_out, double* a_out,
                              nb_ckpt_meta* meta) {
     nb_status st = check_sys(b, sys);
     if (st != NB_OK) return st;
-    return guarded([&] { return b->batch.get_state(sys, xv_out, a_out, meta); });
+    return guarded([&] {
+        nb::DeviceScope ds(b->batch.device());
+        return b->batch.get_state(sys, xv_out, a_out, meta);
+    });
 }
 
 nb_status nb_batch_set_state(nb_batch_t b, int32_t sys, const double* xv_in, const double* a_in,
                              const nb_ckpt_meta* meta) {
     nb_status st = check_sys(b, sys);
     if (st != NB_OK) return st;
-    return guarded([&] { return b->batch.set_state(sys, xv_in, a_in, meta); });
+    return guarded([&] {
+        nb::DeviceScope ds(b->batch.device());
+        return b->batch.set_state(sys, xv_in, a_in, meta);
+    });
 }
 
 nb_status nb_batch_set_pair_cfg(nb_batch_t b, const nb_pair_cfg* cfg) {
@@ -409,6 +456,7 @@ nb_status nb_batch_set_pair_cfg(nb_batch_t b, const nb_pair_cfg* cfg) {
 nb_status nb_batch_autotune(nb_batch_t b, int reps, nb_pair_cfg* best) {
     if (!b) return set_error(NB_EINVAL, "null batch");
     return guarded([&]() -> nb_status {
+        nb::DeviceScope ds(b->batch.device());
         nb::PairCfg c{};
         double ms = 0;
         nb_status st = b->batch.autotune(reps, &c, &ms);
@@ -419,12 +467,18 @@ nb_status nb_batch_autotune(nb_batch_t b, int reps, nb_pair_cfg* best) {
 
 nb_status nb_batch_profile(nb_batch_t b, int enable) {
     if (!b) return set_error(NB_EINVAL, "null batch");
-    return guarded([&] { return b->batch.set_profile(enable != 0); });
+    return guarded([&] {
+        nb::DeviceScope ds(b->batch.device());
+        return b->batch.set_profile(enable != 0);
+    });
 }
 
 nb_status nb_batch_profile_read(nb_batch_t b, nb_prof* out, int reset) {
     if (!b) return set_error(NB_EINVAL, "null batch");
-    return guarded([&] { return b->batch.read_profile(out, reset != 0); });
+    return guarded([&] {
+        nb::DeviceScope ds(b->batch.device());
+        return b->batch.read_profile(out, reset != 0);
+    });
 }
 
 }  // extern "C"

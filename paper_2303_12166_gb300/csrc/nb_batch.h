@@ -61,6 +61,23 @@ double model_roche_L1(double q);
 nb_status build_system(const nb_desc& d, const nb_params& p, SystemInit& out);
 nb_status check_params(const nb_params& p);
 
+// Makes `dev` the calling thread's current CUDA device for the scope and
+// restores the previous one (a handle's calls may come from any thread, and
+// its memory, streams and launches belong to the device it was created on).
+struct DeviceScope {
+    int prev = -1;
+    explicit DeviceScope(int dev) {
+        int cur = -1;
+        if (cudaGetDevice(&cur) == cudaSuccess && cur != dev && cudaSetDevice(dev) == cudaSuccess)
+            prev = cur;
+    }
+    ~DeviceScope() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+    DeviceScope(const DeviceScope&) = delete;
+    DeviceScope& operator=(const DeviceScope&) = delete;
+};
+
 class Batch {
 public:
     Batch() = default;
@@ -113,6 +130,7 @@ public:
     bool active(int s) const { return sc_[s].active != 0; }
     int64_t device_bytes() const { return bytes_; }
     cudaStream_t stream() const { return stream_; }
+    int device() const { return device_; }  // the CUDA device the batch lives on
     int prec() const { return prec_; }
     const BatchDev& dev() const { return d_; }
     int nitems() const { return (int)(cfg_.sym && prec_ == 32 ? sitems_ : items_).size(); }

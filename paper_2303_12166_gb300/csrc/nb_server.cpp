@@ -131,6 +131,14 @@ struct nb_server {
 };
 
 void nb_server::run() {
+    // this thread launches the batch's work: on the device it was created on
+    if (cudaSetDevice(batch.device()) != cudaSuccess) {
+        std::lock_guard<std::mutex> lk(mu);
+        fatal = NB_ECUDA;
+        fatal_msg = "server thread: cudaSetDevice failed";
+        cv.notify_all();
+        return;
+    }
     for (;;) {
         // ---- admit
         std::vector<std::pair<int, Request>> admit;
@@ -399,6 +407,7 @@ void nb_server_destroy(nb_server_t srv) {
     }
     if (srv->worker.joinable()) srv->worker.join();
     try {
+        nb::DeviceScope ds(srv->batch.device());  // the slots' memory is freed there
         delete srv;
     } catch (...) {
     }
