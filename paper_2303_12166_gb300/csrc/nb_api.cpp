@@ -8,6 +8,7 @@
 #include <memory>
 #include <mutex>
 #include <new>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -41,9 +42,10 @@ nb_status guarded(F&& f) {
     }
 }
 
-// Process-wide tuning cache: (element count, precision) -> best variant.
+// Process-wide tuning cache: (element count, precision, device) -> best
+// variant and its time.
 std::mutex g_tune_mu;
-std::map<std::pair<int64_t, int>, std::pair<nb::PairCfg, double>> g_tune_cache;
+std::map<std::tuple<int64_t, int, int>, std::pair<nb::PairCfg, double>> g_tune_cache;
 
 nb_pair_cfg to_abi(const nb::PairCfg& c, double ms) {
     nb_pair_cfg o{};
@@ -250,7 +252,7 @@ nb_status nb_autotune(nb_system_t sys, int reps, nb_pair_cfg* best) {
     if (!sys) return set_error(NB_EINVAL, "null system");
     return guarded([&]() -> nb_status {
         nb::DeviceScope ds(sys->batch.device());
-        const auto key = std::make_pair(sys->info.n, sys->batch.prec());
+        const auto key = std::make_tuple(sys->info.n, sys->batch.prec(), sys->batch.device());
         {
             std::lock_guard<std::mutex> g(g_tune_mu);
             auto it = g_tune_cache.find(key);
