@@ -48,6 +48,15 @@ MUTANTS = [
      "Re_d = n_d > 0 ? Rs_d / sqrt((double)n_d) : 0.0;"),
     ("coincident elements not skipped", "if (!(d2 > 0.0)) continue;               "
      "/* i == j or coincident */", "if (j == i) continue;"),
+    ("potential softened on r^2", "eg -= 0.5 * G * m[i] * m[j] / (r + eps);",
+     "eg -= 0.5 * G * m[i] * m[j] / sqrt(d2 + eps * eps);"),
+    ("potential pairs counted twice", "eg -= 0.5 * G * m[i] * m[j] / (r + eps);",
+     "eg -= G * m[i] * m[j] / (r + eps);"),
+    ("repulsion energy with the wrong sign",
+     "er += 0.5 * 0.5 * (gam[i] + gam[j]) * orc_lens_U(r, 0.5 * (R[i] + R[j]));",
+     "er -= 0.5 * 0.5 * (gam[i] + gam[j]) * orc_lens_U(r, 0.5 * (R[i] + R[j]));"),
+    ("repulsion energy with the summed radius", "orc_lens_U(r, 0.5 * (R[i] + R[j]))",
+     "orc_lens_U(r, (R[i] + R[j]))"),
 ]
 
 
