@@ -3,8 +3,9 @@
 Each case below plants one mistake into a copy of oracle/nb_oracle.c (a
 wrong sign, a dropped or transposed term, a misread equation), compiles it,
 and runs the pins of test_oracle_pins.py against it: at least one pin must
-fail.  The planted copies live in a temporary directory; the real oracle is
-untouched.
+fail.  The numpy diagnostics of oracle/oracle.py get the same treatment
+(a planted copy of the module bound to the real compiled oracle).  The
+planted copies live in a temporary directory; the real oracle is untouched.
 """
 import importlib.util
 import os
@@ -111,3 +112,65 @@ def test_control_unmodified_copy_passes_every_pin(tmp_path):
     orc = oracle.load_variant(oracle.compile_source(str(copy), str(tmp_path / "libcopy.so")))
     for fn, kw in _pins():
         fn(orc, **kw)
+
+
+# mistakes planted in the numpy diagnostics of oracle.py
+PY_MUTANTS = [
+    ("L1 plane side flipped", "past = proj < xl1 * sep", "past = proj > xl1 * sep"),
+    ("L1 of the inverse mass ratio", "xl1 = roche_L1(q) if rl_L1 is None else rl_L1",
+     "xl1 = roche_L1(1.0 / q) if rl_L1 is None else rl_L1"),
+    ("lobe test inverted", "inlobe[k] = roche_phi(q, xi, yi, zi) >= phi_c",
+     "inlobe[k] = roche_phi(q, xi, yi, zi) <= phi_c"),
+    ("unbound test inverted", "unb = e > 0", "unb = e < 0"),
+    ("kinetic energy without the half", '"E_kin": float(0.5 * np.sum(m * np.sum(v * v, axis=1))),',
+     '"E_kin": float(np.sum(m * np.sum(v * v, axis=1))),'),
+    ("angular momentum as v x x", '"L": (m[:, None] * np.cross(x, v)).sum(axis=0),',
+     '"L": (m[:, None] * np.cross(v, x)).sum(axis=0),'),
+    ("centre of mass unweighted", '"com": (m[:, None] * x).sum(axis=0) / m.sum(),',
+     '"com": x.mean(axis=0),'),
+]
+
+
+def _py_pins():
+    spec = importlib.util.spec_from_file_location("oracle_pins", os.path.join(HERE,
+                                                                             "test_oracle_pins.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return [mod.test_diagnostics_L1_count, mod.test_diagnostics_lobe_and_unbound,
+            mod.test_diagnostics_two_body_closed_form,
+            mod.test_energy_bounded_elastic_and_decreasing_inelastic]
+
+
+@pytest.mark.parametrize("name,old,new", PY_MUTANTS, ids=[m[0] for m in PY_MUTANTS])
+def test_pins_detect_planted_mistake_in_diagnostics(tmp_path, name, old, new):
+    from oracle import oracle
+    lib = oracle.build()
+    src = open(os.path.join(ROOT, "oracle", "oracle.py")).read()
+    assert src.count(old) == 1, f"mutation site not unique for {name!r}"
+    path = tmp_path / "oracle_mutant.py"
+    path.write_text(src.replace(old, new))
+    spec = importlib.util.spec_from_file_location("oracle_py_mutant", str(path))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod._LIB_OVERRIDE = lib
+    failed = []
+    for fn in _py_pins():
+        try:
+            fn(mod)
+        except Exception as e:
+            failed.append(f"{fn.__name__}: {type(e).__name__}")
+            break
+    assert failed, f"no pin caught the planted mistake: {name}"
+
+
+def test_control_unmodified_diagnostics_pass_every_pin(tmp_path):
+    from oracle import oracle
+    lib = oracle.build()
+    path = tmp_path / "oracle_copy.py"
+    path.write_text(open(os.path.join(ROOT, "oracle", "oracle.py")).read())
+    spec = importlib.util.spec_from_file_location("oracle_py_copy", str(path))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod._LIB_OVERRIDE = lib
+    for fn in _py_pins():
+        fn(mod)

@@ -481,6 +481,13 @@ def test_diagnostics_L1_count(orc):
     d2 = orc.diagnostics(x2, v, m, R, gam, eps=0.01, n_donor=nd, q=q)
     assert d2["n_past_L1"] == 5
     assert d2["m_past_L1"] == pytest.approx(5 * m[0], rel=1e-14)
+    # L1 lies nearer the lighter star: with the donor the lighter one
+    # (q = 0.5), a donor element at the midpoint of the two centres is
+    # already on the accretor's side of L1
+    x3 = x.copy()
+    x3[0] = 0.5 * (d["com_accretor"] + d["com_donor"])
+    d3 = orc.diagnostics(x3, v, m, R, gam, eps=0.01, n_donor=nd, q=q)
+    assert d3["n_past_L1"] == 1
 
 
 def test_diagnostics_lobe_and_unbound(orc):
@@ -521,3 +528,22 @@ def test_eccentric_ic_follows_kepler(orc):
     a = orc.make_ic(8, 8, q, seed=3)
     b = orc.make_ic(8, 8, q, seed=3, ecc=0.0)
     assert all(np.array_equal(u, w) for u, w in zip(a, b))
+
+
+def test_diagnostics_two_body_closed_form(orc):
+    """Two point masses (m1 = 0.3, m2 = 0.7) on the circular orbit of
+    separation a = 1 about their centre of mass (G = 1, omega = 1), the
+    orbit about +z: E_kin = mu a^2 omega^2 / 2, E_grav = -G m1 m2 / (a + eps)
+    (Eq. 4's potential), L = mu a^2 omega along +z, P = 0, centre of mass at
+    the origin, with mu = m1 m2 / (m1 + m2) = 0.21."""
+    m = np.array([0.3, 0.7])
+    x = np.array([[-0.7, 0.0, 0.0], [0.3, 0.0, 0.0]])
+    v = np.array([[0.0, -0.7, 0.0], [0.0, 0.3, 0.0]])
+    eps = 0.05
+    d = orc.diagnostics(x, v, m, np.zeros(2), np.zeros(2), G=1.0, eps=eps)
+    assert d["E_kin"] == pytest.approx(0.105, rel=1e-14)
+    assert d["E_grav"] == pytest.approx(-0.21 / 1.05, rel=1e-14)
+    assert d["E_rep"] == 0.0
+    assert np.allclose(d["L"], [0.0, 0.0, 0.21], atol=1e-15)
+    assert np.allclose(d["P"], 0.0, atol=1e-15)
+    assert np.allclose(d["com"], 0.0, atol=1e-15)
