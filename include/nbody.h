@@ -230,6 +230,18 @@ double nb_roche_L1(double q);
 #define NB_PRESET_RED_GIANT 2
 nb_status nb_preset(int32_t which, int64_t n, nb_desc* desc, nb_params* params);
 
+/* The initial state nb_create_system would build from (desc, params) --
+ * the recipe of nb_desc (methodology section: element mass from the star's
+ * mass and element count, element radius from the star's radius and count,
+ * star radii from Eq. 3; gamma from params.kappa_gamma), or desc's xv_in /
+ * mrg_in where given -- without creating a system.  Host only, no GPU.
+ * xv_out: caller-owned n x 6 doubles (x, y, z, vx, vy, vz per element in
+ * particle order), n = n_donor + n_accretor; mrg_out: caller-owned n x 3
+ * doubles (mass, initial radius, gamma) or NULL.  NB_EINVAL for invalid
+ * arguments (nothing written). */
+nb_status nb_initial_state(const nb_desc* desc, const nb_params* params, double* xv_out,
+                           double* mrg_out);
+
 /* ---- single system ---------------------------------------------------- */
 
 /* Build a system (initial conditions on the host, FP64), copy it to the

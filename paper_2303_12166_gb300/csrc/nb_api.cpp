@@ -161,6 +161,28 @@ nb_status nb_preset(int32_t which, int64_t n, nb_desc* d, nb_params* p) {
 }
 double nb_roche_L1(double q) { return nb::model_roche_L1(q); }
 
+nb_status nb_initial_state(const nb_desc* desc, const nb_params* params, double* xv_out,
+                           double* mrg_out) {
+    return guarded([&]() -> nb_status {
+        if (!desc || !params || !xv_out) return set_error(NB_EINVAL, "null argument");
+        nb::SystemInit si;
+        nb_status st = nb::build_system(*desc, *params, si);
+        if (st != NB_OK) return st;
+        for (int64_t i = 0; i < si.n; ++i) {
+            for (int c = 0; c < 3; ++c) {
+                xv_out[6 * i + c] = si.x[3 * i + c];
+                xv_out[6 * i + 3 + c] = si.v[3 * i + c];
+            }
+            if (mrg_out) {
+                mrg_out[3 * i + 0] = si.m[i];
+                mrg_out[3 * i + 1] = si.R0[i];
+                mrg_out[3 * i + 2] = si.gam[i];
+            }
+        }
+        return NB_OK;
+    });
+}
+
 nb_status nb_create_system(const nb_desc* desc, const nb_params* params, void* stream,
                            nb_system_t* out) {
     return guarded([&]() -> nb_status {

@@ -106,6 +106,8 @@ _sig("nb_desc_default", ctypes.c_int, [ctypes.POINTER(nb_desc)])
 _sig("nb_roche_rL", _D, [_D, _D])
 _sig("nb_roche_L1", _D, [_D])
 _sig("nb_preset", ctypes.c_int, [_I32, _I64, ctypes.POINTER(nb_desc), ctypes.POINTER(nb_params)])
+_sig("nb_initial_state", ctypes.c_int,
+     [ctypes.POINTER(nb_desc), ctypes.POINTER(nb_params), _P, _P])
 _sig("nb_create_system", ctypes.c_int,
      [ctypes.POINTER(nb_desc), ctypes.POINTER(nb_params), _P, ctypes.POINTER(_P)])
 _sig("nb_destroy", None, [_P])
@@ -224,6 +226,23 @@ def nb_preset(which: int, n: int):
     d, p = nb_desc(), nb_params()
     _check(_lib.nb_preset(int(which), int(n), ctypes.byref(d), ctypes.byref(p)), "nb_preset")
     return d, p
+
+
+def nb_initial_state(desc: nb_desc, params: nb_params):
+    """(xv (n,6), mrg (n,3)): the initial state a system built from (desc,
+    params) starts from -- positions and velocities, and per element mass,
+    initial radius and gamma.  Host only; no system is created."""
+    if desc.xv_in or desc.mrg_in:
+        raise ValueError("pass a descriptor without caller arrays")
+    n = int(desc.n_donor) + int(desc.n_accretor)
+    if n < 1:
+        raise ValueError("need at least one element")
+    xv = np.empty((n, 6), dtype=np.float64)
+    mrg = np.empty((n, 3), dtype=np.float64)
+    _check(_lib.nb_initial_state(ctypes.byref(desc), ctypes.byref(params),
+                                 xv.ctypes.data_as(_P), mrg.ctypes.data_as(_P)),
+           "nb_initial_state")
+    return xv, mrg
 
 
 def dump_state(system, path: str) -> None:

@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -114,3 +115,43 @@ def test_caller_arrays_are_size_checked_before_the_call():
         nbm.nb_create_system(desc, params, xv_in=np.zeros((64, 6)), mrg_in=np.zeros(5))
     # the descriptor keeps no pointer after a refused call
     assert not desc.xv_in and not desc.mrg_in
+
+
+CASES_IC = [
+    (dict(n_donor=512, n_accretor=512, q=0.5, f_donor=0.8, f_accretor=0.5, sigma_v=1e-3,
+          seed=0, stream=0), dict()),
+    (dict(n_donor=300, n_accretor=120, q=0.25, f_donor=0.95, f_accretor=0.3, sigma_v=3e-3,
+          seed=7, stream=4, ecc=0.4), dict(kappa_gamma=5.0, rl_coeff=0.6, flags=2)),
+    (dict(n_donor=3, n_accretor=0, q=2.0, f_donor=0.5, f_accretor=0.5, sigma_v=0.0,
+          seed=1, stream=0), dict(G=0.7)),
+]
+
+
+@pytest.mark.parametrize("desc,params", CASES_IC)
+def test_library_initial_state_matches_the_oracle(orc, desc, params):
+    """The library's host-side initial-condition recipe (no GPU) against the
+    oracle's, element by element."""
+    from paper_2303_12166_gb300 import nbody as nbm
+    xv, mrg = nbm.nb_initial_state(nbm.nb_desc_default(**desc), nbm.nb_params_default(**params))
+    p = nbm.nb_params_default(**params)
+    ox, ov, om, oR, og = orc.make_ic(desc["n_donor"], desc["n_accretor"], desc["q"],
+                                     f_donor=desc["f_donor"], f_accretor=desc["f_accretor"],
+                                     sigma_v=desc["sigma_v"], seed=desc["seed"],
+                                     stream=desc["stream"], G=p.G, kappa_gamma=p.kappa_gamma,
+                                     rl_coeff=p.rl_coeff, ecc=desc.get("ecc", 0.0),
+                                     no_spin=bool(p.flags & 2))
+    assert np.abs(xv[:, :3] - ox).max() < 1e-14
+    assert np.abs(xv[:, 3:] - ov).max() < 1e-14
+    assert np.allclose(mrg[:, 0], om, rtol=1e-15, atol=0)
+    assert np.allclose(mrg[:, 1], oR, rtol=1e-14, atol=0)
+    assert np.allclose(mrg[:, 2], og, rtol=1e-13, atol=0)
+
+
+def test_initial_state_refuses_invalid_descriptions():
+    from paper_2303_12166_gb300 import nbody as nbm
+    with pytest.raises(nbm.NbError) as ei:
+        nbm.nb_initial_state(nbm.nb_desc_default(q=-1.0), nbm.nb_params_default())
+    assert ei.value.status == nbm.NB_EINVAL
+    with pytest.raises(ValueError):
+        nbm.nb_initial_state(nbm.nb_desc_default(n_donor=0, n_accretor=0),
+                             nbm.nb_params_default())
