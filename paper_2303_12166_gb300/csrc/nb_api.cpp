@@ -187,6 +187,7 @@ nb_status nb_create_system(const nb_desc* desc, const nb_params* params, void* s
                            nb_system_t* out) {
     return guarded([&]() -> nb_status {
         if (!desc || !params || !out) return set_error(NB_EINVAL, "null argument");
+        nb::TraceRange tr("nb_create_system");
         *out = nullptr;
         nb::SystemInit si;
         nb_status st = nb::build_system(*desc, *params, si);
@@ -209,6 +210,7 @@ void nb_destroy(nb_system_t sys) {
     if (!sys) return;
     try {
         nb::DeviceScope ds(sys->batch.device());  // its memory is freed there
+        nb::TraceRange tr("nb_destroy");
         delete sys;
     } catch (...) {
     }
@@ -225,6 +227,7 @@ nb_status nb_forces(nb_system_t sys, double* acc_out, int out_on_device) {
     if (!sys) return set_error(NB_EINVAL, "null system");
     return guarded([&] {
         nb::DeviceScope ds(sys->batch.device());
+        nb::TraceRange tr("nb_forces");
         return sys->batch.forces_out(0, acc_out, out_on_device != 0);
     });
 }
@@ -233,6 +236,7 @@ nb_status nb_step(nb_system_t sys, int64_t nsteps) {
     if (!sys) return set_error(NB_EINVAL, "null system");
     return guarded([&] {
         nb::DeviceScope ds(sys->batch.device());
+        nb::TraceRange tr("nb_step");
         return sys->batch.step(nsteps);
     });
 }
@@ -241,6 +245,7 @@ nb_status nb_sync(nb_system_t sys) {
     if (!sys) return set_error(NB_EINVAL, "null system");
     return guarded([&] {
         nb::DeviceScope ds(sys->batch.device());
+        nb::TraceRange tr("nb_sync");
         return sys->batch.sync();
     });
 }
@@ -249,6 +254,7 @@ nb_status nb_diagnostics(nb_system_t sys, nb_diag* out) {
     if (!sys) return set_error(NB_EINVAL, "null system");
     return guarded([&] {
         nb::DeviceScope ds(sys->batch.device());
+        nb::TraceRange tr("nb_diagnostics");
         return sys->batch.diagnostics(0, out);
     });
 }
@@ -257,6 +263,7 @@ nb_status nb_get_state(nb_system_t sys, double* xv_out, double* a_out, nb_ckpt_m
     if (!sys) return set_error(NB_EINVAL, "null system");
     return guarded([&] {
         nb::DeviceScope ds(sys->batch.device());
+        nb::TraceRange tr("nb_get_state");
         return sys->batch.get_state(0, xv_out, a_out, meta);
     });
 }
@@ -266,6 +273,7 @@ nb_status nb_set_state(nb_system_t sys, const double* xv_in, const double* a_in,
     if (!sys) return set_error(NB_EINVAL, "null system");
     return guarded([&] {
         nb::DeviceScope ds(sys->batch.device());
+        nb::TraceRange tr("nb_set_state");
         return sys->batch.set_state(0, xv_in, a_in, meta);
     });
 }
@@ -274,6 +282,7 @@ nb_status nb_autotune(nb_system_t sys, int reps, nb_pair_cfg* best) {
     if (!sys) return set_error(NB_EINVAL, "null system");
     return guarded([&]() -> nb_status {
         nb::DeviceScope ds(sys->batch.device());
+        nb::TraceRange tr("nb_autotune");
         const auto key = std::make_tuple(sys->info.n, sys->batch.prec(), sys->batch.device());
         {
             std::lock_guard<std::mutex> g(g_tune_mu);
@@ -347,6 +356,7 @@ nb_status nb_profile(nb_system_t sys, int enable) {
     if (!sys) return set_error(NB_EINVAL, "null system");
     return guarded([&] {
         nb::DeviceScope ds(sys->batch.device());
+        nb::TraceRange tr("nb_profile");
         return sys->batch.set_profile(enable != 0);
     });
 }
@@ -355,6 +365,7 @@ nb_status nb_profile_read(nb_system_t sys, nb_prof* out, int reset) {
     if (!sys) return set_error(NB_EINVAL, "null system");
     return guarded([&] {
         nb::DeviceScope ds(sys->batch.device());
+        nb::TraceRange tr("nb_profile_read");
         return sys->batch.read_profile(out, reset != 0);
     });
 }
@@ -365,6 +376,7 @@ nb_status nb_batch_create(const nb_desc* descs, const nb_params* params, int32_t
     return guarded([&]() -> nb_status {
         if (!descs || !params || !out || nsys < 1)
             return set_error(NB_EINVAL, "nb_batch_create: need nsys >= 1 and non-null arrays");
+        nb::TraceRange tr("nb_batch_create");
         *out = nullptr;
         std::vector<nb::SystemInit> si(nsys);
         std::vector<int64_t> sizes(nsys);
@@ -392,6 +404,7 @@ void nb_batch_destroy(nb_batch_t b) {
     if (!b) return;
     try {
         nb::DeviceScope ds(b->batch.device());
+        nb::TraceRange tr("nb_batch_destroy");
         delete b;
     } catch (...) {
     }
@@ -417,6 +430,7 @@ nb_status nb_batch_step(nb_batch_t b, int64_t nsteps) {
     if (!b) return set_error(NB_EINVAL, "null batch");
     return guarded([&] {
         nb::DeviceScope ds(b->batch.device());
+        nb::TraceRange tr("nb_batch_step");
         return b->batch.step(nsteps);
     });
 }
@@ -425,6 +439,7 @@ nb_status nb_batch_sync(nb_batch_t b) {
     if (!b) return set_error(NB_EINVAL, "null batch");
     return guarded([&] {
         nb::DeviceScope ds(b->batch.device());
+        nb::TraceRange tr("nb_batch_sync");
         return b->batch.sync();
     });
 }
@@ -434,6 +449,7 @@ nb_status nb_batch_forces(nb_batch_t b, int32_t sys, double* acc_out, int out_on
     if (st != NB_OK) return st;
     return guarded([&] {
         nb::DeviceScope ds(b->batch.device());
+        nb::TraceRange tr("nb_batch_forces");
         return b->batch.forces_out(sys, acc_out, out_on_device != 0);
     });
 }
@@ -443,6 +459,7 @@ nb_status nb_batch_diagnostics(nb_batch_t b, int32_t sys, nb_diag* out) {
     if (st != NB_OK) return st;
     return guarded([&] {
         nb::DeviceScope ds(b->batch.device());
+        nb::TraceRange tr("nb_batch_diagnostics");
         return b->batch.diagnostics(sys, out);
     });
 }
@@ -453,6 +470,7 @@ nb_status nb_batch_get_state(nb_batch_t b, int32_t sys, double* xv_out, double* 
     if (st != NB_OK) return st;
     return guarded([&] {
         nb::DeviceScope ds(b->batch.device());
+        nb::TraceRange tr("nb_batch_get_state");
         return b->batch.get_state(sys, xv_out, a_out, meta);
     });
 }
@@ -463,6 +481,7 @@ nb_status nb_batch_set_state(nb_batch_t b, int32_t sys, const double* xv_in, con
     if (st != NB_OK) return st;
     return guarded([&] {
         nb::DeviceScope ds(b->batch.device());
+        nb::TraceRange tr("nb_batch_set_state");
         return b->batch.set_state(sys, xv_in, a_in, meta);
     });
 }
@@ -481,6 +500,7 @@ nb_status nb_batch_autotune(nb_batch_t b, int reps, nb_pair_cfg* best) {
     if (!b) return set_error(NB_EINVAL, "null batch");
     return guarded([&]() -> nb_status {
         nb::DeviceScope ds(b->batch.device());
+        nb::TraceRange tr("nb_batch_autotune");
         nb::PairCfg c{};
         double ms = 0;
         nb_status st = b->batch.autotune(reps, &c, &ms);
@@ -493,6 +513,7 @@ nb_status nb_batch_profile(nb_batch_t b, int enable) {
     if (!b) return set_error(NB_EINVAL, "null batch");
     return guarded([&] {
         nb::DeviceScope ds(b->batch.device());
+        nb::TraceRange tr("nb_batch_profile");
         return b->batch.set_profile(enable != 0);
     });
 }
@@ -501,6 +522,7 @@ nb_status nb_batch_profile_read(nb_batch_t b, nb_prof* out, int reset) {
     if (!b) return set_error(NB_EINVAL, "null batch");
     return guarded([&] {
         nb::DeviceScope ds(b->batch.device());
+        nb::TraceRange tr("nb_batch_profile_read");
         return b->batch.read_profile(out, reset != 0);
     });
 }

@@ -4,6 +4,7 @@
 // slots, the pair-kernel work list, and the step sequencing.  The single
 // system C API, the batched API and the server are all thin layers over it.
 #pragma once
+#include <nvtx3/nvToolsExt.h>
 #include <cstdint>
 #include <string>
 #include <utility>
@@ -60,6 +61,15 @@ double model_roche_rL(double q, double coeff);
 double model_roche_L1(double q);
 nb_status build_system(const nb_desc& d, const nb_params& p, SystemInit& out);
 nb_status check_params(const nb_params& p);
+
+// A named NVTX range for the scope (profiler timelines and ncu's --nvtx
+// filters); without an attached tool the calls return at once.
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // Makes `dev` the calling thread's current CUDA device for the scope and
 // restores the previous one (a handle's calls may come from any thread, and

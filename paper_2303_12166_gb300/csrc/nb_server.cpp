@@ -159,44 +159,47 @@ void nb_server::run() {
             }
         }
         std::vector<int> loaded;
-        for (auto& [s, r] : admit) {
-            nb::SystemInit si;
-            nb_desc d = r.desc;
-            d.xv_in = r.xv.empty() ? nullptr : r.xv.data();
-            d.mrg_in = r.mrg.empty() ? nullptr : r.mrg.data();
-            nb_status st = nb::build_system(d, r.params, si);
-            if (st == NB_OK && si.n > slot_n)
-                st = set_error(NB_EBUDGET, "request of %lld elements exceeds the slot size %lld",
-                               (long long)si.n, (long long)slot_n);
-            if (st == NB_OK && r.params.force_prec != batch.prec())
-                st = set_error(NB_EINVAL, "the server runs force_prec %d", batch.prec());
-            if (st == NB_OK) st = batch.load(s, si, true);
-            std::lock_guard<std::mutex> lk(mu);
-            if (st != NB_OK) {
-                nb_result res{};
-                res.status = st;
-                res.t_submit = r.t_submit;
-                res.t_start = res.t_finish = now();
-                done[r.ticket] = res;
-                where.erase(r.ticket);
-                slot_used[s] = 0;
-                cv.notify_all();  // a drain may be waiting for this ticket
-                continue;
-            }
-            active[s].req = std::move(r);
-            active[s].done = 0;
-            active[s].t_start = now();
-            loaded.push_back(s);
-        }
-        if (!loaded.empty()) {
-            // initial accelerations of the newcomers only
-            nb_status st = batch.init_acc_subset(loaded);
-            if (st != NB_OK) {
+        {
+            nb::TraceRange tr_admit("nb_server admit");
+            for (auto& [s, r] : admit) {
+                nb::SystemInit si;
+                nb_desc d = r.desc;
+                d.xv_in = r.xv.empty() ? nullptr : r.xv.data();
+                d.mrg_in = r.mrg.empty() ? nullptr : r.mrg.data();
+                nb_status st = nb::build_system(d, r.params, si);
+                if (st == NB_OK && si.n > slot_n)
+                    st = set_error(NB_EBUDGET, "request of %lld elements exceeds the slot size %lld",
+                                   (long long)si.n, (long long)slot_n);
+                if (st == NB_OK && r.params.force_prec != batch.prec())
+                    st = set_error(NB_EINVAL, "the server runs force_prec %d", batch.prec());
+                if (st == NB_OK) st = batch.load(s, si, true);
                 std::lock_guard<std::mutex> lk(mu);
-                fatal = st;
-                fatal_msg = nb::last_error();
-                cv.notify_all();  // wake drains: the server has stopped
-                return;
+                if (st != NB_OK) {
+                    nb_result res{};
+                    res.status = st;
+                    res.t_submit = r.t_submit;
+                    res.t_start = res.t_finish = now();
+                    done[r.ticket] = res;
+                    where.erase(r.ticket);
+                    slot_used[s] = 0;
+                    cv.notify_all();  // a drain may be waiting for this ticket
+                    continue;
+                }
+                active[s].req = std::move(r);
+                active[s].done = 0;
+                active[s].t_start = now();
+                loaded.push_back(s);
+            }
+            if (!loaded.empty()) {
+                // initial accelerations of the newcomers only
+                nb_status st = batch.init_acc_subset(loaded);
+                if (st != NB_OK) {
+                    std::lock_guard<std::mutex> lk(mu);
+                    fatal = st;
+                    fatal_msg = nb::last_error();
+                    cv.notify_all();  // wake drains: the server has stopped
+                    return;
+                }
             }
         }
         // ---- advance the runs with the least remaining work (n^2 x steps
@@ -225,10 +228,13 @@ void nb_server::run() {
         int64_t chunk = tick_steps;
         for (int s : run) chunk = std::min(chunk, active[s].req.nsteps - active[s].done);
         nb_status st = NB_OK;
-        if (chunk > 0)
-            st = run.size() == act.size() ? batch.step(chunk) : batch.step_subset(run, chunk);
         std::vector<nb::SysMut> flags;
-        if (st == NB_OK) st = batch.read_flags(flags);
+        {
+            nb::TraceRange tr_step("nb_server step");
+            if (chunk > 0)
+                st = run.size() == act.size() ? batch.step(chunk) : batch.step_subset(run, chunk);
+            if (st == NB_OK) st = batch.read_flags(flags);
+        }
         if (st != NB_OK) {
             std::lock_guard<std::mutex> lk(mu);
             fatal = st;
@@ -238,6 +244,7 @@ void nb_server::run() {
         }
         std::vector<char> stepped(nslots, 0);
         for (int s : run) stepped[s] = 1;
+        nb::TraceRange tr_retire("nb_server retire");
         // ---- retire finished (or failed) runs
         for (int s = 0; s < nslots; ++s) {
             if (!slot_used[s] || !batch.active(s) || !stepped[s]) continue;
