@@ -88,8 +88,8 @@ def test_row_range_covers_every_row_once():
         row_range(5, 2, 2)
 
 
-# a 61-element binary (ragged split over 2 ranks) with contacts and donor
-# growth, 6 steps
+# a 61-element binary (ragged split over 2 or 3 ranks) with contacts and
+# donor growth, 6 steps
 ROWS_IC = dict(n_donor=40, n_accretor=21, q=0.5, f_donor=0.9, f_accretor=0.6, sigma_v=1e-2,
                seed=5)
 ROWS_P = dict(G=1.0, eps=0.01, beta=0.4, dt=2e-3)
@@ -135,7 +135,8 @@ def _rows_worker(rank, world, port, out):
     dist.destroy_process_group()
 
 
-def test_row_split_system_matches_one_process(orc):
+@pytest.mark.parametrize("world", [2, 3])
+def test_row_split_system_matches_one_process(orc, world):
     import numpy as np
     import torch.multiprocessing as mp
     x, v, m, R0, gam = orc.make_ic(**ROWS_IC)
@@ -145,7 +146,7 @@ def test_row_split_system_matches_one_process(orc):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rows_worker, args=(r, 2, port, q)) for r in range(2)]
+    procs = [ctx.Process(target=_rows_worker, args=(r, world, port, q)) for r in range(world)]
     for p in procs:
         p.start()
     res = [q.get(timeout=120) for _ in procs]
