@@ -59,3 +59,15 @@ def test_traffic_record_matches_sources():
                     "(bench.py then reports traffic null)")
     cfg = dict(zip(bench.PAIR_CFG_KEYS, [int(v) for v in rec["pair_cfg"].split(",")]))
     assert bench._pair_traffic(rec["workload"], cfg) == rec["dram_bytes_per_launch"]
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    """Under a multi-rank launch only rank 0 times the oracle and prints; the
+    other ranks exit 0 without work or output."""
+    env = dict(os.environ, RANK="1", LOCAL_RANK="1", WORLD_SIZE="2")
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--workload", "binary_1k", "--steps", "1", "--warmup", "0",
+                          "--gpus", "2"], capture_output=True, text=True, timeout=300, cwd=ROOT,
+                         env=env)
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert not [l for l in out.stdout.splitlines() if l.startswith("{")]
