@@ -214,6 +214,51 @@ def _config(name, w, extra=None):
     return cfg
 
 
+# ------------------------------------------------------------------ error against the oracle
+def _rms_rel(a, ref):
+    """sqrt(sum |a - ref|^2 / sum |ref|^2) over elements (the per-step force
+    metric of the parity tests)."""
+    num = float(np.sum((np.asarray(a) - np.asarray(ref)) ** 2))
+    den = float(np.sum(np.asarray(ref) ** 2))
+    return float(np.sqrt(num / den)) if den > 0 else float(np.sqrt(num))
+
+
+def _oracle_ic(desc, params=None):
+    """(m, R0, gamma) of a description from the oracle's own recipe."""
+    from oracle import oracle
+    _, _, m, R, g = oracle.make_ic(desc["n_donor"], desc["n_accretor"], desc["q"],
+                                   f_donor=desc["f_donor"], f_accretor=desc["f_accretor"],
+                                   sigma_v=desc.get("sigma_v", 1e-3), seed=desc.get("seed", 0),
+                                   stream=desc.get("stream", 0))
+    return m, R, g
+
+
+def _sample_rows(n, n_donor, nrows, seed):
+    """Sampled rows plus the ends of the donor and accretor ranges."""
+    import synth
+    edge = [0, n_donor - 1, n_donor, n - 1]
+    rnd = (synth.u01(seed, 77, nrows) * n).astype(np.int64)
+    return np.unique(np.clip(np.concatenate([edge, rnd]), 0, n - 1))
+
+
+def force_error(desc, eps, beta, x, v, a_gpu, rows, k, ic=None):
+    """Error of the library's accelerations a_gpu (n x 3) on `rows` against
+    the FP64 oracle's direct sum (Eqs. 4-6) at the same state (x, v) with the
+    element radii of step k (donor growth law)."""
+    from oracle import oracle
+    m, R0, g = ic if ic is not None else _oracle_ic(desc)
+    R = np.array(R0, dtype=np.float64)
+    nd = desc["n_donor"]
+    rate = desc.get("expand_rate", 0.0)
+    if rate:
+        R[:nd] *= oracle.donor_scale(k, desc["f_donor"], rate, desc.get("expand_steps", -1))
+    ref = oracle.forces_rows(rows, x, v, m, R, g, G=1.0, eps=eps, beta=beta)
+    got = np.asarray(a_gpu)[rows]
+    return {"force_rms_rel": _rms_rel(got, ref),
+            "force_max_abs_rel": float(np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)),
+            "rows": int(len(rows)), "step": int(k), "vs": "oracle (FP64 direct sum)"}
+
+
 # ------------------------------------------------------------------ CPU oracle timing
 def _oracle_sample(w, target_s=10.0, seed_rows=11):
     """Time the FP64 oracle's direct sum on a bounded sample of rows of the
@@ -232,12 +277,12 @@ def _oracle_sample(w, target_s=10.0, seed_rows=11):
     nrows = int(min(n, max(64, 64 * target_s / dt)))
     rows = (synth.u01(seed_rows, 2, nrows) * n).astype(np.int64)
     t0 = time.perf_counter()
-    oracle.forces_rows(rows, x, v, m, R, g, G=1.0, eps=w["eps"], beta=0.5)
+    ref = oracle.forces_rows(rows, x, v, m, R, g, G=1.0, eps=w["eps"], beta=0.5)
     el = time.perf_counter() - t0
     pairs = float(nrows) * n
     return pairs / el, oracle.num_threads(), (
         f"FP64 oracle direct sum (Eqs. 4-6) for {nrows} sampled elements against all {n} "
-        f"elements ({pairs:.3e} pairs, {el:.1f} s)"), (x, v, m, R, g), el
+        f"elements ({pairs:.3e} pairs, {el:.1f} s)"), (x, v, m, R, g), el, rows, ref
 
 
 def run_reference(args):
@@ -294,7 +339,8 @@ def measure_batched(nbm, torch, dev, stream, args, ws, rank):
     [2,048, 65,536]) advanced in one batch: one persistent pair-kernel launch
     per step for all systems.  Systems are dealt to ranks (no exchange).
     Compared with the same systems advanced one at a time through the
-    single-system API, with and without FP64 diagnostics every step."""
+    single-system API, with and without FP64 diagnostics every step, each
+    system timed on its own (no rescaling)."""
     import synth
     from paper_2303_12166_gb300.dist import max_over_ranks, shard, sum_over_ranks
     systems = synth.sweep_systems(args.sweep_systems, seed=0)
@@ -316,6 +362,19 @@ def measure_batched(nbm, torch, dev, stream, args, ws, rank):
     torch.cuda.synchronize(dev)
     b.sync()
     prof = b.profile_read(reset=True)
+    # error against the oracle of three systems (smallest, median, largest)
+    # at their state after the timed steps
+    acc = []
+    if rank == 0:
+        order = sorted(range(len(mine)), key=lambda i: descs[i].n_donor + descs[i].n_accretor)
+        for i in sorted({order[0], order[len(order) // 2], order[-1]}):
+            xv, _, meta = b.get_state(i, with_acc=False)
+            a = b.forces(i)
+            d = systems[mine[i]]
+            n_i = d["n_donor"] + d["n_accretor"]
+            e = force_error(d, SWEEP_PARAMS["eps"], SWEEP_PARAMS["beta"], xv[:, :3], xv[:, 3:],
+                            a, _sample_rows(n_i, d["n_donor"], 256, 4 + i), int(meta.step))
+            acc.append(dict(e, system=int(mine[i]), n=int(n_i)))
     b.close()
     ms = max_over_ranks(ev0.elapsed_time(ev1), dev)
     pairs_mine = float(sum((d.n_donor + d.n_accretor) ** 2 for d in descs))
@@ -329,40 +388,39 @@ def measure_batched(nbm, torch, dev, stream, args, ws, rank):
            "pair_cfg": {k: tuned[k] for k in PAIR_CFG_KEYS},
            "phase_ms": {"pair": prof["pair_ms"], "contact": prof["contact_ms"],
                         "update": prof["update_ms"]},
-           "gpu_launches": int(prof["kernels"])}
-    if rank == 0 and args.per_system_sample > 0:
-        # the same kind of systems one at a time (a sample, extrapolated per
-        # system-step): plain stepping, and stepping with FP64 diagnostics
-        sample = [systems[s] for s in range(0, len(systems), len(systems) // args.per_system_sample)]
-        sample = sample[:args.per_system_sample]
-        sysms = [nbm.System(nbm.nb_desc_default(**d), nbm.nb_params_default(**SWEEP_PARAMS),
-                            stream=stream) for d in sample]
-        k = 3
-        for sy in sysms:
-            sy.step(1)
-            sy.sync()
-        t0 = time.perf_counter()
-        for sy in sysms:
-            sy.step(k)
-            sy.sync()
-        plain = len(sysms) * k / (time.perf_counter() - t0)
-        t0 = time.perf_counter()
-        for sy in sysms:
-            for _ in range(k):
+           "gpu_launches": int(prof["kernels"]),
+           "accuracy": {"systems": acc,
+                        "max_force_rms_rel": max((a["force_rms_rel"] for a in acc), default=None),
+                        "tolerance": 1e-5}}
+    if rank == 0 and ws == 1 and args.per_system_steps > 0:
+        # the same systems one at a time through the single-system API, each
+        # timed on its own: plain stepping (nb_step), and stepping with the
+        # FP64 diagnostics (nb_step(1) + nb_diagnostics) every step
+        k = args.per_system_steps
+        t_plain = t_diag = 0.0
+        for d in systems:
+            with nbm.System(nbm.nb_desc_default(**d), nbm.nb_params_default(**SWEEP_PARAMS),
+                            stream=stream) as sy:
                 sy.step(1)
                 sy.diagnostics()
-        diag = len(sysms) * k / (time.perf_counter() - t0)
-        for sy in sysms:
-            sy.close()
-        # the sample's size mix differs from the sweep's; normalise per pair
-        pairs_sample = float(sum((d["n_donor"] + d["n_accretor"]) ** 2 for d in sample))
-        per_sys_pairs = pairs / len(systems)
+                sy.sync()
+                t0 = time.perf_counter()
+                sy.step(k)
+                sy.sync()
+                t_plain += time.perf_counter() - t0
+                t0 = time.perf_counter()
+                for _ in range(k):
+                    sy.step(1)
+                    sy.diagnostics()
+                t_diag += time.perf_counter() - t0
         out["per_system_path"] = {
-            "systems_sampled": len(sample), "steps": k,
-            "plain_system_steps_per_s": plain * (pairs_sample / len(sample)) / per_sys_pairs,
-            "fp64_diag_system_steps_per_s": diag * (pairs_sample / len(sample)) / per_sys_pairs,
-            "note": "one system at a time through nb_step / nb_diagnostics, rescaled to the "
-                    "sweep's mean pairs per system"}
+            "systems": len(systems), "steps_each": k,
+            "plain_system_steps_per_s": len(systems) * k / t_plain,
+            "fp64_diag_system_steps_per_s": len(systems) * k / t_diag,
+            "note": "every system of the sweep, one at a time through nb_step / "
+                    "nb_diagnostics, host wall clock per system (no rescaling); the batched "
+                    "form's results equal these runs bit for bit (tested), so both forms have "
+                    "the same error against the oracle"}
         out["speedup_vs_per_system_fp64_diag"] = out["value"] / \
             out["per_system_path"]["fp64_diag_system_steps_per_s"]
         out["speedup_vs_per_system_plain"] = out["value"] / \
@@ -383,6 +441,13 @@ def measure_fp64_path(nbm, torch, dev, stream, args):
         with nbm.System(desc, params, stream=stream) as sy:
             if prec == 32:
                 sy.autotune(1)
+            a0 = sy.forces()
+            xv0 = sy.get_state(with_acc=False)[0]
+            n = w["n_donor"] + w["n_accretor"]
+            out[f"fp{prec}_accuracy"] = dict(
+                force_error(w, w["eps"], 0.5, xv0[:, :3], xv0[:, 3:], a0,
+                            _sample_rows(n, w["n_donor"], 512, 3), 0),
+                tolerance=1e-5 if prec == 32 else 1e-12)
             sy.step(1)
             sy.sync()
             sy.profile(True)
@@ -419,6 +484,31 @@ def measure_served(nbm, stream, args):
     finally:
         nbm.nb_server_destroy(srv)
     bad = [r for r in res if r["status"] != 0]
+    # three requests (the least work) run again alone with the server's pair
+    # configuration: the same diagnostics bit for bit, and the error against
+    # the oracle of the accelerations at their final state
+    acc = []
+    cheap = sorted(range(len(trace)), key=lambda r: (trace[r]["desc"]["n_donor"] +
+                                                      trace[r]["desc"]["n_accretor"]) ** 2 *
+                   trace[r]["nsteps"])[:3]
+    for r in cheap:
+        d = dict(trace[r]["desc"])
+        with nbm.System(nbm.nb_desc_default(**d), nbm.nb_params_default(**SWEEP_PARAMS),
+                        stream=stream) as sy:
+            sy.set_pair_cfg(*[scfg[k] for k in PAIR_CFG_KEYS])
+            sy.step(trace[r]["nsteps"])
+            sy.sync()
+            dg = sy.diagnostics()
+            xv, _, meta = sy.get_state(with_acc=False)
+            a = sy.forces()
+        served_d = res[r]["diag"]
+        same = all(np.array_equal(np.asarray(dg[k]), np.asarray(served_d[k]))
+                   for k in ("step", "e_kin", "p", "l", "com", "separation", "n_past_L1",
+                             "n_in_accretor_lobe", "n_unbound"))
+        n_r = d["n_donor"] + d["n_accretor"]
+        e = force_error(d, SWEEP_PARAMS["eps"], SWEEP_PARAMS["beta"], xv[:, :3], xv[:, 3:], a,
+                        _sample_rows(n_r, d["n_donor"], 256, 40 + r), int(meta.step))
+        acc.append(dict(e, request=int(r), n=int(n_r), alone_equals_served=bool(same)))
     lat = np.array([r["t_finish"] - r["t_submit"] for r in res])
     span = max(r["t_finish"] for r in res) - min(r["t_submit"] for r in res)
     pairs = float(sum(r["n"] ** 2 * r["steps"] for r in res))
@@ -431,7 +521,10 @@ def measure_served(nbm, stream, args):
             "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)),
             "makespan_s": span, "value": pairs / span, "unit": "pairs/s",
-            "system_steps_per_s": steps / span}
+            "system_steps_per_s": steps / span,
+            "accuracy": {"requests": acc,
+                         "max_force_rms_rel": max((a["force_rms_rel"] for a in acc), default=None),
+                         "tolerance": 1e-5}}
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -464,6 +557,9 @@ def run_ours(args):
         tuned = sysm.pair_cfg()
     else:
         tuned = sysm.autotune(2) if not args.fp64 else sysm.pair_cfg()
+    # accelerations at the initial state with the configuration timed below
+    # (compared with the oracle after the timed region)
+    a_initial = sysm.forces()
 
     sysm.step(args.warmup)
     sysm.sync()
@@ -541,11 +637,40 @@ def run_ours(args):
                "h2d_bytes_per_step": int(n * (48 + 24)), "d2h_bytes_per_step": int(n * (48 + 24)),
                "steps": steps_e2e, "host_buffers": "page-locked"}
 
+    # the state after every timed and end-to-end step, and its accelerations
+    xv_f, _, meta_f = sysm.get_state(with_acc=False)
+    a_final = sysm.forces()
+
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        rate, cores, sample, _, _ = _oracle_sample(w, target_s=args.cpu_seconds)
-        cpu = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle",
-               "sample": sample}
+    accuracy = None
+    if rank == 0:
+        eps, beta = w["eps"], 0.5
+        ic = None
+        if ws == 1 and not args.no_cpu_baseline:
+            rate, cores, sample, full_ic, _, rows0, ref0 = _oracle_sample(
+                w, target_s=args.cpu_seconds)
+            cpu = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                   "sample": sample}
+            ic = full_ic[2:]
+            initial = {"force_rms_rel": _rms_rel(a_initial[rows0], ref0),
+                       "force_max_abs_rel": float(np.abs(a_initial[rows0] - ref0).max() /
+                                                  np.abs(ref0).max()),
+                       "rows": int(len(rows0)), "step": 0,
+                       "vs": "oracle (FP64 direct sum), the cpu_baseline sample's rows"}
+        else:
+            from oracle import oracle
+            x0, v0, m0, R0, g0 = oracle.make_ic(
+                w["n_donor"], w["n_accretor"], w["q"], f_donor=w["f_donor"],
+                f_accretor=w["f_accretor"], sigma_v=w["sigma_v"], seed=w["seed"])
+            ic = (m0, R0, g0)
+            initial = force_error(w, eps, beta, x0, v0, a_initial,
+                                  _sample_rows(n, w["n_donor"], 1024, 1), 0, ic)
+        final = force_error(w, eps, beta, xv_f[:, :3], xv_f[:, 3:], a_final,
+                            _sample_rows(n, w["n_donor"], 1024, 2), int(meta_f.step), ic)
+        accuracy = {"initial": initial, "final": final,
+                    "tolerance": 1e-12 if args.fp64 else 1e-5,
+                    "metric": "RMS-relative acceleration error on the sampled rows, at the "
+                              "library's own state and the radii of that step"}
 
     working_set = sysm.info.device_bytes
     sysm.close()
@@ -587,6 +712,7 @@ def run_ours(args):
                          "kernel": "pair_sym_kernel" if sym else "pair_f32_kernel",
                          "kernel_ms": pair_ms},
             "cpu_baseline": cpu,
+            "accuracy": accuracy,
             "e2e": e2e,
             "gpu_launches": int(prof["kernels"]),
             "phase_ms": {"pair": prof["pair_ms"], "contact": prof["contact_ms"],
@@ -616,8 +742,9 @@ def main(argv=None):
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-sweep and served measurements")
     ap.add_argument("--sweep-systems", type=int, default=256)
-    ap.add_argument("--batched-steps", type=int, default=10)
-    ap.add_argument("--per-system-sample", type=int, default=8)
+    ap.add_argument("--batched-steps", type=int, default=100)
+    ap.add_argument("--per-system-steps", type=int, default=5,
+                    help="steps each sweep system is timed for alone (0: skip)")
     ap.add_argument("--served-requests", type=int, default=64)
     ap.add_argument("--served-steps-div", type=int, default=100)
     ap.add_argument("--pair-cfg", default="",

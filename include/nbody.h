@@ -442,11 +442,16 @@ void nb_server_destroy(nb_server_t srv);
  * Its scratch is one fixed array of about 2.4 MB in the library's device
  * image, held by every GPU that loads the library until the process exits;
  * the call allocates nothing (no cudaMalloc, cudaFree or allocating library
- * routine).  The first call on a device looks up the array's device address
- * with that device current; make it before any stream capture.  Calls share
- * the array: calls whose work overlaps on the GPU race and must be
- * serialised.  Blocks until acc_out is written; NB_ETIMEOUT if a device
- * wait gave up. */
+ * routine).  The first call on a device is where the driver loads the
+ * library's device code (lazy module loading, CUDA's default) and with it
+ * places the scratch array in device memory; it also looks up the array's
+ * device address with that device current.  Make that first call at set-up
+ * time; later calls take no device memory.  Calls share the array: calls
+ * whose work overlaps on the GPU race and must be serialised.  Blocks until
+ * acc_out is written (it copies a status word to host memory and
+ * synchronises the stream), so it must not be called on a stream that is
+ * capturing: NB_EINVAL there, and the capture is left intact.  NB_ETIMEOUT
+ * if a device wait gave up. */
 #define NB_NOALLOC_MAX_N 16384
 nb_status nb_pair_forces_noalloc(const double* xyzm, int64_t n, double G, double eps,
                                  double* acc_out, void* stream);

@@ -21,10 +21,15 @@
 //
 // The arithmetic is the library's FP32 pair kernel (nb_pair.cu) unchanged,
 // run with one built launch shape; the result is the FP64 sum of its
-// partial sums.  The call blocks until acc_out is written.  The device
-// address of the array is looked up (cudaGetSymbolAddress) by the first
-// call on each device, with that device current; make that first call
-// before any stream capture begins.
+// partial sums.  The call blocks until acc_out is written: it ends with a
+// copy of the status word to host memory and a stream synchronisation, which
+// a stream capture does not allow, so it refuses (NB_EINVAL) a stream that is
+// capturing instead of breaking the caller's capture.  The first call on a
+// device is where the driver loads this file's device code (under lazy
+// module loading) and so places the scratch array in device memory, and it
+// looks up the array's device address (cudaGetSymbolAddress) with that
+// device current; make that first call at set-up time, before any stream
+// capture begins.  Later calls take no device memory.
 #include <cstring>
 #include <mutex>
 
@@ -170,6 +175,17 @@ extern "C" nb_status nb_pair_forces_noalloc(const double* xyzm, int64_t n, doubl
                          (long long)n, (long long)kMaxN);
     if (!(G >= 0) || !(eps >= 0))
         return set_error(NB_EINVAL, "nb_pair_forces_noalloc: need G >= 0 and eps >= 0");
+    {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        const cudaError_t ce = cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cs);
+        if (ce != cudaSuccess)
+            return set_error(NB_ECUDA, "nb_pair_forces_noalloc: cudaStreamIsCapturing: %s",
+                             cudaGetErrorString(ce));
+        if (cs != cudaStreamCaptureStatusNone)
+            return set_error(NB_EINVAL,
+                             "nb_pair_forces_noalloc: the stream is capturing (the call copies "
+                             "to host memory and synchronises the stream)");
+    }
     void* addr = nullptr;
     nb_status st = scratch_address(&addr);
     if (st != NB_OK) return st;

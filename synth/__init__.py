@@ -108,18 +108,21 @@ def served_trace(nreq: int = 64, seed: int = 0, rate_hz: float = 20.0, nmin: int
                  nmax: int = 262144, smin: int = 1000, smax: int = 20000, steps_div: int = 1):
     """Poisson arrivals (exponential gaps, mean 1/rate_hz), element count
     log-uniform in [nmin, nmax] (3/4 donor), steps uniform in [smin, smax]
-    (divided by steps_div), q uniform in [0.1, 1]."""
+    (divided by steps_div), q uniform in [0.1, 1], donor expansion rate
+    uniform in [0.5, 2]e-5 r_L per step (the sweep's range)."""
     gaps = -np.log(1.0 - u01(seed, 31, nreq)) / rate_hz
     t = np.cumsum(gaps) - gaps[0]
     n = log_uniform_int(nmin, nmax, nreq, seed, 32)
     steps = smin + np.floor(u01(seed, 33, nreq) * (smax - smin + 1)).astype(np.int64)
     steps = np.maximum(1, steps // steps_div)
     q = uniform_between(0.1, 1.0, nreq, seed, 34)
+    rate = uniform_between(0.5e-5, 2.0e-5, nreq, seed, 35)
     out = []
     for r in range(nreq):
         nd = int(round(0.75 * n[r]))
         out.append(dict(t_arrival=float(t[r]), nsteps=int(steps[r]),
                         desc=dict(n_donor=nd, n_accretor=int(n[r]) - nd, q=float(q[r]),
-                                  f_donor=0.9, f_accretor=0.5, sigma_v=1e-3, seed=seed,
+                                  f_donor=0.9, f_accretor=0.5, expand_rate=float(rate[r]),
+                                  expand_steps=-1, sigma_v=1e-3, seed=seed,
                                   stream=5000 + r)))
     return out

@@ -177,6 +177,56 @@ def test_forces_full_size_sampled(nbm, orc, name, nrows):
     assert rms_rel(a[rows], ref) <= 1e-5
 
 
+def _grown_radii(orc, R0, n_donor, desc, k):
+    """Element radii of step k: donor radii scaled by the growth law, the
+    accretor's fixed."""
+    R = np.array(R0, dtype=np.float64)
+    R[:n_donor] *= orc.donor_scale(k, desc["f_donor"], desc["expand_rate"], desc["expand_steps"])
+    return R
+
+
+def test_binary_64k_growing_donor_sampled(nbm, orc):
+    """The 65,536-element binary (q = 0.3, eps 0.005, dt 5e-4) with the donor
+    growing from 0.9 to 1.15 r_L over 10^4 steps, stepped on the GPU at full
+    size.  At steps 25 and 50: the accelerations at the state (x^k, v^k) with
+    the radii of step k, and the stored a^k of the integrator at (x^k,
+    v^{k-1/2}), against the oracle on sampled rows -- 320 random rows, the
+    donor/accretor index boundary and the 64 donor elements nearest the
+    accretor (the donor's surface facing L1, where its growth acts first)."""
+    desc, params = workload_kwargs("binary_64k")
+    ox, ov, om, oR, og = oracle_ic(orc, desc, params)
+    nd, dt = desc["n_donor"], params["dt"]
+    with _make(nbm, desc, params) as s:
+        n = s.n
+        k = 0
+        for k_next in (25, 50):
+            s.step(k_next - k)
+            s.sync()
+            k = k_next
+            x, v, a_stored, meta = _state(s)
+            assert meta.step == k
+            a = s.forces()
+            near_l1 = np.argsort(x[:nd, 0])[:64]  # donor centre at +x, accretor at -x
+            rows = np.unique(np.concatenate([
+                [0, 1, nd - 1, nd, nd + 1, n - 1], near_l1,
+                (synth.u01(7, k, 320) * n).astype(np.int64)]))
+            Rk = _grown_radii(orc, oR, nd, desc, k)
+            kw = dict(G=1.0, eps=params["eps"], beta=params["beta"])
+            ref = orc.forces_rows(rows, x, v, om, Rk, og, **kw)
+            assert rms_rel(a[rows], ref) <= 1e-5
+            # the integrator's a^k used the half-step velocity v^{k-1/2}
+            vh = v - 0.5 * dt * a_stored
+            ref_h = orc.forces_rows(rows, x, vh, om, Rk, og, **kw)
+            assert rms_rel(a_stored[rows], ref_h) <= 1e-5
+            # the growth is visible at this tolerance: the initial radii
+            # give accelerations farther off than the tolerance
+            ref0 = orc.forces_rows(rows, x, v, om, oR, og, **kw)
+            assert rms_rel(ref0, ref) > 1e-4
+            assert s.diagnostics()["r_donor"] == pytest.approx(
+                orc.donor_scale(k, desc["f_donor"], desc["expand_rate"], desc["expand_steps"]),
+                rel=1e-15)
+
+
 # ---------------------------------------------------------------- diagnostics
 def test_diagnostics_match_oracle(nbm, orc):
     desc, params = workload_kwargs("binary_1k")
