@@ -302,6 +302,38 @@ nb_status Batch::free_(void** p) {
     return NB_OK;
 }
 
+int64_t onesided_chunks(int64_t n, int64_t I, int tile, int64_t slots) {
+    // Chunk count from the system's own size and the launch shape only
+    // (never from the rest of the batch), so a system gives bitwise the same
+    // result alone and in a batch: the smallest count whose items fill the
+    // persistent grid's waves to 96 %, with chunks of at least kMinChunkTiles
+    // tiles.
+    constexpr int64_t kMinChunkTiles = 16;
+    const int64_t nib = (n + I - 1) / I;
+    const int64_t ntiles = (n + tile - 1) / tile;
+    const int64_t smax = std::min<int64_t>(NB_MAX_CHUNKS, ntiles);
+    const int64_t smax_sys = std::max<int64_t>(1, std::min(smax, ntiles / kMinChunkTiles));
+    slots = std::max<int64_t>(1, slots);
+    double best = -1;
+    int64_t S = 1;
+    for (int64_t cand = 1; cand <= smax_sys; ++cand) {
+        const int64_t items = nib * cand;
+        const int64_t waves = (items + slots - 1) / slots;
+        const double eff = (double)items / (double)(waves * slots);
+        if (eff > best + 1e-12) {
+            best = eff;
+            S = cand;
+        }
+        if (eff >= 0.96) {
+            S = cand;
+            break;
+        }
+    }
+    // the count the tiles-per-chunk rounding leaves
+    const int64_t tpc = (ntiles + S - 1) / S;
+    return (ntiles + tpc - 1) / tpc;
+}
+
 static uint32_t next_pow2(uint64_t v) {
     uint64_t p = 1;
     while (p < v) p <<= 1;
@@ -322,6 +354,7 @@ nb_status Batch::init(const std::vector<int64_t>& n_per_slot, int prec, cudaStre
     runs_.assign(nsys, {});
     rmax_d0_.assign(nsys, 0.0);
     rmax_a_.assign(nsys, 0.0);
+    fx_ok_.assign(nsys, 0);
     int64_t off = 0;
     for (int s = 0; s < nsys; ++s) {
         const int64_t n = n_per_slot[s];
@@ -352,7 +385,13 @@ nb_status Batch::init(const std::vector<int64_t>& n_per_slot, int prec, cudaStre
     }
     NB_TRY(alloc_((void**)&d_.sys_of, nt * sizeof(int32_t)));
     NB_TRY(alloc_((void**)&d_.cont, nt * sizeof(double4_32a)));
-    d_.nchunk_alloc = 0;
+    {
+        // fixed-point pair sums of the symmetric kernel: three int64 arrays
+        unsigned long long* base = nullptr;
+        NB_TRY(alloc_((void**)&base, 3 * nt * sizeof(unsigned long long)));
+        d_.facc = Fx3SoA{base, base + nt, base + 2 * nt};
+    }
+    d_.part_cap = 0;
     d_.part = nullptr;
     uint64_t nb = std::max<uint64_t>(4096, 2 * (uint64_t)off);
     nb = std::min<uint64_t>(nb, contact_max_buckets());
@@ -429,6 +468,32 @@ nb_status Batch::load(int s, const SystemInit& si, bool defer_forces) {
     c.rmax_donor0 = rd;
     c.rmax_acc = ra;
     if (!(rd > 0 || ra > 0)) c.contacts = 0;  // no element has a radius
+    {
+        // Fixed-point scale of the symmetric kernel's sums: every share of an
+        // element's pair term has magnitude <= G m_j / eps^2, so G M_sys /
+        // eps^2 bounds the sum of their magnitudes; 2^s puts that bound at
+        // <= 2^60 (no partial sum can overflow an int64).  The layout is used
+        // where its resolution 2^-s, relative to the acceleration scale
+        // G M_sys / L^2 of the system (L: the largest distance of an element
+        // from the centre of mass), is at most 2^-32: (L / eps)^2 <= 2^28.
+        double msum = 0, l2 = 0;
+        for (int64_t i = 0; i < si.n; ++i) {
+            msum += si.m[i];
+            double d2 = 0;
+            for (int k = 0; k < 3; ++k) {
+                const double d = si.x[3 * i + k] - si.origin[k];
+                d2 += d * d;
+            }
+            l2 = std::max(l2, d2);
+        }
+        const double bound = si.eps > 0 ? si.G * msum / (si.eps * si.eps) : 0.0;
+        int sh = bound > 0 ? (int)std::floor(60.0 - std::log2(bound)) : 120;
+        sh = std::min(120, std::max(-120, sh));
+        c.fx_scale = std::ldexp(1.0, sh);
+        c.fx_inv = std::ldexp(1.0, -sh);
+        c.fx_scale_f = std::ldexp(1.0f, sh);
+        fx_ok_[s] = si.eps > 0 && std::sqrt(l2) <= 16384.0 * si.eps ? 1 : 0;
+    }
     k_[s] = 0;
     mass_[s] = si.m;
     runs_[s].clear();
@@ -497,7 +562,6 @@ nb_status Batch::set_pair_cfg(const PairCfg& c) {
                          "pair configuration tile=%d bi=%d threads=%d minb=%d nr=%d not built",
                          c.tile, c.bi, c.threads, c.minb, c.nr);
     cfg_ = c;
-    cfg_explicit_ = true;
     planned_ = false;
     return NB_OK;
 }
@@ -509,10 +573,10 @@ double Batch::pairs_per_step() const {
     return p;
 }
 
-// ordered pair interactions an item evaluates: in the symmetric list an
-// item against later blocks (j0 > i0) serves both sides
-static double item_pairs(const PairItem& it, bool sym) {
-    return (sym && it.j0 > it.i0 ? 2.0 : 1.0) * (double)it.iend_rel * (double)it.nj;
+// ordered pair interactions an item evaluates: an item of the symmetric
+// kernel against later blocks (chunk < 0) serves both sides
+static double item_pairs(const PairItem& it) {
+    return (it.chunk < 0 ? 2.0 : 1.0) * (double)it.iend_rel * (double)it.nj;
 }
 
 nb_status Batch::plan_pairs_() {
@@ -527,39 +591,15 @@ nb_status Batch::plan_pairs_() {
     for (int s = 0; s < nslots(); ++s)
         if (sc_[s].active) act.push_back(s);
     items_.clear();
-    int maxchunks = 1;
     dynamic_ = act.size() > 1;
     for (int s : act) {
         SysConst& c = sc_[s];
         const int64_t nib = (c.n + I - 1) / I;
         const int64_t ntiles = (c.n + tile - 1) / tile;
-        const int64_t smax = std::min<int64_t>(NB_MAX_CHUNKS, ntiles);
-        // Chunk count from the system's own size and the launch shape only
-        // (never from the rest of the batch), so a system gives bitwise the
-        // same result alone and in a batch: the smallest count whose items
-        // fill the persistent grid's waves to 96 %, with chunks of at least
-        // kMinChunkTiles tiles.
-        constexpr int64_t kMinChunkTiles = 16;
-        const int64_t smax_sys = std::max<int64_t>(1, std::min(smax, ntiles / kMinChunkTiles));
-        double best = -1;
-        int64_t S = 1;
-        for (int64_t cand = 1; cand <= smax_sys; ++cand) {
-            const int64_t items = nib * cand;
-            const int64_t waves = (items + slots - 1) / slots;
-            const double eff = (double)items / (double)(waves * slots);
-            if (eff > best + 1e-12) {
-                best = eff;
-                S = cand;
-            }
-            if (eff >= 0.96) {
-                S = cand;
-                break;
-            }
-        }
+        int64_t S = onesided_chunks(c.n, I, tile, slots);
         const int64_t tpc = (ntiles + S - 1) / S;  // tiles per chunk
         S = (ntiles + tpc - 1) / tpc;
         c.nchunks = (int32_t)S;
-        maxchunks = std::max<int>(maxchunks, (int)S);
         for (int64_t ib = 0; ib < nib; ++ib) {
             for (int64_t ch = 0; ch < S; ++ch) {
                 PairItem it{};
@@ -603,15 +643,24 @@ nb_status Batch::plan_pairs_() {
             return (int64_t)a.iend_rel * a.nj > (int64_t)b.iend_rel * b.nj;
         });
     }
-    int maxslots = maxchunks;
-    int64_t jp_total = 0;
+    // partial slots: each system's own range, c.nchunks slots of c.npad
+    // elements (the one-sided layout; a symmetric plan uses them for the
+    // potential pass and for systems not summed in fixed point)
+    int64_t part_total = 0;
+    for (int s : act) {
+        SysConst& c = sc_[s];
+        c.part_off = part_total;
+        part_total += (int64_t)c.nchunks * c.npad;
+    }
     sitems_.clear();
-    for (SysConst& c : sc_) c.sym = 0;
+    for (SysConst& c : sc_) c.fxp = 0;
     if (f32 && cfg_.sym) {
-        // Each unordered pair once: block K against itself (slot 0, one-sided)
-        // and against the later blocks in items of at most C tiles (slots
-        // 1, 2, ...), C from the system's own size and the launch shape only,
-        // so that a system gives bitwise the same result alone and in a batch.
+        // Each unordered pair once: block K against itself (one-sided) and
+        // against the later blocks in items of at most C tiles (chunk -1: both
+        // sides), C from the system's own size and the launch shape only, so
+        // that a system gives bitwise the same result alone and in a batch.
+        // A system whose softening is too small for the fixed-point sums
+        // keeps its one-sided items.
         const int64_t B = I;
         const int64_t tpb = B / tile;
         constexpr int64_t kItemsPerSlot = 24;
@@ -619,24 +668,21 @@ nb_status Batch::plan_pairs_() {
         constexpr int64_t kMaxRowItems = 64;
         for (int s : act) {
             SysConst& c = sc_[s];
+            if (!fx_ok_[s]) {
+                for (const PairItem& it : items_)
+                    if (it.sys == s) sitems_.push_back(it);
+                continue;
+            }
+            c.fxp = 1;
             const int64_t nbk = (c.n + B - 1) / B;
             const int64_t ntiles = (c.n + tile - 1) / tile;
             int64_t toff = 0;
             for (int64_t K = 0; K < nbk; ++K) toff += std::max<int64_t>(0, ntiles - (K + 1) * tpb);
-            // at most kMaxRowItems items per row (partial slots per element)
+            // at most kMaxRowItems items per row
             const int64_t C = std::max<int64_t>(
                 std::max<int64_t>(kMinChunkTiles,
                                   (toff + slots * kItemsPerSlot - 1) / (slots * kItemsPerSlot)),
                 (ntiles - tpb + kMaxRowItems - 1) / kMaxRowItems);
-            c.sym = 1;
-            c.sym_blk = (int32_t)B;
-            c.sym_tpb = (int32_t)tpb;
-            c.sym_chunk = (int32_t)C;
-            c.sym_ntiles = ntiles;
-            c.jp_off = jp_total;
-            jp_total += nbk * (nbk - 1) / 2 * B;
-            maxslots = std::max<int>(
-                maxslots, 1 + (int)((std::max<int64_t>(0, ntiles - tpb) + C - 1) / C));
             for (int64_t K = 0; K < nbk; ++K) {
                 PairItem d{};
                 d.i0 = c.off + K * B;
@@ -651,53 +697,28 @@ nb_status Batch::plan_pairs_() {
                     PairItem it = d;
                     it.j0 = c.off + (jt0 + r * C) * tile;
                     it.nj = (int32_t)(std::min<int64_t>(C, ntiles - jt0 - r * C) * tile);
-                    it.chunk = (int32_t)(1 + r);
+                    it.chunk = -1;
                     sitems_.push_back(it);
                 }
             }
         }
         std::stable_sort(sitems_.begin(), sitems_.end(), [](const PairItem& a, const PairItem& b) {
-            return item_pairs(a, true) > item_pairs(b, true);
+            return item_pairs(a) > item_pairs(b);
         });
-        if (maxslots > NB_MAX_CHUNKS * 4)
-            return set_error(NB_EINVAL, "symmetric pair plan needs %d partial slots", maxslots);
     }
-    {
-        // room for the buffers this plan grows (checked before anything is
-        // freed, so a plan that does not fit leaves the batch as it was)
-        size_t need = 0, have = 0;
-        if (maxslots > d_.nchunk_alloc)
-            need += (size_t)(maxslots - d_.nchunk_alloc) * d_.ntot * sizeof(double4_32a);
-        if (jp_total > jpart_cap_) need += 3 * (size_t)(jp_total - jpart_cap_) * sizeof(float);
-        size_t total = 0;
-        if (need > 0 && cudaMemGetInfo(&have, &total) == cudaSuccess && need + (64u << 20) > have) {
-            if (f32 && cfg_.sym && !cfg_explicit_) {
-                // the default symmetric plan does not fit: one-sided instead
-                cfg_ = kOneSided;
-                return plan_pairs_();
-            }
+    if (part_total > d_.part_cap) {
+        // room for the partial slots (checked before anything is freed, so a
+        // plan that does not fit leaves the batch as it was)
+        const size_t need = (size_t)(part_total - d_.part_cap) * sizeof(double4_32a);
+        size_t have = 0, total = 0;
+        if (cudaMemGetInfo(&have, &total) == cudaSuccess && need + (64u << 20) > have)
             return set_error(NB_ENOMEM,
                              "pair plan needs %.2f GB more device memory, %.2f GB free",
                              need / 1e9, have / 1e9);
-        }
-    }
-    if (maxslots > d_.nchunk_alloc) {
-        // grow the partial-sum buffer (chunk-major)
-        d_.nchunk_alloc = 0;
+        d_.part_cap = 0;
         NB_TRY(free_((void**)&d_.part));
-        NB_TRY(alloc_((void**)&d_.part, (size_t)maxslots * d_.ntot * sizeof(double4_32a)));
-        d_.nchunk_alloc = maxslots;
-    }
-    if (jp_total > jpart_cap_) {
-        // j-side shares of the symmetric plan: three component arrays
-        jpart_cap_ = 0;
-        float* old = d_.jpart.x;
-        d_.jpart = Vec3SoA{};
-        NB_TRY(free_((void**)&old));
-        float* base = nullptr;
-        NB_TRY(alloc_((void**)&base, 3 * (size_t)jp_total * sizeof(float)));
-        d_.jpart = Vec3SoA{base, base + jp_total, base + 2 * jp_total};
-        jpart_cap_ = jp_total;
+        NB_TRY(alloc_((void**)&d_.part, (size_t)part_total * sizeof(double4_32a)));
+        d_.part_cap = part_total;
     }
     auto upload = [&](const std::vector<PairItem>& v, PairItem*& dptr, int& cap) -> nb_status {
         if ((int)v.size() > cap) {
@@ -740,7 +761,13 @@ nb_status Batch::launch_pairs_(bool pot, int nitems_limit) {
         ctr = counter_d_;
     }
     cudaEvent_t ev = prof_begin_();
-    if (prec_ == 32 && cfg_.sym && !pot) {
+    if (sym) {
+        // the fixed-point sums start from zero every pass
+        bool fx = false;
+        for (const SysConst& c : sc_) fx = fx || (c.active && c.fxp);
+        if (fx)
+            NB_CU(cudaMemsetAsync(d_.facc.x, 0, 3 * (size_t)d_.ntot * sizeof(unsigned long long),
+                                  stream_));
         NB_CU(launch_pair_sym(d_, tmass_d_, sitems_d_, n, cfg_, ctr, stream_));
     } else if (prec_ == 32) {
         PairCfg c = cfg_;
@@ -855,7 +882,7 @@ nb_status Batch::autotune(int reps, PairCfg* best, double* best_ms) {
                              ? (int)list.size()
                              : std::min<int>((int)list.size(), 2 * std::max(cfg_.grid, 1));
         double pairs = 0;
-        for (int q = 0; q < nlim; ++q) pairs += item_pairs(list[q], cfg_.sym != 0);
+        for (int q = 0; q < nlim; ++q) pairs += item_pairs(list[q]);
         if ((st = launch_pairs_(false, nlim)) != NB_OK) break;  // warm-up
         cudaEventRecord(e0, stream_);
         for (int r = 0; r < reps && st == NB_OK; ++r) st = launch_pairs_(false, nlim);
@@ -879,14 +906,13 @@ nb_status Batch::autotune(int reps, PairCfg* best, double* best_ms) {
     kernels_ = 0;
     pairs_done_ = 0;
     cfg_ = st == NB_OK ? best_c : keep;
-    if (st == NB_OK) cfg_explicit_ = true;
     planned_ = false;
     if (st != NB_OK) return st;
     NB_TRY(plan_pairs_());
     if (best) *best = cfg_;
     // report the time of one full pair pass at the measured rate
     double pairs_all = 0;
-    for (const PairItem& it : cfg_.sym ? sitems_ : items_) pairs_all += item_pairs(it, cfg_.sym != 0);
+    for (const PairItem& it : cfg_.sym ? sitems_ : items_) pairs_all += item_pairs(it);
     if (best_ms) *best_ms = best_t * pairs_all;
     return NB_OK;
 }

@@ -15,8 +15,8 @@
 
 namespace nb {
 
-// The one-sided configuration used where the symmetric kernel's buffers do
-// not fit (best one-sided variant: 6 of 8 slots share a reciprocal).
+// The best one-sided configuration (6 of 8 slots share a reciprocal): the
+// server's choice for small slots.
 constexpr PairCfg kOneSided{256, 8, 128, 0, 2, 0, 0, 6, 0};
 
 // Thread-local error text behind nb_last_error().
@@ -61,6 +61,10 @@ double model_roche_rL(double q, double coeff);
 double model_roche_L1(double q);
 nb_status build_system(const nb_desc& d, const nb_params& p, SystemInit& out);
 nb_status check_params(const nb_params& p);
+// j-chunks (partial slots per element) of a system of n elements in the
+// one-sided layout: i-blocks of I elements, tiles of `tile`, a persistent
+// grid of `slots` resident CTAs.
+int64_t onesided_chunks(int64_t n, int64_t I, int tile, int64_t slots);
 
 // A named NVTX range for the scope (profiler timelines and ncu's --nvtx
 // filters); without an attached tool the calls return at once.
@@ -180,12 +184,12 @@ private:
     };
     std::vector<std::vector<MassRun>> runs_;
     std::vector<double> rmax_d0_, rmax_a_;
+    // 1: the system's softening allows the symmetric kernel's fixed-point sums
+    // (SysConst::fxp; the scale is set at load)
+    std::vector<char> fx_ok_;
     // default: the symmetric kernel with rotating shares (12 i-elements per
-    // thread, 2 shared-reciprocal slots); while the caller has not chosen a
-    // configuration, a plan whose share buffers do not fit falls back to the
-    // one-sided kOneSided (O(N) memory)
+    // thread, 2 shared-reciprocal slots)
     PairCfg cfg_{256, 12, 128, 0, 2, 0, 0, 2, 3};
-    bool cfg_explicit_ = false;
     float* tmass_d_ = nullptr;   // per j-tile common G m (see launch_pair_f32)
     int64_t tmass_cap_ = 0;
     std::vector<PairItem> items_;      // one-sided work list (also the potential pass)
@@ -195,7 +199,6 @@ private:
     PairItem* sitems_d_ = nullptr;
     int sitems_cap_ = 0;
     int pot_grid_ = 0;                 // persistent grid of the one-sided list
-    int64_t jpart_cap_ = 0;            // elements of each jpart component array
     int* counter_d_ = nullptr;
     bool dynamic_ = false;
     bool planned_ = false;

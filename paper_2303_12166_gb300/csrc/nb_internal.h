@@ -19,8 +19,10 @@
 //                                       copy of the position (contact term)
 //   v32  3 x float                      FP32 copy of the velocity
 //   sys_of int32                        owning system (-1 for padding)
-// Pair sums land in `part` (double4_32a per element and j-chunk); the contact
-// term in `cont` (double4_32a: a, e_rep).
+// Pair sums land either in `part` (double4_32a per element and j-chunk, each
+// system's slots in a range of its own) or, with the symmetric kernel, in the
+// fixed-point accumulators `facc` (three int64 per element, see SysConst);
+// the contact term in `cont` (double4_32a: a, e_rep).
 #pragma once
 #include <cstdint>
 #include <vector>
@@ -50,19 +52,32 @@ struct SysConst {
     int32_t contacts;   // 0: gravity only
     int32_t nchunks;    // j-chunks whose partial sums form the pair term
     float eps_f;        // eps in FP32
-    // Pair sums taken once per unordered pair (each side gets its share):
-    // blocks of sym_blk elements; block K's own partial slots are 0 (the
-    // block against itself) and 1..ceil(max(0, sym_ntiles - (K+1) sym_tpb) /
-    // sym_chunk) (the later blocks, sym_chunk tiles per slot); the share of
-    // element e of block K from each earlier block I sits in jpart at
-    // jp_off + (K (K-1)/2 + I) sym_blk + (e - K sym_blk).
-    int32_t sym;        // 1: the last force pass used this layout
-    int32_t sym_blk;
-    int32_t sym_tpb;    // j-tiles per block
-    int32_t sym_chunk;  // j-tiles per partial slot
-    int64_t sym_ntiles; // j-tiles of the system
-    int64_t jp_off;
+    // Partial slot ch of element i sits at part[part_off + ch npad + (i - off)]
+    // (part_index below): each system's slots in a range of its own.
+    int64_t part_off;
+    // Fixed-point pair sums of the symmetric kernel (fxp = 1): every share of
+    // the pair term of element i -- the i-side sum of each work item and the
+    // j-side share of every tile -- is rounded to an integer multiple of
+    // fx_inv = 2^-s and added to facc[i] with an integer atomic add.  Integer
+    // addition is associative, so the sum does not depend on the order in
+    // which the persistent CTAs finish: the result is deterministic with one
+    // accumulator per element instead of one slot per (block, element).  The
+    // scale 2^s keeps G M_sys / eps^2 (a bound on the sum of the magnitudes
+    // of all shares of an element) below 2^60, so no partial sum overflows;
+    // the resolution relative to the system's acceleration scale G M_sys / L^2
+    // (L its extent) is (L / eps)^2 2^-60, and the layout is used only where
+    // that is at most 2^-32 (L / eps <= 16384; the other systems of a
+    // symmetric plan are summed one-sided into `part`).
+    int32_t fxp;
+    float fx_scale_f;   // 2^s in FP32
+    double fx_scale;    // 2^s
+    double fx_inv;      // 2^-s
 };
+
+// Index of partial slot ch of element i (batch index) of system c in `part`.
+__host__ __device__ inline int64_t part_index(const SysConst& c, int ch, int64_t i) {
+    return c.part_off + (int64_t)ch * c.npad + (i - c.off);
+}
 
 // Device-written per-system record.
 struct SysMut {
@@ -74,7 +89,9 @@ struct SysMut {
 
 // One unit of the pair kernel: the i-block [i0, i0 + I) (clipped to the
 // system) against the j-range [j0, j0 + nj) of the same system; the sum is
-// written to partial slot `chunk`.
+// written to partial slot `chunk`, or added to the fixed-point accumulators
+// of a system with SysConst::fxp.  chunk < 0 marks an item of the symmetric
+// kernel against later blocks, which serves both sides of every pair.
 struct PairItem {
     int64_t i0;
     int64_t j0;
@@ -98,6 +115,14 @@ struct Vec3SoA {
     float* z;
 };
 
+// Fixed-point pair sums (two's complement int64 in units of 2^-s of the
+// element's system), one array per component.
+struct Fx3SoA {
+    unsigned long long* x;
+    unsigned long long* y;
+    unsigned long long* z;
+};
+
 // Device arrays of a batch (all pointers are device memory).
 struct BatchDev {
     int64_t ntot;          // total padded elements
@@ -111,10 +136,10 @@ struct BatchDev {
     Vec3SoA plo;           // each ntot
     Vec3SoA v32;           // each ntot
     int32_t* sys_of;
-    double4_32a* part;         // NB chunks * ntot
-    int32_t nchunk_alloc;  // chunks allocated in part
-    Vec3SoA jpart;         // shares of later blocks' pair sums (see SysConst)
-    double4_32a* cont;         // ntot
+    double4_32a* part;     // partial slots of every system (SysConst::part_off)
+    int64_t part_cap;      // elements of part
+    Fx3SoA facc;           // ntot each: fixed-point pair sums (SysConst::fxp)
+    double4_32a* cont;     // ntot
     const SysConst* sc;
     SysMut* sm;
     // contact grid

@@ -10,15 +10,18 @@
 // kernel) and leaves per unordered pair 15 FP32 operations instead of 24.
 //
 // Work split.  A system's elements form blocks of B = threads x BI elements.
-// Block K against itself is summed one-sided (item j0 == i0, partial slot
-// 0).  Block K against every later block is cut into items of at most
-// sym_chunk j-tiles (partial slots 1, 2, ...); such an item adds the i-side
-// sums to its partial slot as the one-sided kernel does and, per j-tile,
-// writes the j-side share of the whole i-block to its own place in `jpart`
-// (one place per (earlier block, element): nothing is added concurrently,
-// so the result is deterministic).  The kick kernel adds, for element e of
-// block K, its slots in order and then the shares of blocks 0 .. K-1 in
-// order.
+// Block K against itself is summed one-sided (item j0 == i0).  Block K
+// against every later block is cut into items of a few j-tiles; such an item
+// sums the i-side as the one-sided kernel does and, per j-tile, the j-side
+// share of the whole i-block.  Both go into the system's fixed-point
+// accumulators (SysConst::fxp): each value is rounded to an integer multiple
+// of 2^-s and added with a 64-bit integer atomic (a reduction in L2), and
+// since integer addition is associative the sums do not depend on the order
+// in which the CTAs finish -- deterministic, bitwise the same alone and in a
+// batch, with 24 bytes per element instead of a slot per (block, element).
+// A system whose softening is too small for that layout (its resolution
+// relative to the system's acceleration scale would exceed 2^-32) gets
+// one-sided items only, summed into its partial slots.
 //
 // j-side sums inside a CTA.  Each thread holds BI i-elements and walks the
 // tile two j at a time, so for a group of 8 j (4 packed registers per
@@ -32,8 +35,9 @@
 // warp's row of the tile's ring slot in shared memory.  The warp that
 // finishes a tile last (a shared counter per ring slot) adds the rows of
 // all warps in warp order, applies -G m_i (uniform i-blocks; else the mass
-// was applied per pair), stores the tile's shares and only then releases
-// the ring slot, so no row is overwritten before it has been read.
+// was applied per pair), adds the tile's shares to the accumulators and only
+// then releases the ring slot, so no row is overwritten before it has been
+// read.
 //
 // The i-side TwoSum accumulators live in shared memory (touched once per
 // tile), which leaves the registers to the pair arithmetic.
@@ -81,6 +85,12 @@ __device__ __forceinline__ f2 shfl_xor2(f2 v, int m) {
 }
 
 __device__ __forceinline__ f2 sel2(bool c, f2 a, f2 b) { return c ? a : b; }
+
+// facc[.] += v (two's complement; the result is not read, so this is a
+// reduction without return)
+__device__ __forceinline__ void fx_add(unsigned long long* p, long long v) {
+    atomicAdd(p, (unsigned long long)v);
+}
 
 // Sum over the warp of 8 values per lane (4 packed registers, j = 2q and
 // 2q + 1 in register q); returns the sum for j = (lane >> 2) & 7.
@@ -330,7 +340,7 @@ template <int TILE, int BI, int NT, int MINB, int U, bool IPK, int SHR>
 __global__ void __launch_bounds__(NT, MINB)
     pair_sym_kernel(PosSoA pj, const float4* __restrict__ jd, const float* __restrict__ tmass,
                     const PairItem* __restrict__ items, int nitems,
-                    double4_32a* __restrict__ part, int64_t ntot, Vec3SoA jpart,
+                    double4_32a* __restrict__ part, Fx3SoA facc,
                     const SysConst* __restrict__ sc, SysMut* __restrict__ sm,
                     int* __restrict__ counter) {
     constexpr int NW = NT / 32;
@@ -394,12 +404,14 @@ __global__ void __launch_bounds__(NT, MINB)
     while (idx < nitems) {
         const PairItem item = items[idx];
         const SysConst& c = sc[item.sys];
-        const bool both = item.j0 > item.i0;  // later blocks: both sides
+        // an item against later blocks (marked by chunk < 0; planned for
+        // systems summed in fixed point only) serves both sides; the others
+        // are one-sided
+        const bool both = item.chunk < 0;
         const float eps = c.eps_f;
         const f2 eps2 = pk(eps, eps);
         const int ntiles = item.nj / TILE;
         const int64_t gt0 = item.j0 / TILE;
-        const int64_t kblk = (item.i0 - c.off) / B;  // i-block index in the system
 
         f2 xi[NP], yi[NP], zi[NP], gmi[NP];
         // common G m of the i-block (> 0), else per element
@@ -532,11 +544,9 @@ __global__ void __launch_bounds__(NT, MINB)
                 last = __shfl_sync(0xffffffffu, last, 0);
                 if (last) {
                     __threadfence_block();
-                    const int64_t jrel0 = item.j0 - c.off + (int64_t)t * TILE;
-                    const int64_t kj = jrel0 / B;
-                    const int64_t base =
-                        c.jp_off + (kj * (kj - 1) / 2 + kblk) * B + (jrel0 - kj * B);
-                    const float scale = gI > 0.f ? -gI : -1.f;
+                    // -G m_i (uniform i-block) and the fixed-point scale 2^s
+                    const float fs = c.fx_scale_f * (gI > 0.f ? -gI : -1.f);
+                    const int64_t jg = item.j0 + (int64_t)t * TILE;
                     for (int jj = lane; jj < TILE; jj += 32) {
                         float sx = 0.f, sy = 0.f, sz = 0.f;
 #pragma unroll
@@ -545,9 +555,9 @@ __global__ void __launch_bounds__(NT, MINB)
                             sy += S.row[st][w][1][jj];
                             sz += S.row[st][w][2][jj];
                         }
-                        jpart.x[base + jj] = scale * sx;
-                        jpart.y[base + jj] = scale * sy;
-                        jpart.z[base + jj] = scale * sz;
+                        fx_add(facc.x + jg + jj, __float2ll_rn(fs * sx));
+                        fx_add(facc.y + jg + jj, __float2ll_rn(fs * sy));
+                        fx_add(facc.z + jg + jj, __float2ll_rn(fs * sz));
                     }
                     if (lane == 0) s_cnt[st] = 0;
                     __syncwarp();
@@ -557,15 +567,32 @@ __global__ void __launch_bounds__(NT, MINB)
         }
         if (tid == 0 && !prod_ok) s_abort[parity] = 1;
 
-        double4_32a* out = part + (int64_t)item.chunk * ntot + item.i0;
+        if (c.fxp) {
+            const double fs = c.fx_scale;
 #pragma unroll
-        for (int b = 0; b < BI; ++b) {
-            const int rel = b * NT + tid;
-            if (rel < item.iend_rel) {
-                out[rel] = make_double4_32a((double)S.acc[0][b][tid] + (double)S.acc[3][b][tid],
-                                            (double)S.acc[1][b][tid] + (double)S.acc[4][b][tid],
-                                            (double)S.acc[2][b][tid] + (double)S.acc[5][b][tid],
-                                            0.0);
+            for (int b = 0; b < BI; ++b) {
+                const int rel = b * NT + tid;
+                if (rel < item.iend_rel) {
+                    const int64_t i = item.i0 + rel;
+                    fx_add(facc.x + i, __double2ll_rn(
+                                           fs * ((double)S.acc[0][b][tid] + (double)S.acc[3][b][tid])));
+                    fx_add(facc.y + i, __double2ll_rn(
+                                           fs * ((double)S.acc[1][b][tid] + (double)S.acc[4][b][tid])));
+                    fx_add(facc.z + i, __double2ll_rn(
+                                           fs * ((double)S.acc[2][b][tid] + (double)S.acc[5][b][tid])));
+                }
+            }
+        } else {
+            double4_32a* out = part + part_index(c, item.chunk, item.i0);
+#pragma unroll
+            for (int b = 0; b < BI; ++b) {
+                const int rel = b * NT + tid;
+                if (rel < item.iend_rel) {
+                    out[rel] = make_double4_32a(
+                        (double)S.acc[0][b][tid] + (double)S.acc[3][b][tid],
+                        (double)S.acc[1][b][tid] + (double)S.acc[4][b][tid],
+                        (double)S.acc[2][b][tid] + (double)S.acc[5][b][tid], 0.0);
+                }
             }
         }
 
@@ -595,7 +622,7 @@ cudaError_t launch_sym_t(const BatchDev& b, const float* tmass, const PairItem* 
     // every plan calls before its first launch (and outside graph capture)
     constexpr size_t smem = sizeof(SymSmem<TILE, BI, NT, IPK>);
     pair_sym_kernel<TILE, BI, NT, MINB, U, IPK, SHR><<<grid, NT, smem, s>>>(
-        b.pj, b.jd, tmass, items, nitems, b.part, b.ntot, b.jpart, b.sc, b.sm, counter);
+        b.pj, b.jd, tmass, items, nitems, b.part, b.facc, b.sc, b.sm, counter);
     return cudaGetLastError();
 }
 

@@ -55,8 +55,8 @@ struct Active {
 };
 
 // Device bytes one element occupies in a slot (arrays of nb_internal.h: the
-// FP64 state, the FP32 copies, the grid arrays at two buckets per element)
-// without the pair sums.
+// FP64 state, the FP32 copies, the grid arrays at two buckets per element,
+// the fixed-point pair sums) without the partial slots.
 size_t bytes_per_element_base() {
     return 4 * 32      // X, V, A, contact
            + 16        // E
@@ -64,29 +64,17 @@ size_t bytes_per_element_base() {
            + 4 + 4 + 8 // owner, key, cell id
            + 4 + 8 + 16 + 16 + 16  // sorted index, cell, position, low parts, velocity
            + 2 * 12    // bucket counts, fills, starts
-           + 24;       // FP32 low parts and velocity copy
+           + 24        // FP32 low parts and velocity copy
+           + 24;       // fixed-point pair sums
 }
 
-// Device bytes of one slot of npad elements with pair configuration c: the
-// base arrays, the partial sums (with the symmetric kernel at most 1 +
-// ceil(later tiles of block 0 / smallest item) slots per element, the plan
-// cutting items of at least 4 tiles and at most 64 per row; a few with the
-// one-sided one) and the symmetric kernel's shares (one FP32 triple per
-// (earlier block, element)).
-size_t slot_bytes(int64_t npad, const nb::PairCfg& c) {
-    size_t bytes = bytes_per_element_base() * (size_t)npad;
-    if (c.sym) {
-        const int64_t B = (int64_t)c.threads * c.bi;
-        const int64_t nbk = (npad + B - 1) / B;
-        const int64_t ntiles = (npad + c.tile - 1) / c.tile;
-        const int64_t later = std::max<int64_t>(0, ntiles - B / c.tile);
-        const int64_t cmin = std::max<int64_t>(4, (later + 63) / 64);
-        const int64_t slots = 1 + (later + cmin - 1) / cmin;
-        bytes += (size_t)slots * 32 * (size_t)npad + (size_t)(nbk * (nbk - 1) / 2) * B * 12;
-    } else {
-        bytes += (size_t)4 * 32 * (size_t)npad;
-    }
-    return bytes;
+// Device bytes of a system of npad elements with pair configuration c on a
+// persistent grid of `slots` resident CTAs: the base arrays and its own
+// partial slots (the one-sided layout's chunk count, which the plan gives
+// every system).
+size_t slot_bytes(int64_t npad, const nb::PairCfg& c, int64_t slots) {
+    const int64_t S = nb::onesided_chunks(npad, (int64_t)c.threads * c.bi, c.tile, slots);
+    return (bytes_per_element_base() + (size_t)S * 32) * (size_t)npad;
 }
 
 // The server's pair kernel: the symmetric one (each unordered pair once)
@@ -284,7 +272,12 @@ nb_status nb_server_create(size_t hbm_budget_bytes, int32_t max_slots, int64_t m
         *out = nullptr;
         const int64_t npad = (max_n + nb::NB_PAD - 1) / nb::NB_PAD * nb::NB_PAD;
         const nb::PairCfg cfg = server_pair_cfg(npad, prec);
-        const size_t per_slot = slot_bytes(npad, cfg);
+        int dev = 0, sms = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t grid_slots =
+            (int64_t)sms * std::max(1, nb::pair_occupancy(cfg));
+        const size_t per_slot = slot_bytes(npad, cfg, grid_slots);
         const int64_t fit = (int64_t)(hbm_budget_bytes / std::max<size_t>(per_slot, 1));
         const int nslots = (int)std::min<int64_t>(max_slots, fit);
         if (nslots < 1)

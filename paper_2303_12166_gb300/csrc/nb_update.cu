@@ -26,67 +26,16 @@ __device__ __forceinline__ double kick1(double v, double hdt, double a) {
     return __dadd_rn(v, __dmul_rn(hdt, a));
 }
 
-// TwoSum (Knuth) in FP32: hi + lo accumulates x with the rounding error of
-// every addition kept in lo.
-__device__ __forceinline__ void two_sum_f(float& hi, float& lo, float x) {
-    const float s = __fadd_rn(hi, x);
-    const float bp = __fsub_rn(s, hi);
-    const float ap = __fsub_rn(s, bp);
-    lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, ap), __fsub_rn(x, bp)));
-    hi = s;
-}
-
 __device__ __forceinline__ double3 total_acc(const BatchDev& b, const SysConst& c, int64_t i) {
     double ax = 0.0, ay = 0.0, az = 0.0;
-    if (c.sym) {
-        // block K's own slots in order, then the shares of blocks 0 .. K-1
-        const int64_t rel = i - c.off;
-        const int64_t B = c.sym_blk;
-        const int64_t K = rel / B;
-        const int64_t rest = c.sym_ntiles - (K + 1) * c.sym_tpb;
-        const int nslot = 1 + (rest > 0 ? (int)((rest + c.sym_chunk - 1) / c.sym_chunk) : 0);
-        for (int ch = 0; ch < nslot; ++ch) {
-            const double4_32a p = b.part[(int64_t)ch * b.ntot + i];
-            ax += p.x;
-            ay += p.y;
-            az += p.z;
-        }
-        // Up to ~1,000 FP32 shares per element: summed on the FP32 pipe with
-        // TwoSum (Knuth; the sum carries its exact rounding error in a low
-        // part), four running sums (blocks I mod 4) so that four blocks'
-        // loads are in flight, combined in FP64 in a fixed order.  (FP64
-        // additions here would bound the kernel by GB300's FP64 rate.)
-        const int64_t base = c.jp_off + (K * (K - 1) / 2) * B + (rel - K * B);
-        float hx[4] = {0.f, 0.f, 0.f, 0.f}, lx[4] = {0.f, 0.f, 0.f, 0.f};
-        float hy[4] = {0.f, 0.f, 0.f, 0.f}, ly[4] = {0.f, 0.f, 0.f, 0.f};
-        float hz[4] = {0.f, 0.f, 0.f, 0.f}, lz[4] = {0.f, 0.f, 0.f, 0.f};
-        int64_t I = 0;
-        for (; I + 4 <= K; I += 4) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                two_sum_f(hx[u], lx[u], b.jpart.x[base + (I + u) * B]);
-                two_sum_f(hy[u], ly[u], b.jpart.y[base + (I + u) * B]);
-                two_sum_f(hz[u], lz[u], b.jpart.z[base + (I + u) * B]);
-            }
-        }
-        for (int u = 0; I < K; ++I, ++u) {
-            two_sum_f(hx[u], lx[u], b.jpart.x[base + I * B]);
-            two_sum_f(hy[u], ly[u], b.jpart.y[base + I * B]);
-            two_sum_f(hz[u], lz[u], b.jpart.z[base + I * B]);
-        }
-        double sx = 0.0, sy = 0.0, sz = 0.0;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            sx += (double)hx[u] + (double)lx[u];
-            sy += (double)hy[u] + (double)ly[u];
-            sz += (double)hz[u] + (double)lz[u];
-        }
-        ax += sx;
-        ay += sy;
-        az += sz;
+    if (c.fxp) {
+        // the symmetric kernel's fixed-point sum (integer multiples of 2^-s)
+        ax = (double)(long long)b.facc.x[i] * c.fx_inv;
+        ay = (double)(long long)b.facc.y[i] * c.fx_inv;
+        az = (double)(long long)b.facc.z[i] * c.fx_inv;
     } else {
         for (int ch = 0; ch < c.nchunks; ++ch) {
-            const double4_32a p = b.part[(int64_t)ch * b.ntot + i];
+            const double4_32a p = b.part[part_index(c, ch, i)];
             ax += p.x;
             ay += p.y;
             az += p.z;
@@ -125,15 +74,12 @@ __device__ __forceinline__ void write_vel32(const BatchDev& b, int64_t i, const 
     b.v32.z[i] = (float)v.z;
 }
 
-// 4 blocks of 256 per SM (64 registers): the share sums are latency-bound
-// and gain more from resident warps than they lose to a small spill
+// 4 blocks of 256 per SM (64 registers): the kernel is latency-bound and
+// gains from resident warps
 template <int MODE, bool KEYS>
 __global__ void __launch_bounds__(256, 4) kick_kernel(BatchDev b, int only) {
-    // elements in reverse order: with the symmetric pair sums an element of
-    // block K adds K blocks' shares, so the longest threads run first
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= b.ntot) return;
-    const int64_t i = b.ntot - 1 - t;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.ntot) return;
     const int s = b.sys_of[i];
     // every element gets a fresh grid key (none for padding / idle systems)
     if (s < 0 || !b.sc[s].active) {
@@ -273,7 +219,7 @@ __global__ void __launch_bounds__(kDiagThreads) diag_pass1_kernel(BatchDev b, in
         }
         // pair potential: sum_j G m_j/(r+eps) was accumulated in part.w
         double pot = 0.0;
-        for (int ch = 0; ch < c.nchunks; ++ch) pot += b.part[(int64_t)ch * b.ntot + i].w;
+        for (int ch = 0; ch < c.nchunks; ++ch) pot += b.part[part_index(c, ch, i)].w;
         v[19] += -0.5 * m * pot;
         if (c.contacts) v[20] += b.cont[i].w;
         if (!(isfinite(x.x) && isfinite(x.y) && isfinite(x.z) && isfinite(u.x) &&

@@ -300,15 +300,16 @@ def test_energy_drift_long_run(nbm, orc):
     assert drift_gpu <= 3.0 * max(drift_orc, 1e-5), (drift_gpu, drift_orc)
 
 
-def test_default_plan_falls_back_to_one_sided_when_shares_do_not_fit(nbm, orc):
-    """With ~2.5 GB of device memory left, a 1,048,576-element system cannot
-    hold the symmetric plan's shares (4.3 GB) and partial slots: the default
-    configuration falls back to the one-sided kernel by itself (no error)
-    and the forces still match the oracle on sampled rows."""
+def test_symmetric_plan_memory_is_linear_in_n(nbm, orc):
+    """The symmetric kernel sums both sides of every pair into one fixed-point
+    accumulator per element (no slot per (block, element)): a
+    1,048,576-element system takes well under 1 GB of device memory in the
+    default symmetric configuration and runs it with only 1.5 GB of the
+    device left free; its forces match the oracle on sampled rows."""
     import torch
     desc, params = workload_kwargs("binary_1m")
     free, _ = torch.cuda.mem_get_info()
-    leave = 2560 << 20
+    leave = 1536 << 20
     if free < leave + (1 << 30):
         pytest.skip("not enough device memory to set the case up")
     hold = torch.empty(free - leave, dtype=torch.uint8, device="cuda")
@@ -317,10 +318,12 @@ def test_default_plan_falls_back_to_one_sided_when_shares_do_not_fit(nbm, orc):
             cfg = s.pair_cfg()
             a = s.forces()
             n = s.n
+            dev_bytes = s.info.device_bytes
     finally:
         del hold
         torch.cuda.empty_cache()
-    assert cfg["symmetric"] == 0
+    assert cfg["symmetric"] == 3
+    assert dev_bytes < 1e9, dev_bytes
     ox, ov, om, oR, og = oracle_ic(orc, desc, params)
     nd = desc["n_donor"]
     rows = np.unique(np.concatenate([[0, nd - 1, nd, n - 1],
@@ -328,6 +331,47 @@ def test_default_plan_falls_back_to_one_sided_when_shares_do_not_fit(nbm, orc):
     ref = orc.forces_rows(rows, ox, ov, om, oR, og, G=1.0, eps=params["eps"],
                           beta=params["beta"])
     assert rms_rel(a[rows], ref) <= 1e-5
+
+
+def test_fixed_point_sums_are_order_independent(nbm):
+    """The persistent CTAs claim work items in an order that varies from run
+    to run; the fixed-point sums make every evaluation bit-for-bit the same
+    (here: five evaluations of a 20,000-element system, several blocks and
+    both-sided items per row)."""
+    s, _ = _cloud_system(nbm, 20000, 91)
+    with s:
+        first = s.forces()
+        for _ in range(4):
+            assert np.array_equal(s.forces(), first)
+
+
+@pytest.mark.parametrize("eps", [0.0, 1e-7])
+def test_small_softening_runs_one_sided_items(nbm, orc, eps):
+    """Softening too small for the fixed-point layout (eps = 0, and eps = 1e-7
+    for a binary of extent ~1): the symmetric plan gives the system one-sided
+    items summed into partial slots.  The forces still match the oracle, and
+    the system gives the same bits alone and in a batch next to a system
+    summed in fixed point."""
+    desc = dict(n_donor=2000, n_accretor=1000, q=0.5, f_donor=0.8, f_accretor=0.5,
+                sigma_v=1e-3, seed=8, stream=0)
+    params = dict(eps=eps, dt=5e-4, beta=0.5)
+    with _make(nbm, desc, params) as s:
+        assert s.pair_cfg()["symmetric"] == 3
+        a = s.forces()
+        s.step(3)
+        s.sync()
+        alone = s.get_state()
+    p = dict(params, G=1.0, kappa_gamma=8.0, rl_coeff=0.69)
+    ox, ov, om, oR, og = oracle_ic(orc, desc, p)
+    ref = orc.forces(ox, ov, om, oR, og, G=1.0, eps=eps, beta=0.5)
+    assert rms_rel(a, ref) <= 1e-5
+    with nbm.Batch([nbm.nb_desc_default(**BINARY), nbm.nb_desc_default(**desc)],
+                   [nbm.nb_params_default(**BINARY_P), nbm.nb_params_default(**params)]) as b:
+        assert np.array_equal(b.forces(1), a)
+        b.step(3)
+        b.sync()
+        mixed = b.get_state(1)
+    assert np.array_equal(mixed[0], alone[0]) and np.array_equal(mixed[1], alone[1])
 
 
 @pytest.mark.parametrize("cfg", [None, ONE_SIDED], ids=["default", "one-sided"])
