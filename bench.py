@@ -463,11 +463,16 @@ def measure_fp64_path(nbm, torch, dev, stream, args):
 
 def measure_served(nbm, stream, args):
     """Poisson arrivals (20/s) of sweep runs: element count log-uniform in
-    [4,096, 262,144], steps uniform in [1,000, 20,000] divided by
-    --served-steps-div; served by continuous batching (nb_server)."""
+    [4,096, 262,144], donor expansion rate in [0.5, 2]e-5 r_L per step, steps
+    uniform in [1,000, 20,000] divided by --served-steps-div; served by
+    continuous batching (nb_server) under the 150 GB budget.  Compared with
+    the same requests run one at a time through the single-system API with
+    the FP64 diagnostics every step (and without them), each request timed
+    alone for a few steps and charged its full step count."""
     import synth
     trace = synth.served_trace(args.served_requests, seed=0, steps_div=args.served_steps_div)
-    srv = nbm.nb_server_create(int(150e9), 64, 262144, 32, stream)
+    budget = int(150e9)
+    srv = nbm.nb_server_create(budget, 64, 262144, 32, stream)
     try:
         info = nbm.nb_server_info(srv)
         scfg = nbm.nb_server_pair_cfg(srv)
@@ -479,11 +484,39 @@ def measure_served(nbm, stream, args):
                 time.sleep(wait)
             tickets.append(nbm.nb_submit(srv, nbm.nb_desc_default(**r["desc"]),
                                          nbm.nb_params_default(**SWEEP_PARAMS), r["nsteps"]))
-        nbm.nb_server_drain(srv, 1800.0)
+        nbm.nb_server_drain(srv, 3600.0)
         res = [nbm.nb_poll(srv, t) for t in tickets]
+        adm = nbm.nb_server_stats_read(srv)
     finally:
         nbm.nb_server_destroy(srv)
     bad = [r for r in res if r["status"] != 0]
+    lat = np.array([r["t_finish"] - r["t_submit"] for r in res])
+    span = max(r["t_finish"] for r in res) - min(r["t_submit"] for r in res)
+    pairs = float(sum(r["n"] ** 2 * r["steps"] for r in res))
+    steps = float(sum(r["steps"] for r in res))
+    mix_elems = sum(r["desc"]["n_donor"] + r["desc"]["n_accretor"] for r in trace)
+
+    # the same requests one at a time (single-system API, the library's
+    # default configuration), each timed for k steps plain and k steps with
+    # the FP64 diagnostics after every step, charged its full step count
+    k = max(1, args.per_request_steps)
+    t_plain = t_diag = 0.0
+    for r in trace:
+        with nbm.System(nbm.nb_desc_default(**r["desc"]), nbm.nb_params_default(**SWEEP_PARAMS),
+                        stream=stream) as sy:
+            sy.step(1)
+            sy.diagnostics()
+            sy.sync()
+            c0 = time.perf_counter()
+            sy.step(k)
+            sy.sync()
+            t_plain += (time.perf_counter() - c0) / k * r["nsteps"]
+            c0 = time.perf_counter()
+            for _ in range(k):
+                sy.step(1)
+                sy.diagnostics()
+            t_diag += (time.perf_counter() - c0) / k * r["nsteps"]
+
     # three requests (the least work) run again alone with the server's pair
     # configuration: the same diagnostics bit for bit, and the error against
     # the oracle of the accelerations at their final state
@@ -496,6 +529,8 @@ def measure_served(nbm, stream, args):
         with nbm.System(nbm.nb_desc_default(**d), nbm.nb_params_default(**SWEEP_PARAMS),
                         stream=stream) as sy:
             sy.set_pair_cfg(*[scfg[k] for k in PAIR_CFG_KEYS])
+            xv, _, meta = sy.get_state(with_acc=False)
+            sy.set_state(xv, None, meta)  # a^0 with the server's configuration
             sy.step(trace[r]["nsteps"])
             sy.sync()
             dg = sy.diagnostics()
@@ -509,22 +544,37 @@ def measure_served(nbm, stream, args):
         e = force_error(d, SWEEP_PARAMS["eps"], SWEEP_PARAMS["beta"], xv[:, :3], xv[:, 3:], a,
                         _sample_rows(n_r, d["n_donor"], 256, 40 + r), int(meta.step))
         acc.append(dict(e, request=int(r), n=int(n_r), alone_equals_served=bool(same)))
-    lat = np.array([r["t_finish"] - r["t_submit"] for r in res])
-    span = max(r["t_finish"] for r in res) - min(r["t_submit"] for r in res)
-    pairs = float(sum(r["n"] ** 2 * r["steps"] for r in res))
-    steps = float(sum(r["steps"] for r in res))
-    return {"workload": f"served_{len(trace)}", "requests": len(trace), "arrival_hz": 20.0,
-            "n_range": [4096, 262144],
-            "steps_range": [1000 // args.served_steps_div, 20000 // args.served_steps_div],
-            "slots": info["nslots"], "failed": len(bad),
-            "pair_cfg": {k: scfg[k] for k in PAIR_CFG_KEYS},
-            "p50_latency_s": float(np.percentile(lat, 50)),
-            "p99_latency_s": float(np.percentile(lat, 99)),
-            "makespan_s": span, "value": pairs / span, "unit": "pairs/s",
-            "system_steps_per_s": steps / span,
-            "accuracy": {"requests": acc,
-                         "max_force_rms_rel": max((a["force_rms_rel"] for a in acc), default=None),
-                         "tolerance": 1e-5}}
+
+    div = args.served_steps_div
+    out = {"workload": f"served_{len(trace)}", "requests": len(trace), "arrival_hz": 20.0,
+           "n_range": [4096, 262144],
+           "steps_range": [max(1, 1000 // div), max(1, 20000 // div)],
+           "steps_scaled": f"config steps [1000, 20000] / {div}" if div != 1 else None,
+           "slots": info["nslots"], "failed": len(bad),
+           "pair_cfg": {k: scfg[k] for k in PAIR_CFG_KEYS},
+           "p50_latency_s": float(np.percentile(lat, 50)),
+           "p99_latency_s": float(np.percentile(lat, 99)),
+           "makespan_s": span, "value": pairs / span, "unit": "pairs/s",
+           "system_steps_per_s": steps / span,
+           "admission": {"budget_bytes": adm["budget_bytes"],
+                         "arena_elements": adm["capacity_elements"],
+                         "mix_elements": int(mix_elems),
+                         "peak_requests_in_flight": adm["peak_requests"],
+                         "peak_bytes_in_flight": adm["peak_bytes"],
+                         "admissions_deferred": adm["admissions_deferred"],
+                         "device_bytes": adm["device_bytes"]},
+           "per_system_path": {
+               "plain_system_steps_per_s": steps / t_plain,
+               "fp64_diag_system_steps_per_s": steps / t_diag,
+               "note": f"every request alone through nb_step (plain) or nb_step(1) + "
+                       f"nb_diagnostics (FP64 diagnostics every step), back to back with no "
+                       f"arrival gaps, each timed for {k} steps and charged its step count"},
+           "speedup_vs_per_system_fp64_diag": (steps / span) / (steps / t_diag),
+           "speedup_vs_per_system_plain": (steps / span) / (steps / t_plain),
+           "accuracy": {"requests": acc,
+                        "max_force_rms_rel": max((a["force_rms_rel"] for a in acc), default=None),
+                        "tolerance": 1e-5}}
+    return out
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -746,7 +796,9 @@ def main(argv=None):
     ap.add_argument("--per-system-steps", type=int, default=5,
                     help="steps each sweep system is timed for alone (0: skip)")
     ap.add_argument("--served-requests", type=int, default=64)
-    ap.add_argument("--served-steps-div", type=int, default=100)
+    ap.add_argument("--served-steps-div", type=int, default=10)
+    ap.add_argument("--per-request-steps", type=int, default=3,
+                    help="steps each served request is timed for alone")
     ap.add_argument("--pair-cfg", default="",
                     help="tile,i_per_thread,threads,min_blocks,nr_slots,i_packed,shared_rcp[,symmetric] (skips the "
                          "autotuner)")

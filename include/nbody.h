@@ -372,12 +372,18 @@ nb_status nb_batch_profile_read(nb_batch_t b, nb_prof* out, int reset);
 
 /* ---- serving: continuous batching of parameter-sweep runs --------------- */
 
-/* A server owns one batch of fixed-size slots on the device (as many slots of
- * max_n elements as hbm_budget_bytes allows, at most max_slots) and a host
- * thread that serves submitted runs: queued runs are admitted in arrival
- * order as slots free up, all admitted runs advance together (one pair
- * kernel launch per step for all of them), and each run is retired the moment
- * it completes its steps, freeing its slot for the next.  State stays on the
+/* A server owns one batch on the device, laid out as an arena of elements
+ * (as many as hbm_budget_bytes holds, at most max_slots x max_n) with
+ * max_slots system records, and a host thread that serves submitted runs.
+ * A queued run is admitted when its own device bytes (its elements' share of
+ * the arena arrays and its partial sums: about 400-600 bytes per element)
+ * fit in what is left of the budget, a free range of its size exists in the
+ * arena and a record is free -- so small runs take little room and many of
+ * them run at once.  Admission goes in arrival order; a later run that fits
+ * may pass an earlier one that waits for room, for at most a few admission
+ * rounds.  All admitted runs advance together (one pair kernel launch per
+ * step for all of them), and each run is retired the moment it completes its
+ * steps, freeing its range and bytes for the next.  State stays on the
  * device for the whole run.  A run's result equals the result of running the
  * same request alone. */
 typedef struct nb_server* nb_server_t;
@@ -394,12 +400,31 @@ typedef struct nb_result {
                              e_tot are NaN (the O(N^2) energy pass is skipped) */
 } nb_result;
 
-/* prec: 32 or 64 (the force precision of every run).  NB_EBUDGET if not even
- * one slot of max_n elements fits the budget. */
+/* prec: 32 or 64 (the force precision of every run).  max_slots: runs in
+ * flight at once; max_n: elements of the largest run.  NB_EBUDGET if not
+ * even one run of max_n elements fits the budget. */
 nb_status nb_server_create(size_t hbm_budget_bytes, int32_t max_slots, int64_t max_n,
                            int32_t prec, void* stream, nb_server_t* out);
+/* *nslots: runs in flight at once (max_slots); *slot_n: the largest run
+ * (max_n padded to 256); *device_bytes: device memory the server holds. */
 nb_status nb_server_info(nb_server_t srv, int32_t* nslots, int64_t* slot_n,
                          int64_t* device_bytes);
+/* Admission state and its peaks since creation. */
+typedef struct nb_server_stats {
+    int64_t capacity_elements;   /* elements of the arena */
+    int64_t budget_bytes;        /* hbm_budget_bytes */
+    int64_t bytes_in_use;        /* device bytes of the runs in flight */
+    int64_t elements_in_use;     /* arena elements they hold (padded) */
+    int64_t requests_running;
+    int64_t requests_queued;
+    int64_t peak_requests;       /* most runs in flight at once */
+    int64_t peak_elements;
+    int64_t peak_bytes;
+    int64_t admissions_deferred; /* times a queued run found no room */
+    int64_t device_bytes;        /* device memory the server holds */
+    int64_t max_request_bytes;   /* device bytes a run of max_n elements takes */
+} nb_server_stats;
+nb_status nb_server_stats_read(nb_server_t srv, nb_server_stats* out);
 /* The pair-kernel configuration the server runs every request with: the
  * symmetric kernel (rotating shares, 12 i-elements per thread) for slots of
  * at least 16,384 elements (FP32), else the one-sided kernel (tile 256, 8
@@ -407,7 +432,7 @@ nb_status nb_server_info(nb_server_t srv, int32_t* nslots, int64_t* slot_n,
  * equals running it alone with this configuration. */
 nb_status nb_server_pair_cfg(nb_server_t srv, nb_pair_cfg* cfg);
 /* Queue a run of nsteps steps; *ticket identifies it.  The arrays of desc are
- * copied.  NB_EBUDGET if the system is larger than a slot. */
+ * copied.  NB_EBUDGET if the system has more than max_n elements. */
 nb_status nb_submit(nb_server_t srv, const nb_desc* desc, const nb_params* params,
                     int64_t nsteps, uint64_t* ticket);
 /* NB_OK with *out filled once the run has finished, NB_PENDING before,

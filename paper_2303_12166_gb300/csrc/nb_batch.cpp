@@ -342,6 +342,35 @@ static uint32_t next_pow2(uint64_t v) {
 
 nb_status Batch::init(const std::vector<int64_t>& n_per_slot, int prec, cudaStream_t stream) {
     if (n_per_slot.empty()) return set_error(NB_EINVAL, "a batch needs at least one slot");
+    for (size_t s = 0; s < n_per_slot.size(); ++s)
+        if (n_per_slot[s] < 1) return set_error(NB_EINVAL, "slot %zu: size must be >= 1", s);
+    return init_(n_per_slot, 0, prec, stream);
+}
+
+nb_status Batch::init_arena(int64_t capacity, int max_systems, int prec, cudaStream_t stream) {
+    if (max_systems < 1 || capacity < NB_PAD)
+        return set_error(NB_EINVAL, "an arena needs >= 1 system record and >= %d elements", NB_PAD);
+    return init_(std::vector<int64_t>(max_systems, 0), capacity, prec, stream);
+}
+
+nb_status Batch::place(int s, int64_t off, int64_t npad) {
+    if (s < 0 || s >= nslots()) return set_error(NB_ENOTFOUND, "no slot %d", s);
+    if (sc_[s].active) return set_error(NB_EINVAL, "slot %d is in use", s);
+    if (off < 0 || npad < NB_PAD || off % NB_PAD || npad % NB_PAD || off + npad > d_.ntot)
+        return set_error(NB_EINVAL, "range [%lld, %lld) is not a padded range of the arena",
+                         (long long)off, (long long)(off + npad));
+    sc_[s].off = off;
+    sc_[s].npad = npad;
+    sc_[s].n = 0;
+    consts_dirty_ = true;
+    planned_ = false;
+    return NB_OK;
+}
+
+// n_per_slot: padded ranges laid out back to back (0: a record with no range
+// yet); arena > 0: that many elements in total instead.
+nb_status Batch::init_(const std::vector<int64_t>& n_per_slot, int64_t arena, int prec,
+                       cudaStream_t stream) {
     if (prec != 32 && prec != 64) return set_error(NB_EINVAL, "prec must be 32 or 64");
     stream_ = stream;
     prec_ = prec;
@@ -358,15 +387,15 @@ nb_status Batch::init(const std::vector<int64_t>& n_per_slot, int prec, cudaStre
     int64_t off = 0;
     for (int s = 0; s < nsys; ++s) {
         const int64_t n = n_per_slot[s];
-        if (n < 1) return set_error(NB_EINVAL, "slot %d: size must be >= 1", s);
         const int64_t npad = (n + NB_PAD - 1) / NB_PAD * NB_PAD;
-        sc_[s].off = off;
+        sc_[s].off = arena > 0 ? 0 : off;
         sc_[s].n = n;
         sc_[s].npad = npad;
         sc_[s].active = 0;
         sc_[s].nchunks = 1;
         off += npad;
     }
+    if (arena > 0) off = (arena + NB_PAD - 1) / NB_PAD * NB_PAD;
     if (off >= ((int64_t)1 << 31)) return set_error(NB_EINVAL, "batch too large (>= 2^31 elements)");
     d_.ntot = off;
     d_.nsys = nsys;
@@ -553,6 +582,10 @@ nb_status Batch::unload(int s) {
     sc_[s].active = 0;
     consts_dirty_ = true;
     planned_ = false;
+    // the range no longer belongs to the slot (it may be placed elsewhere)
+    if (sc_[s].npad > 0)
+        NB_CU(cudaMemsetAsync(d_.sys_of + sc_[s].off, 0xff, sc_[s].npad * sizeof(int32_t),
+                              stream_));
     return push_consts_();
 }
 

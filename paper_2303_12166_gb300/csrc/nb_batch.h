@@ -102,10 +102,19 @@ public:
     // Allocate room for systems of the given padded sizes on `stream`.
     // prec: 32 or 64 (pair term precision for every system of the batch).
     nb_status init(const std::vector<int64_t>& n_per_slot, int prec, cudaStream_t stream);
+    // An arena of `capacity` elements with `max_systems` system records that
+    // own no elements yet: place() gives an inactive record its range.
+    nb_status init_arena(int64_t capacity, int max_systems, int prec, cudaStream_t stream);
+    // Give inactive record s the element range [off, off + npad) (both
+    // multiples of NB_PAD, inside the arena; ranges of records in use must
+    // not overlap -- the caller's allocator keeps them apart).
+    nb_status place(int s, int64_t off, int64_t npad);
+    int64_t capacity() const { return d_.ntot; }
     // Load a system into slot s (host -> device), make it active and
     // evaluate its initial acceleration unless `defer_forces`.
     nb_status load(int s, const SystemInit& si, bool defer_forces = false);
-    // Deactivate a slot (its elements are skipped by every kernel).
+    // Deactivate a slot: its elements are skipped by every kernel and no
+    // longer owned by it (the range can be placed again).
     nb_status unload(int s);
 
     // Pair-kernel configuration (tile, i-blocking, threads).
@@ -159,6 +168,8 @@ public:
     nb_status read_profile(nb_prof* out, bool reset);
 
 private:
+    nb_status init_(const std::vector<int64_t>& n_per_slot, int64_t arena, int prec,
+                    cudaStream_t stream);
     nb_status alloc_(void** p, size_t bytes);
     // free one allocation made by alloc_ (after the stream drains); p = null
     nb_status free_(void** p);

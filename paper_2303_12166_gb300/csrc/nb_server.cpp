@@ -1,24 +1,33 @@
 // nb_server.cpp -- serving parameter-sweep runs by continuous batching.
 //
-// One host thread owns a Batch of fixed-size slots (as many as the device
-// memory budget allows).  Requests (a system description, parameters and a
-// step count) queue in arrival order; whenever slots are free the thread
-// admits queued requests -- builds their initial state, loads it into free
-// slots and evaluates their initial acceleration -- and then advances a set
-// of active systems together by a chunk of steps: one persistent pair-kernel
-// launch, one contact pass and one update per step for all of them, replayed
-// from a CUDA graph.  The set is chosen shortest remaining work first (n^2 x
-// steps left), adding runs until a step holds enough pair interactions to
-// fill the GPU: short requests do not wait on every step of long ones, and
-// the device stays busy.  The chunk ends at the next completion in the set,
-// so a finished run is retired (its final diagnostics recorded, its slot
-// freed) without waiting for the others, and requests that arrived
+// One host thread owns a Batch laid out as an arena of elements (sized from
+// the device memory budget) with a fixed number of system records.
+// Requests (a system description, parameters and a step count) queue in
+// arrival order.  A request is admitted when its own device bytes (its
+// elements' share of the arena arrays plus its partial slots) fit in what is
+// left of the budget and a free range of its padded size exists in the arena
+// (first fit, freed ranges coalesced): a 4,096-element run takes 4,096
+// elements of room, not a slot sized for the largest run.  Admission scans
+// the queue in order and may admit a later request that fits while an
+// earlier one waits for room, but stops passing a waiting head of the queue
+// after a few rounds so that large runs are not starved.  On admission the
+// thread builds the run's initial state, loads it into its range and
+// evaluates its initial acceleration, then advances a set of active systems
+// together by a chunk of steps: one persistent pair-kernel launch, one
+// contact pass and one update per step for all of them, replayed from a
+// CUDA graph.  The set is chosen shortest remaining work first (n^2 x steps
+// left), adding runs until a step holds enough pair interactions to fill the
+// GPU: short requests do not wait on every step of long ones, and the device
+// stays busy.  The chunk ends at the next completion in the set, so a
+// finished run is retired (its final diagnostics recorded, its range and
+// bytes freed) without waiting for the others, and requests that arrived
 // meanwhile are admitted at once.  State stays on the device for the whole
 // run.
 //
-// A system's trajectory does not depend on what else shares the batch or on
-// how its steps are chunked (see nb_batch.cpp), so each result equals the
-// result of running the same request alone.
+// A system's trajectory does not depend on what else shares the batch, on
+// where in the arena it sits or on how its steps are chunked (see
+// nb_batch.cpp), so each result equals the result of running the same
+// request alone.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -95,10 +104,57 @@ nb::PairCfg server_pair_cfg(int64_t slot_n, int prec) {
 
 }  // namespace
 
+// Free ranges of the arena (element offsets, multiples of NB_PAD): first
+// fit, a freed range merged with its free neighbours.
+class RangeAlloc {
+public:
+    void reset(int64_t cap) {
+        free_.clear();
+        if (cap > 0) free_[0] = cap;
+    }
+    bool take(int64_t len, int64_t* off) {
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < len) continue;
+            *off = it->first;
+            const int64_t rest = it->second - len;
+            const int64_t at = it->first + len;
+            free_.erase(it);
+            if (rest > 0) free_[at] = rest;
+            return true;
+        }
+        return false;
+    }
+    void give(int64_t off, int64_t len) {
+        auto next = free_.lower_bound(off);
+        if (next != free_.end() && off + len == next->first) {
+            len += next->second;
+            next = free_.erase(next);
+        }
+        if (next != free_.begin()) {
+            auto prev = std::prev(next);
+            if (prev->first + prev->second == off) {
+                prev->second += len;
+                return;
+            }
+        }
+        free_[off] = len;
+    }
+
+private:
+    std::map<int64_t, int64_t> free_;  // offset -> length
+};
+
+// The queue's head may be passed by later requests that fit for this many
+// admission rounds; after that nothing is admitted ahead of it.
+constexpr int kMaxHeadPasses = 8;
+
 struct nb_server {
     Batch batch;
-    int64_t slot_n = 0;
-    int nslots = 0;
+    nb::PairCfg cfg{};
+    int64_t slot_n = 0;       // largest request (padded)
+    int nslots = 0;           // system records: requests running at once
+    size_t budget = 0;        // device bytes the runs may take
+    int64_t grid_slots = 1;   // resident CTAs of the pair kernel's grid
     int64_t tick_steps = 64;
     Clock::time_point t0;
     std::mutex mu;
@@ -107,7 +163,15 @@ struct nb_server {
     std::map<uint64_t, nb_result> done;
     std::map<uint64_t, int> where;  // ticket -> 0 queued, 1 running
     std::vector<int> slot_used;     // 0 free
-    std::vector<Active> active;     // per slot
+    std::vector<Active> active;     // per record
+    std::vector<int64_t> rec_off, rec_npad;
+    std::vector<size_t> rec_bytes;
+    RangeAlloc arena;
+    size_t bytes_in_use = 0;
+    int64_t elems_in_use = 0;
+    int running = 0;
+    int head_passes = 0;
+    nb_server_stats stats{};
     uint64_t next_ticket = 1;
     bool stop = false;
     nb_status fatal = NB_OK;
@@ -115,6 +179,14 @@ struct nb_server {
     std::thread worker;
 
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+    // the range and bytes of record s back to the free pool (lock held)
+    void release(int s) {
+        arena.give(rec_off[s], rec_npad[s]);
+        bytes_in_use -= rec_bytes[s];
+        elems_in_use -= rec_npad[s];
+        running -= 1;
+        slot_used[s] = 0;
+    }
     void run();
 };
 
@@ -128,23 +200,52 @@ void nb_server::run() {
         return;
     }
     for (;;) {
-        // ---- admit
+        // ---- admit: in arrival order, each request that fits (its own bytes
+        // within the budget, a free range of its size, a free record)
         std::vector<std::pair<int, Request>> admit;
         {
             std::unique_lock<std::mutex> lk(mu);
-            bool any_active = std::any_of(slot_used.begin(), slot_used.end(),
-                                          [](int u) { return u != 0; });
-            if (!any_active && queue.empty() && !stop)
+            if (running == 0 && queue.empty() && !stop)
                 cv.wait_for(lk, std::chrono::milliseconds(50));
             if (stop) return;
-            for (int s = 0; s < nslots && !queue.empty(); ++s) {
-                if (slot_used[s]) continue;
-                Request r = std::move(queue.front());
-                queue.pop_front();
-                slot_used[s] = 1;
-                where[r.ticket] = 1;
-                admit.emplace_back(s, std::move(r));
+            bool head_waits = false;
+            for (auto it = queue.begin(); it != queue.end();) {
+                int s = -1;
+                for (int k = 0; k < nslots; ++k)
+                    if (!slot_used[k]) {
+                        s = k;
+                        break;
+                    }
+                if (s < 0) break;  // every record is running
+                const int64_t n = it->desc.n_donor + it->desc.n_accretor;
+                const int64_t npad = (n + nb::NB_PAD - 1) / nb::NB_PAD * nb::NB_PAD;
+                const size_t bytes = slot_bytes(npad, cfg, grid_slots);
+                int64_t off = 0;
+                if (bytes_in_use + bytes <= budget && arena.take(npad, &off)) {
+                    slot_used[s] = 1;
+                    rec_off[s] = off;
+                    rec_npad[s] = npad;
+                    rec_bytes[s] = bytes;
+                    bytes_in_use += bytes;
+                    elems_in_use += npad;
+                    running += 1;
+                    if (it == queue.begin()) head_passes = 0;
+                    where[it->ticket] = 1;
+                    admit.emplace_back(s, std::move(*it));
+                    it = queue.erase(it);
+                    continue;
+                }
+                stats.admissions_deferred += 1;
+                if (it == queue.begin()) {
+                    head_waits = true;
+                    if (head_passes >= kMaxHeadPasses) break;  // no one passes it now
+                }
+                ++it;
             }
+            if (head_waits && !admit.empty()) head_passes += 1;
+            stats.peak_requests = std::max<int64_t>(stats.peak_requests, running);
+            stats.peak_elements = std::max<int64_t>(stats.peak_elements, elems_in_use);
+            stats.peak_bytes = std::max<int64_t>(stats.peak_bytes, (int64_t)bytes_in_use);
         }
         std::vector<int> loaded;
         {
@@ -156,10 +257,11 @@ void nb_server::run() {
                 d.mrg_in = r.mrg.empty() ? nullptr : r.mrg.data();
                 nb_status st = nb::build_system(d, r.params, si);
                 if (st == NB_OK && si.n > slot_n)
-                    st = set_error(NB_EBUDGET, "request of %lld elements exceeds the slot size %lld",
-                                   (long long)si.n, (long long)slot_n);
+                    st = set_error(NB_EBUDGET, "request of %lld elements exceeds the largest "
+                                   "request size %lld", (long long)si.n, (long long)slot_n);
                 if (st == NB_OK && r.params.force_prec != batch.prec())
                     st = set_error(NB_EINVAL, "the server runs force_prec %d", batch.prec());
+                if (st == NB_OK) st = batch.place(s, rec_off[s], rec_npad[s]);
                 if (st == NB_OK) st = batch.load(s, si, true);
                 std::lock_guard<std::mutex> lk(mu);
                 if (st != NB_OK) {
@@ -169,7 +271,7 @@ void nb_server::run() {
                     res.t_start = res.t_finish = now();
                     done[r.ticket] = res;
                     where.erase(r.ticket);
-                    slot_used[s] = 0;
+                    release(s);
                     cv.notify_all();  // a drain may be waiting for this ticket
                     continue;
                 }
@@ -255,7 +357,7 @@ void nb_server::run() {
             res.t_finish = now();
             done[a.req.ticket] = res;
             where.erase(a.req.ticket);
-            slot_used[s] = 0;
+            release(s);
             cv.notify_all();
         }
     }
@@ -275,26 +377,42 @@ nb_status nb_server_create(size_t hbm_budget_bytes, int32_t max_slots, int64_t m
         int dev = 0, sms = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const int64_t grid_slots =
-            (int64_t)sms * std::max(1, nb::pair_occupancy(cfg));
-        const size_t per_slot = slot_bytes(npad, cfg, grid_slots);
-        const int64_t fit = (int64_t)(hbm_budget_bytes / std::max<size_t>(per_slot, 1));
-        const int nslots = (int)std::min<int64_t>(max_slots, fit);
-        if (nslots < 1)
+        const int64_t grid_slots = (int64_t)sms * std::max(1, nb::pair_occupancy(cfg));
+        // the most partial slots any request up to max_n elements takes
+        int64_t smax = 1;
+        for (int64_t n = nb::NB_PAD; n <= npad; n += nb::NB_PAD)
+            smax = std::max(smax, nb::onesided_chunks(n, (int64_t)cfg.threads * cfg.bi, cfg.tile,
+                                                      grid_slots));
+        const size_t per_elem = bytes_per_element_base() + (size_t)smax * 32;
+        if (slot_bytes(npad, cfg, grid_slots) > hbm_budget_bytes)
             return set_error(NB_EBUDGET,
-                             "nb_server_create: one slot of %lld elements needs ~%zu bytes, over "
+                             "nb_server_create: a request of %lld elements needs ~%zu bytes, over "
                              "the budget of %zu",
-                             (long long)max_n, per_slot, hbm_budget_bytes);
+                             (long long)max_n, slot_bytes(npad, cfg, grid_slots), hbm_budget_bytes);
+        // arena: as many elements as the budget holds at the most bytes per
+        // element, at most max_slots requests of max_n elements
+        int64_t cap = (int64_t)std::min<double>((double)hbm_budget_bytes / (double)per_elem,
+                                                (double)max_slots * (double)npad);
+        cap = std::max<int64_t>(cap / nb::NB_PAD * nb::NB_PAD, npad);
         std::unique_ptr<nb_server> owner(new nb_server());
         nb_server* srv = owner.get();
+        srv->cfg = cfg;
         srv->slot_n = npad;
-        srv->nslots = nslots;
+        srv->nslots = max_slots;
+        srv->budget = hbm_budget_bytes;
+        srv->grid_slots = grid_slots;
         srv->t0 = Clock::now();
-        srv->slot_used.assign(nslots, 0);
-        srv->active.assign(nslots, Active{});
+        srv->slot_used.assign(max_slots, 0);
+        srv->active.assign(max_slots, Active{});
+        srv->rec_off.assign(max_slots, 0);
+        srv->rec_npad.assign(max_slots, 0);
+        srv->rec_bytes.assign(max_slots, 0);
+        srv->arena.reset(cap);
+        srv->stats.capacity_elements = cap;
+        srv->stats.budget_bytes = (int64_t)hbm_budget_bytes;
+        srv->stats.max_request_bytes = (int64_t)slot_bytes(npad, cfg, grid_slots);
         srv->batch.set_use_graph(true);
-        nb_status st = srv->batch.init(std::vector<int64_t>(nslots, npad), prec,
-                                       static_cast<cudaStream_t>(stream));
+        nb_status st = srv->batch.init_arena(cap, max_slots, prec, static_cast<cudaStream_t>(stream));
         if (st == NB_OK) st = srv->batch.set_pair_cfg(cfg);
         if (st != NB_OK) return st;
         srv->worker = std::thread([srv] { srv->run(); });
@@ -303,6 +421,18 @@ nb_status nb_server_create(size_t hbm_budget_bytes, int32_t max_slots, int64_t m
     } catch (const std::exception& e) {
         return set_error(NB_EINVAL, "nb_server_create: %s", e.what());
     }
+}
+
+nb_status nb_server_stats_read(nb_server_t srv, nb_server_stats* out) {
+    if (!srv || !out) return set_error(NB_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    *out = srv->stats;
+    out->bytes_in_use = (int64_t)srv->bytes_in_use;
+    out->elements_in_use = srv->elems_in_use;
+    out->requests_running = srv->running;
+    out->requests_queued = (int64_t)srv->queue.size();
+    out->device_bytes = srv->batch.device_bytes();
+    return NB_OK;
 }
 
 nb_status nb_server_info(nb_server_t srv, int32_t* nslots, int64_t* slot_n, int64_t* device_bytes) {
@@ -341,7 +471,7 @@ nb_status nb_submit(nb_server_t srv, const nb_desc* desc, const nb_params* param
         r.nsteps = nsteps;
         const int64_t n = desc->n_donor + desc->n_accretor;
         if (n < 1 || n > srv->slot_n)
-            return set_error(NB_EBUDGET, "nb_submit: %lld elements do not fit a slot of %lld",
+            return set_error(NB_EBUDGET, "nb_submit: %lld elements: the server takes 1 .. %lld",
                              (long long)n, (long long)srv->slot_n);
         if (desc->xv_in) r.xv.assign(desc->xv_in, desc->xv_in + 6 * n);
         if (desc->mrg_in) r.mrg.assign(desc->mrg_in, desc->mrg_in + 3 * n);

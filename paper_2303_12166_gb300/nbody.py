@@ -79,6 +79,13 @@ class nb_result(ctypes.Structure):
                 ("t_submit", _D), ("t_start", _D), ("t_finish", _D), ("diag", nb_diag)]
 
 
+class nb_server_stats(ctypes.Structure):
+    _fields_ = [(k, _I64) for k in (
+        "capacity_elements", "budget_bytes", "bytes_in_use", "elements_in_use",
+        "requests_running", "requests_queued", "peak_requests", "peak_elements", "peak_bytes",
+        "admissions_deferred", "device_bytes", "max_request_bytes")]
+
+
 class nb_unit_rates(ctypes.Structure):
     _fields_ = [("sm_count", _I32), ("mufu_sqrt_per_s_sm", _D), ("mufu_rcp_per_s_sm", _D),
                 ("fp32_lanes_per_s_sm", _D)]
@@ -145,6 +152,7 @@ _sig("nb_poll", ctypes.c_int, [_P, _U64, ctypes.POINTER(nb_result)])
 _sig("nb_server_drain", ctypes.c_int, [_P, _D])
 _sig("nb_server_clock", _D, [_P])
 _sig("nb_server_pair_cfg", ctypes.c_int, [_P, ctypes.POINTER(nb_pair_cfg)])
+_sig("nb_server_stats_read", ctypes.c_int, [_P, ctypes.POINTER(nb_server_stats)])
 _sig("nb_measure_unit_rates", ctypes.c_int, [ctypes.POINTER(nb_unit_rates), _P])
 _sig("nb_server_destroy", None, [_P])
 _sig("nb_set_pair_cfg", ctypes.c_int, [_P, ctypes.POINTER(nb_pair_cfg)])
@@ -606,6 +614,12 @@ def nb_server_info(h) -> dict:
     _check(_lib.nb_server_info(_P(h), ctypes.byref(ns), ctypes.byref(sn), ctypes.byref(db)),
            "nb_server_info")
     return {"nslots": ns.value, "slot_n": sn.value, "device_bytes": db.value}
+
+
+def nb_server_stats_read(h) -> dict:
+    st = nb_server_stats()
+    _check(_lib.nb_server_stats_read(_P(h), ctypes.byref(st)), "nb_server_stats_read")
+    return {name: int(getattr(st, name)) for name, _ in nb_server_stats._fields_}
 
 
 def nb_server_pair_cfg(h) -> dict:

@@ -140,20 +140,30 @@ def test_server_results_equal_alone(nbm):
         assert np.isnan(d["e_grav"])
 
 
-def test_server_budget_and_errors(nbm):
-    # a budget that holds a single slot: runs are served one after another
-    one_slot = 4096 * 600
+def test_server_admits_by_request_bytes(nbm):
+    """Admission counts each run's own device bytes against the budget.  The
+    budget holds one run of the largest size (4,096 elements) but not that
+    run and a 1,024-element one: the three small runs queued behind the large
+    one wait until it is retired, then all three run at once."""
     with pytest.raises(nbm.NbError) as ei:
         nbm.nb_server_create(1000, 4, 4096, 32)
     assert ei.value.status == nbm.NB_EBUDGET
-    srv = nbm.nb_server_create(one_slot, 4, 4096, 32)
+    probe = nbm.nb_server_create(1 << 30, 8, 4096, 32)
     try:
-        assert nbm.nb_server_info(srv)["nslots"] == 1
-        s = SYSTEMS[0]
-        t1 = nbm.nb_submit(srv, nbm.nb_desc_default(**s["desc"]),
-                           nbm.nb_params_default(**s["params"]), 8)
-        t2 = nbm.nb_submit(srv, nbm.nb_desc_default(**s["desc"]),
-                           nbm.nb_params_default(**s["params"]), 8)
+        per_big = nbm.nb_server_stats_read(probe)["max_request_bytes"]
+    finally:
+        nbm.nb_server_destroy(probe)
+    budget = int(per_big * 1.1)
+    big = dict(desc=dict(n_donor=3000, n_accretor=1000, q=0.4, f_donor=0.9, f_accretor=0.5,
+                         sigma_v=1e-3, seed=5), params=dict(eps=0.006, dt=5e-4, beta=0.5))
+    small = SYSTEMS[0]  # 1,024 elements: a quarter of the large run's bytes
+    srv = nbm.nb_server_create(budget, 8, 4096, 32)
+    try:
+        assert nbm.nb_server_info(srv)["nslots"] == 8
+        t_big = nbm.nb_submit(srv, nbm.nb_desc_default(**big["desc"]),
+                              nbm.nb_params_default(**big["params"]), 20)
+        t_small = [nbm.nb_submit(srv, nbm.nb_desc_default(**small["desc"]),
+                                 nbm.nb_params_default(**small["params"]), 8) for _ in range(3)]
         with pytest.raises(nbm.NbError) as ei:
             nbm.nb_submit(srv, nbm.nb_desc_default(n_donor=5000, n_accretor=5000),
                           nbm.nb_params_default(), 1)
@@ -165,13 +175,53 @@ def test_server_budget_and_errors(nbm):
             with pytest.raises(nbm.NbError) as ei:
                 nbm.nb_server_drain(srv, bad)
             assert ei.value.status == nbm.NB_EINVAL
-        nbm.nb_server_drain(srv, float("inf"))  # no limit: returns when both are done
-        r1, r2 = nbm.nb_poll(srv, t1), nbm.nb_poll(srv, t2)
-        assert r1["status"] == r2["status"] == nbm.NB_OK
-        assert r2["t_start"] >= r1["t_finish"]
-        assert r1["diag"]["e_kin"] == r2["diag"]["e_kin"]
+        nbm.nb_server_drain(srv, float("inf"))  # no limit: returns when all are done
+        rb = nbm.nb_poll(srv, t_big)
+        rs = [nbm.nb_poll(srv, t) for t in t_small]
+        st = nbm.nb_server_stats_read(srv)
     finally:
         nbm.nb_server_destroy(srv)
+    assert rb["status"] == nbm.NB_OK and all(r["status"] == nbm.NB_OK for r in rs)
+    for r in rs:
+        assert r["t_start"] >= rb["t_finish"]
+    # the three small runs were in flight together
+    assert max(r["t_start"] for r in rs) < min(r["t_finish"] for r in rs)
+    assert rs[0]["diag"]["e_kin"] == rs[1]["diag"]["e_kin"] == rs[2]["diag"]["e_kin"]
+    assert st["peak_requests"] == 3
+    assert st["peak_bytes"] <= budget
+    assert st["admissions_deferred"] > 0
+    assert st["requests_running"] == 0 and st["bytes_in_use"] == 0
+
+
+def test_server_many_small_runs_share_the_arena(nbm):
+    """Runs much smaller than the largest size take only their own room:
+    with max_n = 65,536 and a budget of two such runs, eight 1,024-element
+    runs are all in flight at once (fixed slots of max_n would hold two)."""
+    probe = nbm.nb_server_create(1 << 30, 16, 65536, 32)
+    try:
+        per_big = nbm.nb_server_stats_read(probe)["max_request_bytes"]
+    finally:
+        nbm.nb_server_destroy(probe)
+    srv = nbm.nb_server_create(int(2.2 * per_big), 16, 65536, 32)
+    s = SYSTEMS[0]
+    runs = [dict(s, desc=dict(s["desc"], seed=40 + k)) for k in range(8)]
+    try:
+        cfg = nbm.nb_server_pair_cfg(srv)
+        tickets = [nbm.nb_submit(srv, nbm.nb_desc_default(**r["desc"]),
+                                 nbm.nb_params_default(**r["params"]), 30) for r in runs]
+        nbm.nb_server_drain(srv, 120.0)
+        res = [nbm.nb_poll(srv, t) for t in tickets]
+        st = nbm.nb_server_stats_read(srv)
+    finally:
+        nbm.nb_server_destroy(srv)
+    assert all(r["status"] == nbm.NB_OK and r["steps"] == 30 for r in res)
+    assert st["peak_requests"] == 8
+    assert st["peak_elements"] == 8 * 1024
+    # wherever a run sat in the arena, its result is the run alone
+    for k in (0, 5):
+        _, _, _, ref = _alone(nbm, runs[k], 30, cfg=cfg)
+        assert res[k]["diag"]["e_kin"] == ref["e_kin"]
+        assert np.array_equal(res[k]["diag"]["com"], ref["com"])
 
 
 def test_server_large_slots_use_symmetric_kernel(nbm):
