@@ -262,6 +262,16 @@ nb_status nb_get_info(nb_system_t sys, nb_info* out);
  * until the result is in acc_out. */
 nb_status nb_forces(nb_system_t sys, double* acc_out, int out_on_device);
 
+/* The same evaluation for the rows [lo, hi) only (0 <= lo < hi <= n):
+ * acc_out receives (hi - lo) x 3 doubles, bit for bit the rows of nb_forces.
+ * Only the pair-kernel work items that contribute to those rows run (the
+ * i-blocks holding them and, with the symmetric kernel, the items whose
+ * j-range holds them); the contact term is evaluated for the whole system.
+ * This is the force step of a row-split run of one system over several
+ * devices (Eqs. 4-6 for the rows a device owns, against all n elements). */
+nb_status nb_forces_rows(nb_system_t sys, int64_t lo, int64_t hi, double* acc_out,
+                         int out_on_device);
+
 /* Enqueue nsteps leap-frog steps (kick-drift-kick):
  *   v^{k+1/2} = v^k + a^k dt/2;  x^{k+1} = x^k + v^{k+1/2} dt;
  *   a^{k+1} = F(x^{k+1}, v^{k+1/2}, radii of step k+1);

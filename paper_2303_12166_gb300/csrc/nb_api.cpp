@@ -232,6 +232,16 @@ nb_status nb_forces(nb_system_t sys, double* acc_out, int out_on_device) {
     });
 }
 
+nb_status nb_forces_rows(nb_system_t sys, int64_t lo, int64_t hi, double* acc_out,
+                         int out_on_device) {
+    if (!sys) return set_error(NB_EINVAL, "null system");
+    return guarded([&] {
+        nb::DeviceScope ds(sys->batch.device());
+        nb::TraceRange tr("nb_forces_rows");
+        return sys->batch.forces_rows_out(0, lo, hi, acc_out, out_on_device != 0);
+    });
+}
+
 nb_status nb_step(nb_system_t sys, int64_t nsteps) {
     if (!sys) return set_error(NB_EINVAL, "null system");
     return guarded([&] {

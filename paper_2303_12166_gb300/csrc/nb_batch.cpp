@@ -783,11 +783,13 @@ nb_status Batch::plan_pairs_() {
     return NB_OK;
 }
 
-nb_status Batch::launch_pairs_(bool pot, int nitems_limit) {
+nb_status Batch::launch_pairs_(bool pot, int nitems_limit, const PairItem* list) {
     const bool sym = prec_ == 32 && cfg_.sym && !pot;
     int n = (int)(sym ? sitems_ : items_).size();
     if (nitems_limit >= 0 && nitems_limit < n) n = nitems_limit;
     if (n == 0) return NB_OK;
+    const PairItem* sl = list ? list : sitems_d_;
+    const PairItem* ol = list ? list : items_d_;
     int* ctr = nullptr;
     if (dynamic_ || sym) {
         NB_CU(cudaMemsetAsync(counter_d_, 0, sizeof(int), stream_));
@@ -801,13 +803,13 @@ nb_status Batch::launch_pairs_(bool pot, int nitems_limit) {
         if (fx)
             NB_CU(cudaMemsetAsync(d_.facc.x, 0, 3 * (size_t)d_.ntot * sizeof(unsigned long long),
                                   stream_));
-        NB_CU(launch_pair_sym(d_, tmass_d_, sitems_d_, n, cfg_, ctr, stream_));
+        NB_CU(launch_pair_sym(d_, tmass_d_, sl, n, cfg_, ctr, stream_));
     } else if (prec_ == 32) {
         PairCfg c = cfg_;
         c.grid = pot_grid_;
-        NB_CU(launch_pair_f32(d_, tmass_d_, items_d_, n, c, pot, ctr, stream_));
+        NB_CU(launch_pair_f32(d_, tmass_d_, ol, n, c, pot, ctr, stream_));
     } else {
-        NB_CU(launch_pair_f64(d_, items_d_, n, cfg_.grid, pot, ctr, stream_));
+        NB_CU(launch_pair_f64(d_, ol, n, cfg_.grid, pot, ctr, stream_));
     }
     kernels_ += 1;
     pairs_done_ += pairs_per_step();
@@ -1106,9 +1108,14 @@ nb_status Batch::forces_out(int s, double* out, bool out_on_device) {
     if (s < 0 || s >= nslots() || !sc_[s].active) return set_error(NB_ENOTFOUND, "no system %d", s);
     if (!out) return set_error(NB_EINVAL, "null output");
     NB_TRY(eval_forces(0, false, false));
-    const int64_t n = sc_[s].n;
+    return rows_out_(s, 0, sc_[s].n, out, out_on_device);
+}
+
+// rows [lo, hi) of system s's last force evaluation into out (host or device)
+nb_status Batch::rows_out_(int s, int64_t lo, int64_t hi, double* out, bool out_on_device) {
+    const int64_t n = hi - lo;
     if (out_on_device) {
-        NB_CU(launch_sum_forces(d_, s, n, out, stream_));
+        NB_CU(launch_sum_forces(d_, s, lo, n, out, stream_));
         return sync();
     }
     if (fout_cap_ < n) {
@@ -1117,10 +1124,46 @@ nb_status Batch::forces_out(int s, double* out, bool out_on_device) {
         NB_TRY(alloc_((void**)&fout_d_, (size_t)n * 3 * sizeof(double)));
         fout_cap_ = n;
     }
-    NB_CU(launch_sum_forces(d_, s, n, fout_d_, stream_));
+    NB_CU(launch_sum_forces(d_, s, lo, n, fout_d_, stream_));
     NB_CU(cudaMemcpyAsync(out, fout_d_, (size_t)n * 3 * sizeof(double), cudaMemcpyDeviceToHost,
                           stream_));
     return sync();
+}
+
+nb_status Batch::forces_rows_out(int s, int64_t lo, int64_t hi, double* out,
+                                 bool out_on_device) {
+    if (s < 0 || s >= nslots() || !sc_[s].active) return set_error(NB_ENOTFOUND, "no system %d", s);
+    if (!out) return set_error(NB_EINVAL, "null output");
+    const SysConst& c = sc_[s];
+    if (!(0 <= lo && lo < hi && hi <= c.n))
+        return set_error(NB_EINVAL, "rows [%lld, %lld) are not a range of 0 .. %lld",
+                         (long long)lo, (long long)hi, (long long)c.n);
+    NB_TRY(plan_pairs_());
+    NB_TRY(push_consts_());
+    // the items that add to rows [lo, hi): their i-block holds some of the
+    // rows, or (both-sided items) their j-range does; each such item is the
+    // plan's own, so every row receives exactly the values of a full pass
+    const int64_t r0 = c.off + lo, r1 = c.off + hi;
+    std::vector<PairItem> sel;
+    const bool sym = prec_ == 32 && cfg_.sym;
+    for (const PairItem& it : sym ? sitems_ : items_) {
+        if (it.sys != s) continue;
+        const bool irows = it.i0 < r1 && it.i0 + it.iend_rel > r0;
+        const bool jrows = it.chunk < 0 && it.j0 < r1 && it.j0 + it.nj > r0;
+        if (irows || jrows) sel.push_back(it);
+    }
+    if ((int)sel.size() > ritems_cap_) {
+        ritems_cap_ = 0;
+        NB_TRY(free_((void**)&ritems_d_));
+        const int want = std::max<int>(64, (int)sel.size());
+        NB_TRY(alloc_((void**)&ritems_d_, (size_t)want * sizeof(PairItem)));
+        ritems_cap_ = want;
+    }
+    NB_CU(cudaMemcpyAsync(ritems_d_, sel.data(), sel.size() * sizeof(PairItem),
+                          cudaMemcpyHostToDevice, stream_));
+    if (any_contacts_()) NB_TRY(contact_pass_(0, false, true));
+    NB_TRY(launch_pairs_(false, (int)sel.size(), ritems_d_));
+    return rows_out_(s, lo, hi, out, out_on_device);
 }
 
 nb_status Batch::read_flags(std::vector<SysMut>& out) {

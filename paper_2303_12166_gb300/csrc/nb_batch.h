@@ -139,6 +139,9 @@ public:
 
     nb_status sync();                 // wait + report device-side flags
     nb_status forces_out(int s, double* out, bool out_on_device);
+    // rows [lo, hi) of system s only (the work items they need; bitwise the
+    // rows of forces_out)
+    nb_status forces_rows_out(int s, int64_t lo, int64_t hi, double* out, bool out_on_device);
     // energy = false skips the potential-energy force pass (e_grav and e_rep
     // are then NaN): O(N) instead of O(N^2)
     nb_status diagnostics(int s, nb_diag* out, bool energy = true);
@@ -175,8 +178,10 @@ private:
     nb_status free_(void** p);
     nb_status push_consts_();
     nb_status plan_pairs_();
-    nb_status launch_pairs_(bool pot, int nitems_limit = -1);
+    // list: a device item list to launch instead of the plan's own (n items)
+    nb_status launch_pairs_(bool pot, int nitems_limit = -1, const PairItem* list = nullptr);
     nb_status step_body_(int64_t n);
+    nb_status rows_out_(int s, int64_t lo, int64_t hi, double* out, bool out_on_device);
     void release_();
 
     int device_ = 0;
@@ -209,6 +214,8 @@ private:
     std::vector<PairItem> sitems_;     // symmetric work list (cfg_.sym)
     PairItem* sitems_d_ = nullptr;
     int sitems_cap_ = 0;
+    PairItem* ritems_d_ = nullptr;     // the items of a row-range evaluation
+    int ritems_cap_ = 0;
     int pot_grid_ = 0;                 // persistent grid of the one-sided list
     int* counter_d_ = nullptr;
     bool dynamic_ = false;

@@ -206,8 +206,10 @@ cudaError_t launch_shadow(const BatchDev& b, int64_t off, int64_t n, cudaStream_
 cudaError_t launch_kick(const BatchDev& b, KickMode mode, bool build_keys, cudaStream_t s);
 // k += 1 for every active system (the last kernel of a step)
 cudaError_t launch_advance(const BatchDev& b, cudaStream_t s);
-// out3: n x 3 doubles, the summed acceleration of system `sys` (n real elements)
-cudaError_t launch_sum_forces(const BatchDev& b, int sys, int64_t n, double* out3, cudaStream_t s);
+// out3: count x 3 doubles, the summed acceleration of rows [r0, r0 + count)
+// of system `sys`
+cudaError_t launch_sum_forces(const BatchDev& b, int sys, int64_t r0, int64_t count, double* out3,
+                              cudaStream_t s);
 // Checkpoint staging of one system (elements [off, off + n)): xv n x 6 and a
 // n x 3 (a may be null), FP64 in caller order, device memory.
 cudaError_t launch_state_pack(const BatchDev& b, int64_t off, int64_t n, double* xv, double* a,

@@ -149,11 +149,12 @@ __global__ void shadow_kernel(BatchDev b, int64_t off, int64_t n) {
     write_vel32(b, i, b.V[i]);
 }
 
-__global__ void sum_forces_kernel(BatchDev b, int s, double* __restrict__ out) {
+__global__ void sum_forces_kernel(BatchDev b, int s, int64_t r0, int64_t count,
+                                  double* __restrict__ out) {
     const SysConst& c = b.sc[s];
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= c.n) return;
-    const double3 a = total_acc(b, c, c.off + r);
+    if (r >= count) return;
+    const double3 a = total_acc(b, c, c.off + r0 + r);
     out[3 * r + 0] = a.x;
     out[3 * r + 1] = a.y;
     out[3 * r + 2] = a.z;
@@ -447,11 +448,11 @@ cudaError_t launch_store_acc(const BatchDev& b, int only, cudaStream_t s) {
     return kick_t<KICK_STORE, false>(b, s, only);
 }
 
-cudaError_t launch_sum_forces(const BatchDev& b, int sys, int64_t n, double* out3,
-                              cudaStream_t s) {
+cudaError_t launch_sum_forces(const BatchDev& b, int sys, int64_t r0, int64_t count,
+                              double* out3, cudaStream_t s) {
     const int nt = 256;
-    const unsigned ng = (unsigned)((n + nt - 1) / nt);
-    if (ng) sum_forces_kernel<<<ng, nt, 0, s>>>(b, sys, out3);
+    const unsigned ng = (unsigned)((count + nt - 1) / nt);
+    if (ng) sum_forces_kernel<<<ng, nt, 0, s>>>(b, sys, r0, count, out3);
     return cudaGetLastError();
 }
 

@@ -120,6 +120,7 @@ _sig("nb_create_system", ctypes.c_int,
 _sig("nb_destroy", None, [_P])
 _sig("nb_get_info", ctypes.c_int, [_P, ctypes.POINTER(nb_info)])
 _sig("nb_forces", ctypes.c_int, [_P, _P, ctypes.c_int])
+_sig("nb_forces_rows", ctypes.c_int, [_P, _I64, _I64, _P, ctypes.c_int])
 _sig("nb_step", ctypes.c_int, [_P, _I64])
 _sig("nb_sync", ctypes.c_int, [_P])
 _sig("nb_diagnostics", ctypes.c_int, [_P, ctypes.POINTER(nb_diag)])
@@ -323,6 +324,18 @@ def nb_forces(h, out=None):
         raise ValueError("out must be a C-contiguous float64 (n, 3) array")
     a = np.empty((n, 3), dtype=np.float64) if out is None else out
     _check(_lib.nb_forces(_P(h), a.ctypes.data_as(_P), 0), "nb_forces")
+    return a
+
+
+def nb_forces_rows(h, lo: int, hi: int):
+    """Accelerations of rows [lo, hi) only: (hi - lo, 3) float64, bit for
+    bit those rows of nb_forces."""
+    n = nb_get_info(h).n
+    if not (0 <= lo < hi <= n):
+        raise ValueError(f"rows [{lo}, {hi}) are not a range of 0 .. {n}")
+    a = np.empty((hi - lo, 3), dtype=np.float64)
+    _check(_lib.nb_forces_rows(_P(h), int(lo), int(hi), a.ctypes.data_as(_P), 0),
+           "nb_forces_rows")
     return a
 
 
@@ -684,6 +697,9 @@ class System:
 
     def forces(self, out=None):
         return nb_forces(self.h, out)
+
+    def forces_rows(self, lo: int, hi: int):
+        return nb_forces_rows(self.h, lo, hi)
 
     def step(self, nsteps: int):
         nb_step(self.h, nsteps)

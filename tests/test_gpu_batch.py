@@ -144,7 +144,8 @@ def test_server_admits_by_request_bytes(nbm):
     """Admission counts each run's own device bytes against the budget.  The
     budget holds one run of the largest size (4,096 elements) but not that
     run and a 1,024-element one: the three small runs queued behind the large
-    one wait until it is retired, then all three run at once."""
+    one (long enough for several admission rounds to pass while it runs)
+    wait until it is retired, then all three run at once."""
     with pytest.raises(nbm.NbError) as ei:
         nbm.nb_server_create(1000, 4, 4096, 32)
     assert ei.value.status == nbm.NB_EBUDGET
@@ -161,7 +162,7 @@ def test_server_admits_by_request_bytes(nbm):
     try:
         assert nbm.nb_server_info(srv)["nslots"] == 8
         t_big = nbm.nb_submit(srv, nbm.nb_desc_default(**big["desc"]),
-                              nbm.nb_params_default(**big["params"]), 20)
+                              nbm.nb_params_default(**big["params"]), 400)
         t_small = [nbm.nb_submit(srv, nbm.nb_desc_default(**small["desc"]),
                                  nbm.nb_params_default(**small["params"]), 8) for _ in range(3)]
         with pytest.raises(nbm.NbError) as ei:
