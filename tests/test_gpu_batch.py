@@ -208,19 +208,21 @@ def test_server_many_small_runs_share_the_arena(nbm):
     runs = [dict(s, desc=dict(s["desc"], seed=40 + k)) for k in range(8)]
     try:
         cfg = nbm.nb_server_pair_cfg(srv)
+        # long enough (several chunks of steps) that all eight are admitted
+        # before the first one finishes
         tickets = [nbm.nb_submit(srv, nbm.nb_desc_default(**r["desc"]),
-                                 nbm.nb_params_default(**r["params"]), 30) for r in runs]
+                                 nbm.nb_params_default(**r["params"]), 400) for r in runs]
         nbm.nb_server_drain(srv, 120.0)
         res = [nbm.nb_poll(srv, t) for t in tickets]
         st = nbm.nb_server_stats_read(srv)
     finally:
         nbm.nb_server_destroy(srv)
-    assert all(r["status"] == nbm.NB_OK and r["steps"] == 30 for r in res)
+    assert all(r["status"] == nbm.NB_OK and r["steps"] == 400 for r in res)
     assert st["peak_requests"] == 8
     assert st["peak_elements"] == 8 * 1024
     # wherever a run sat in the arena, its result is the run alone
     for k in (0, 5):
-        _, _, _, ref = _alone(nbm, runs[k], 30, cfg=cfg)
+        _, _, _, ref = _alone(nbm, runs[k], 400, cfg=cfg)
         assert res[k]["diag"]["e_kin"] == ref["e_kin"]
         assert np.array_equal(res[k]["diag"]["com"], ref["com"])
 
