@@ -132,8 +132,8 @@ def _pair_traffic(workload, cfg):
     with open(p) as f:
         rec = json.load(f)
     key = ",".join(str(cfg[k]) for k in PAIR_CFG_KEYS)
-    if rec.get("workload") != workload or rec.get("pair_cfg") != key or \
-            rec.get("sources_sha256_16") != pair_sources_sha():
+    if rec.get("workload") != workload or key not in rec.get("applies_to", [rec.get("pair_cfg")]) \
+            or rec.get("sources_sha256_16") != pair_sources_sha():
         return None
     return float(rec["dram_bytes_per_launch"])
 

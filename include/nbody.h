@@ -320,10 +320,8 @@ nb_status nb_measure_unit_rates(nb_unit_rates* out, void* stream);
 /* Select a pair-kernel variant; it must be one of nb_pair_cfg_variants'
  * (NB_EINVAL otherwise).  The field ms is ignored.  Until a variant is
  * selected (or tuned), a system runs the symmetric kernel with rotating
- * shares (tile 256, 12 i-elements per thread, 2 shared-reciprocal slots),
- * or the one-sided kernel (tile 256, 8 i-elements, 6 shared-reciprocal
- * slots) when the symmetric kernel's O(N^2 / 1536) share buffers do not
- * fit in device memory. */
+ * shares (tile 256, 12 i-elements per thread, no shared reciprocal), which
+ * sums both sides of every pair into O(N) fixed-point accumulators. */
 nb_status nb_set_pair_cfg(nb_system_t sys, const nb_pair_cfg* cfg);
 nb_status nb_get_pair_cfg(nb_system_t sys, nb_pair_cfg* cfg);
 /* The built pair-kernel variants (an implementation detail of this library;

@@ -204,8 +204,8 @@ private:
     // (SysConst::fxp; the scale is set at load)
     std::vector<char> fx_ok_;
     // default: the symmetric kernel with rotating shares (12 i-elements per
-    // thread, 2 shared-reciprocal slots)
-    PairCfg cfg_{256, 12, 128, 0, 2, 0, 0, 2, 3};
+    // thread, every reciprocal on the MUFU unit: the fastest at 1M elements)
+    PairCfg cfg_{256, 12, 128, 0, 2, 0, 0, 0, 3};
     float* tmass_d_ = nullptr;   // per j-tile common G m (see launch_pair_f32)
     int64_t tmass_cap_ = 0;
     std::vector<PairItem> items_;      // one-sided work list (also the potential pass)

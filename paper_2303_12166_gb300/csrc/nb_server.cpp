@@ -96,7 +96,7 @@ constexpr double kMinPairsPerStep = 1e10;
 
 nb::PairCfg server_pair_cfg(int64_t slot_n, int prec) {
     if (prec == 32 && slot_n >= 16384) {
-        const nb::PairCfg sym{256, 12, 128, 0, 2, 0, 0, 2, 3};
+        const nb::PairCfg sym{256, 12, 128, 0, 2, 0, 0, 0, 3};
         if (nb::pair_cfg_supported(sym)) return sym;
     }
     return nb::kOneSided;

@@ -188,18 +188,21 @@ def _grown_radii(orc, R0, n_donor, desc, k):
 def test_binary_64k_growing_donor_sampled(nbm, orc):
     """The 65,536-element binary (q = 0.3, eps 0.005, dt 5e-4) with the donor
     growing from 0.9 to 1.15 r_L over 10^4 steps, stepped on the GPU at full
-    size.  At steps 25 and 50: the accelerations at the state (x^k, v^k) with
-    the radii of step k, and the stored a^k of the integrator at (x^k,
-    v^{k-1/2}), against the oracle on sampled rows -- 320 random rows, the
-    donor/accretor index boundary and the 64 donor elements nearest the
-    accretor (the donor's surface facing L1, where its growth acts first)."""
+    size.  At steps 25, 50 and 1,000: the accelerations at the state (x^k,
+    v^k) with the radii of step k, and the stored a^k of the integrator at
+    (x^k, v^{k-1/2}), against the oracle on sampled rows -- 320 random rows,
+    the donor/accretor index boundary and the 64 donor elements nearest the
+    accretor (the donor's surface facing L1, where its growth acts first).
+    At the first two, while the start's overlaps still push hard, the
+    initial radii would give forces farther from the oracle than the
+    tolerance: the growth is visible."""
     desc, params = workload_kwargs("binary_64k")
     ox, ov, om, oR, og = oracle_ic(orc, desc, params)
     nd, dt = desc["n_donor"], params["dt"]
     with _make(nbm, desc, params) as s:
         n = s.n
         k = 0
-        for k_next in (25, 50):
+        for k_next in (25, 50, 1000):
             s.step(k_next - k)
             s.sync()
             k = k_next
@@ -218,10 +221,11 @@ def test_binary_64k_growing_donor_sampled(nbm, orc):
             vh = v - 0.5 * dt * a_stored
             ref_h = orc.forces_rows(rows, x, vh, om, Rk, og, **kw)
             assert rms_rel(a_stored[rows], ref_h) <= 1e-5
-            # the growth is visible at this tolerance: the initial radii
-            # give accelerations farther off than the tolerance
-            ref0 = orc.forces_rows(rows, x, v, om, oR, og, **kw)
-            assert rms_rel(ref0, ref) > 1e-4
+            if k <= 50:
+                # the growth is visible at this tolerance: the initial radii
+                # give accelerations farther off than the tolerance
+                ref0 = orc.forces_rows(rows, x, v, om, oR, og, **kw)
+                assert rms_rel(ref0, ref) > 1e-4
             assert s.diagnostics()["r_donor"] == pytest.approx(
                 orc.donor_scale(k, desc["f_donor"], desc["expand_rate"], desc["expand_steps"]),
                 rel=1e-15)
