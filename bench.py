@@ -693,9 +693,12 @@ def run_ours(args):
         rates = {"sm_mhz": mhz,
                  "fp32_lanes_per_clk_sm": r["fp32_lanes_per_s_sm"] / (mhz * 1e6),
                  "mufu_sqrt_per_clk_sm": r["mufu_sqrt_per_s_sm"] / (mhz * 1e6),
-                 "mufu_rcp_per_clk_sm": r["mufu_rcp_per_s_sm"] / (mhz * 1e6)}
+                 "mufu_rcp_per_clk_sm": r["mufu_rcp_per_s_sm"] / (mhz * 1e6),
+                 "pair_mix_evals_per_clk_sm": r["pair_mix_evals_per_s_sm"] / (mhz * 1e6)}
+        pair_mix_per_s = r["pair_mix_evals_per_s_sm"] * r["sm_count"]
     except nbm.NbError:
         rates = None
+        pair_mix_per_s = None
     ppc, x_opt = pairs_per_sm_clk(sym, rates)
     peak_pairs = props.multi_processor_count * sm_max_mhz * 1e6 * ppc
     pair_ms = prof["pair_ms"] / max(prof["pair_launches"], 1)
@@ -794,6 +797,16 @@ def run_ours(args):
                                        f"{'2 interactions (i and j sides)' if sym else '1 interaction'}"
                                        f" per evaluation, a fraction {x_opt:.3f} of reciprocals shared",
                          "unit_rates": rates,
+                         # the symmetric kernel's own instruction mix run from
+                         # registers (no memory traffic) at its launch shape
+                         "mix_ceiling": None if (pair_mix_per_s is None or not sym) else {
+                             "value": 2.0 * pair_mix_per_s, "unit": "pairs/s",
+                             "frac": achieved / (2.0 * pair_mix_per_s),
+                             "basis": "pair_mix_kernel: the rotating step of the symmetric "
+                                      "kernel (12 i-elements x 2 j per thread, 15 packed FP32 + "
+                                      "4 MUFU per i-element, 3 shuffles) from registers, 2 x 128 "
+                                      "threads per SM, measured in this run; 2 interactions per "
+                                      "evaluation"},
                          "kernel": "pair_sym_kernel" if sym else "pair_f32_kernel",
                          "kernel_ms": pair_ms},
             "cpu_baseline": cpu,

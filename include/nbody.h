@@ -306,14 +306,19 @@ nb_status nb_autotune(nb_system_t sys, int reps, nb_pair_cfg* best);
  * current device at the clock it runs at (an implementation aid of this
  * library; the paper has no counterpart): MUFU square roots and
  * reciprocals, and FP32 lanes of packed FMA, per second per SM (one wave of
- * resident blocks timed with CUDA events, best of three).  Divide by the SM
- * clock for per-clock rates.  Runs for ~20 ms on `stream`, blocks until
+ * resident blocks timed with CUDA events, best of three); and the pair
+ * evaluations per second per SM of the symmetric kernel's own arithmetic
+ * (its rotating step, 15 packed FP32 and 4 MUFU operations per i-element and
+ * j-pair, with its shuffles) run from registers at its launch shape: the
+ * rate the instruction mix reaches with no memory traffic.  Divide by the
+ * SM clock for per-clock rates.  Runs for ~40 ms on `stream`, blocks until
  * done. */
 typedef struct {
     int32_t sm_count;
     double mufu_sqrt_per_s_sm;
     double mufu_rcp_per_s_sm;
     double fp32_lanes_per_s_sm;
+    double pair_mix_evals_per_s_sm;
 } nb_unit_rates;
 nb_status nb_measure_unit_rates(nb_unit_rates* out, void* stream);
 

@@ -11,11 +11,21 @@
 // not.)  The MUFU chains add one FP32
 // addition per operation to keep the values in range; it runs on the FP32
 // pipe and does not limit the MUFU count.
+//
+// A fourth probe runs the symmetric pair kernel's arithmetic itself from
+// registers: the rotating form's step (12 i-elements per thread against two
+// j, 15 packed FP32 operations and 4 MUFU operations per i-element, the
+// three shuffles that pass the j-side sums on) with no memory traffic, at
+// the pair kernel's launch shape (2 blocks of 128 threads per SM, 255
+// registers).  Its evaluations per second are the rate the instruction mix
+// reaches when nothing else limits it: the pair kernel's ceiling in practice,
+// next to the bound computed from the separate pipe rates.
 #include <algorithm>
 #include <cstdint>
 #include <vector>
 
 #include "nb_batch.h"
+#include "nb_pair_common.cuh"
 
 namespace nb {
 namespace {
@@ -64,6 +74,95 @@ __global__ void __launch_bounds__(kThreads) unit_rate_kernel(float seed, float* 
     sink[blockIdx.x * kThreads + threadIdx.x] = s;
 }
 
+constexpr int kMixBI = 12;         // i-elements per thread
+constexpr int kMixThreads = 128;
+constexpr int kMixBlocksPerSM = 2;
+constexpr int kMixSteps = 4096;    // rotating steps per thread
+
+__global__ void __launch_bounds__(kMixThreads, kMixBlocksPerSM)
+    pair_mix_kernel(float seed, float eps, float* sink) {
+    using namespace pairk;
+    const int lane = threadIdx.x & 31;
+    const int next = (lane + 1) & 31;
+    f2 xi[kMixBI], yi[kMixBI], zi[kMixBI], ax[kMixBI], ay[kMixBI], az[kMixBI];
+#pragma unroll
+    for (int b = 0; b < kMixBI; ++b) {
+        const float v = seed + 1e-3f * threadIdx.x + 0.01f * b;
+        xi[b] = pk(v, v + 0.1f);
+        yi[b] = pk(0.5f * v, v - 0.2f);
+        zi[b] = pk(v - 0.3f, 0.25f * v);
+        ax[b] = ay[b] = az[b] = 0ull;
+    }
+    // the j-pair: moved a little every step (three packed additions, where
+    // the pair kernel loads it from shared memory)
+    f2 px = pk(0.3f, 0.7f), py = pk(-0.2f, 0.4f), pz = pk(0.1f, -0.6f);
+    const f2 dp = pk(1e-5f, -2e-5f);
+    const f2 eps2 = pk(eps, eps);
+    const f2 floor2 = pk(kD2Floor, kD2Floor);
+    f2 sx = 0ull, sy = 0ull, sz = 0ull;
+#pragma unroll 8
+    for (int st = 0; st < kMixSteps; ++st) {
+#pragma unroll
+        for (int b = 0; b < kMixBI; ++b) {
+            const f2 dx = sub2(px, xi[b]);
+            const f2 dy = sub2(py, yi[b]);
+            const f2 dz = sub2(pz, zi[b]);
+            const f2 d2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, floor2)));
+            const f2 r = sqrt2(d2);
+            const f2 t1 = add2(r, eps2);
+            const f2 f = rcp2(mul2(mul2(t1, t1), r));
+            ax[b] = fma2(f, dx, ax[b]);
+            ay[b] = fma2(f, dy, ay[b]);
+            az[b] = fma2(f, dz, az[b]);
+            sx = fma2(f, dx, sx);
+            sy = fma2(f, dy, sy);
+            sz = fma2(f, dz, sz);
+        }
+        sx = __shfl_sync(0xffffffffu, sx, next);
+        sy = __shfl_sync(0xffffffffu, sy, next);
+        sz = __shfl_sync(0xffffffffu, sz, next);
+        px = add2(px, dp);
+        py = add2(py, dp);
+        pz = add2(pz, dp);
+    }
+    f2 t = add2(sx, add2(sy, sz));
+#pragma unroll
+    for (int b = 0; b < kMixBI; ++b) t = add2(t, add2(ax[b], add2(ay[b], az[b])));
+    sink[blockIdx.x * kMixThreads + threadIdx.x] = sum2(t);
+}
+
+// pair evaluations per second per SM of pair_mix_kernel, best of three
+nb_status measure_mix(int sms, float* sink, cudaStream_t s, double* rate) {
+    const int blocks = sms * kMixBlocksPerSM;
+    cudaEvent_t e0, e1;
+    NB_CU(cudaEventCreate(&e0));
+    cudaError_t e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return set_error(NB_ECUDA, "%s", cudaGetErrorString(e));
+    }
+    pair_mix_kernel<<<blocks, kMixThreads, 0, s>>>(0.37f, 0.005f, sink);  // warm-up
+    float best = 0.f;
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+        cudaEventRecord(e0, s);
+        pair_mix_kernel<<<blocks, kMixThreads, 0, s>>>(0.37f, 0.005f, sink);
+        cudaEventRecord(e1, s);
+        e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && (best == 0.f || ms < best)) best = ms;
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return set_error(NB_ECUDA, "pair-mix probe: %s", cudaGetErrorString(e));
+    if (!(best > 0.f)) return set_error(NB_ECUDA, "pair-mix probe: no time recorded");
+    // two j per packed register, kMixBI i-elements per thread
+    const double evals_sm = (double)kMixBlocksPerSM * kMixThreads * kMixSteps * kMixBI * 2.0;
+    *rate = evals_sm / (best * 1e-3);
+    return NB_OK;
+}
+
 // operations (lanes) per second per SM, best of three timed launches
 template <int OP>
 nb_status measure(int sms, float* sink, double lanes_per_op, cudaStream_t s, double* rate) {
@@ -106,12 +205,13 @@ extern "C" nb_status nb_measure_unit_rates(nb_unit_rates* out, void* stream) {
     int dev = 0, sms = 0;
     NB_CU(cudaGetDevice(&dev));
     NB_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int blocks = sms * kBlocksPerSM;
+    const int blocks = sms * std::max(kBlocksPerSM * kThreads, kMixBlocksPerSM * kMixThreads);
     float* sink = nullptr;
-    NB_CU(cudaMallocAsync((void**)&sink, (size_t)blocks * kThreads * sizeof(float), s));
+    NB_CU(cudaMallocAsync((void**)&sink, (size_t)blocks * sizeof(float), s));
     nb_status st = measure<0>(sms, sink, 1.0, s, &out->mufu_sqrt_per_s_sm);
     if (st == NB_OK) st = measure<1>(sms, sink, 1.0, s, &out->mufu_rcp_per_s_sm);
     if (st == NB_OK) st = measure<2>(sms, sink, 2.0, s, &out->fp32_lanes_per_s_sm);
+    if (st == NB_OK) st = measure_mix(sms, sink, s, &out->pair_mix_evals_per_s_sm);
     cudaFreeAsync(sink, s);
     out->sm_count = sms;
     if (st == NB_OK) NB_CU(cudaStreamSynchronize(s));

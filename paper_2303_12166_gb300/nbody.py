@@ -88,7 +88,7 @@ class nb_server_stats(ctypes.Structure):
 
 class nb_unit_rates(ctypes.Structure):
     _fields_ = [("sm_count", _I32), ("mufu_sqrt_per_s_sm", _D), ("mufu_rcp_per_s_sm", _D),
-                ("fp32_lanes_per_s_sm", _D)]
+                ("fp32_lanes_per_s_sm", _D), ("pair_mix_evals_per_s_sm", _D)]
 
 
 class nb_info(ctypes.Structure):

@@ -507,6 +507,12 @@ def test_unit_rate_probe(nbm):
     # the two MUFU operations and the FP32 lanes keep the SM's 1 : 8 ratio
     ratio = r["fp32_lanes_per_s_sm"] / r["mufu_rcp_per_s_sm"]
     assert 7.0 <= ratio <= 9.0, r
+    # the symmetric kernel's instruction mix from registers: at most the
+    # bound of the separate pipes (15 FP32 lanes and 2 MUFU per evaluation)
+    mix = r["pair_mix_evals_per_s_sm"]
+    bound = min(r["fp32_lanes_per_s_sm"] / 15.0,
+                1.0 / (1.0 / r["mufu_sqrt_per_s_sm"] + 1.0 / r["mufu_rcp_per_s_sm"]))
+    assert 0.3 * bound <= mix <= 1.02 * bound, r
 
 
 # ---------------------------------------------------------------- stored values
