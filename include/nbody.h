@@ -187,11 +187,15 @@ typedef struct nb_pair_cfg {
                               whose two pairs per packed register share one
                               MUFU reciprocal (1/a = b/(ab)); used while
                               eps >= 1e-4, else the plain reciprocal */
-    int32_t symmetric;     /* >= 1: every unordered pair evaluated once and both
-                              elements get their share (Newton's third law),
-                              with this many groups of 8 j-elements in flight
-                              per thread; then nr_slots, i_packed and
-                              shared_rcp are 0.  0: one-sided sums */
+    int32_t symmetric;     /* 0: one-sided sums.  >= 1: every unordered pair
+                              evaluated once and both elements get their
+                              share (Newton's third law), both sides summed
+                              into per-element fixed-point accumulators; the
+                              j-side sums of a warp by a reduction with 1 or
+                              2 groups of 8 j-elements in flight per thread
+                              (1, 2) or rotating between the lanes (3).
+                              nr_slots is then 0; i_packed and shared_rcp as
+                              nb_pair_cfg_variants lists them */
     double ms;             /* measured time of one pair pass (autotune), else 0 */
 } nb_pair_cfg;
 
