@@ -475,6 +475,57 @@ def measure_fp64_path(nbm, torch, dev, stream, args):
     return out
 
 
+def measure_config1_run(nbm, torch, dev, stream, args):
+    """The 65,536-element binary run as configured: 10,000 steps with the
+    donor growing from 0.9 to 1.15 r_L (L1 overflow), in chunks of 500
+    steps, CUDA events around the whole run; the error against the oracle of
+    the accelerations at the final state, and the mass-transfer diagnostics
+    there."""
+    w = _workload("binary_64k")
+    n = w["n_donor"] + w["n_accretor"]
+    desc = nbm.nb_desc_default(n_donor=w["n_donor"], n_accretor=w["n_accretor"], q=w["q"],
+                               f_donor=w["f_donor"], f_accretor=w["f_accretor"],
+                               expand_rate=w["expand_rate"], expand_steps=w["expand_steps"],
+                               sigma_v=w["sigma_v"], seed=w["seed"])
+    params = nbm.nb_params_default(eps=w["eps"], dt=w["dt"], beta=0.5)
+    total, chunk = args.config1_steps, 500
+    with nbm.System(desc, params, stream=stream) as sy:
+        tuned = sy.autotune(1)
+        d0 = sy.diagnostics()
+        torch.cuda.synchronize(dev)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        done = 0
+        while done < total:
+            k = min(chunk, total - done)
+            sy.step(k)
+            done += k
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        sy.sync()
+        ms = ev0.elapsed_time(ev1)
+        d1 = sy.diagnostics()
+        xv, _, meta = sy.get_state(with_acc=False)
+        a = sy.forces()
+    acc = force_error(w, w["eps"], 0.5, xv[:, :3], xv[:, 3:], a,
+                      _sample_rows(n, w["n_donor"], 1024, 5), int(meta.step))
+    return {"workload": "binary_64k", "steps": total, "ms": ms, "ms_per_step": ms / total,
+            "value": float(n) * n * total / (ms * 1e-3), "unit": "pairs/s",
+            "pair_cfg": {k: tuned[k] for k in PAIR_CFG_KEYS},
+            "r_donor": [float(d0["r_donor"]), float(d1["r_donor"])],
+            "donor_past_L1": [int(d0["n_past_L1"]), int(d1["n_past_L1"])],
+            "donor_in_accretor_lobe": [int(d0["n_in_accretor_lobe"]),
+                                       int(d1["n_in_accretor_lobe"])],
+            "mass_in_accretor_lobe": float(d1["m_in_accretor_lobe"]),
+            "unbound": int(d1["n_unbound"]),
+            "e_tot": [float(d0["e_tot"]), float(d1["e_tot"])],
+            "l_z": [float(d0["l"][2]), float(d1["l"][2])],
+            "accuracy": dict(acc, tolerance=1e-5),
+            "note": "timed in chunks of 500 steps (one CUDA graph each); the donor radius "
+                    "reaches 1.15 r_L at step 10,000"}
+
+
 def measure_served(nbm, stream, args):
     """Poisson arrivals (20/s) of sweep runs: element count log-uniform in
     [4,096, 262,144], donor expansion rate in [0.5, 2]e-5 r_L per step, steps
@@ -760,12 +811,14 @@ def run_ours(args):
                               "library's own state and the radii of that step"}
 
     sysm.close()
-    batched = served = fp64_path = None
+    batched = served = fp64_path = config1 = None
     if not args.no_extras:
         batched = measure_batched(nbm, torch, dev, stream, args, ws, rank)
         if rank == 0 and ws == 1:
             served = measure_served(nbm, stream, args)
             fp64_path = measure_fp64_path(nbm, torch, dev, stream, args)
+            if args.config1_steps > 0:
+                config1 = measure_config1_run(nbm, torch, dev, stream, args)
     if rank == 0:
         cfg = _config(args.workload, w, {
             "force_prec": 64 if args.fp64 else 32,
@@ -819,6 +872,7 @@ def run_ours(args):
             "batched": batched,
             "served": served,
             "fp64_path": fp64_path,
+            "config1_run": config1,
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -844,6 +898,8 @@ def main(argv=None):
     ap.add_argument("--per-system-steps", type=int, default=5,
                     help="steps each sweep system is timed for alone (0: skip)")
     ap.add_argument("--served-requests", type=int, default=64)
+    ap.add_argument("--config1-steps", type=int, default=10000,
+                    help="steps of the 65,536-element growing-donor run (0: skip)")
     ap.add_argument("--served-steps-div", type=int, default=10)
     ap.add_argument("--per-request-steps", type=int, default=3,
                     help="steps each served request is timed for alone")
