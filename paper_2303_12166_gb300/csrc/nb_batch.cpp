@@ -437,6 +437,7 @@ nb_status Batch::init_(const std::vector<int64_t>& n_per_slot, int64_t arena, in
     NB_TRY(alloc_((void**)&d_.spos, nt * sizeof(float4)));
     NB_TRY(alloc_((void**)&d_.slo, nt * sizeof(float4)));
     NB_TRY(alloc_((void**)&d_.svel, nt * sizeof(float4)));
+    NB_TRY(alloc_((void**)&d_.srlo, nt * sizeof(float)));
     {
         float* base = nullptr;
         NB_TRY(alloc_((void**)&base, 6 * nt * sizeof(float)));

@@ -29,12 +29,15 @@
 // its FP32 value clears a bound on its rounding error; otherwise (and for
 // contacts shallower than 1e-3 (R_i + R_j)^2 in Rs^2 - d^2, where the FP32
 // depth would lose digits) the pair is redone from the FP64 state.  The
-// force magnitude is FP32 with the overlap depth (Rs^2 - d^2)/(Rs + r), so
-// the volume pi (4R + r) depth^2 / 12 suffers no cancellation and its
-// relative error stays ~1e-7.  FP64 throughput on this GPU is a small
-// fraction of FP32, which is why FP64 is kept off the common path.  The
-// FP64 force path and the energy variant (diagnostics) evaluate every
-// candidate in FP64.
+// distance and the overlap depth Rs - r of a contact settled in FP32 are
+// computed in double-float from the double-float positions and radii, the
+// rest of the force magnitude in FP32 with the volume in its depth form
+// pi (2 Rs + r) depth^2 / 12 (no cancellation): an element pressed from all
+// sides gets many large pair forces that nearly cancel, and an FP32 depth
+// (~5e-7 relative error) left ~5e-6 of the net acceleration there.  FP64
+// throughput on this GPU is a small fraction of FP32, which is why FP64 is
+// kept off the common path.  The FP64 force path and the energy variant
+// (diagnostics) evaluate every candidate in FP64.
 #include "nb_device.cuh"
 
 namespace nb {
@@ -159,10 +162,11 @@ __global__ void scatter_kernel(BatchDev b, int kofs) {
     b.spos[slot] = make_float4(b.pj.x[i], b.pj.y[i], b.pj.z[i], (float)R);
     b.slo[slot] = make_float4(b.plo.x[i], b.plo.y[i], b.plo.z[i], (float)b.E[i].y);
     b.svel[slot] = make_float4(b.v32.x[i], b.v32.y[i], b.v32.z[i], __int_as_float(s));
+    b.srlo[slot] = (float)(R - (double)(float)R);
 }
 
 // Insertion sort of every bucket by element index (buckets hold a few
-// elements); the cell ids and FP32 positions move along.
+// elements); the cell ids and the rest of the payload move along.
 __global__ void bucket_sort_kernel(BatchDev b) {
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= b.nbucket) return;
@@ -174,10 +178,12 @@ __global__ void bucket_sort_kernel(BatchDev b) {
     float4* sp = b.spos + base;
     float4* sl = b.slo + base;
     float4* sv = b.svel + base;
+    float* sr = b.srlo + base;
     for (uint32_t u = 1; u < c; ++u) {
         const uint32_t v = s[u];
         const uint64_t vc = sc[u];
         const float4 vp = sp[u], vl = sl[u], vv = sv[u];
+        const float vr = sr[u];
         uint32_t w = u;
         while (w > 0 && s[w - 1] > v) {
             s[w] = s[w - 1];
@@ -185,6 +191,7 @@ __global__ void bucket_sort_kernel(BatchDev b) {
             sp[w] = sp[w - 1];
             sl[w] = sl[w - 1];
             sv[w] = sv[w - 1];
+            sr[w] = sr[w - 1];
             --w;
         }
         s[w] = v;
@@ -192,11 +199,55 @@ __global__ void bucket_sort_kernel(BatchDev b) {
         sp[w] = vp;
         sl[w] = vl;
         sv[w] = vv;
+        sr[w] = vr;
     }
 }
 
 __device__ __forceinline__ float max_abs3(float4 p) {
     return fmaxf(fabsf(p.x), fmaxf(fabsf(p.y), fabsf(p.z)));
+}
+
+// ---- double-float arithmetic (a value as hi + lo, two FP32 numbers): the
+// error-free sum (Knuth's TwoSum) and product (with a fused multiply-add,
+// Dekker's TwoProduct), and the few operations built on them that the
+// contact depth needs.  Each rounds explicitly (no contraction).
+__device__ __forceinline__ void two_sum_ef(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (s, e) -> (h, l) with |l| <= half an ulp of h (|e| small against s)
+__device__ __forceinline__ void df_norm(float s, float e, float& h, float& l) {
+    h = __fadd_rn(s, e);
+    l = __fsub_rn(e, __fsub_rn(h, s));
+}
+
+// (ah + al) + (bh + bl)
+__device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float& h, float& l) {
+    float s, e;
+    two_sum_ef(ah, bh, s, e);
+    df_norm(s, __fadd_rn(e, __fadd_rn(al, bl)), h, l);
+}
+
+// (h + l)^2, dropping l^2
+__device__ __forceinline__ void df_sqr(float h, float l, float& ph, float& pl) {
+    const float p = __fmul_rn(h, h);
+    const float e = __fmaf_rn(h, h, -p);  // exact rounding error of h * h
+    df_norm(p, __fmaf_rn(__fmul_rn(2.f, h), l, e), ph, pl);
+}
+
+// sqrt(ah + al): the FP32 root refined by one Newton step on the exact
+// residual (ah + al) - y^2
+__device__ __forceinline__ void df_sqrt(float ah, float al, float& h, float& l) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(ah));
+    const float p = __fmul_rn(y, y);
+    const float e = __fmaf_rn(y, y, -p);
+    const float res = __fadd_rn(__fsub_rn(__fsub_rn(ah, p), e), al);
+    float inv2y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv2y) : "f"(__fmul_rn(2.f, y)));
+    df_norm(y, __fmul_rn(res, inv2y), h, l);
 }
 
 // Contact of (i, j) from the FP64 state, with the decisions of the direct
@@ -281,6 +332,7 @@ __global__ void __launch_bounds__(128, 8) contact_kernel(BatchDev b, int kofs, u
         Ri = ei.x * ((int64_t)i < dend ? scale : 1.0);
     }
     const float Rif = pi4.w;
+    const float Rilo = b.srlo[t];
     const float gif = li4.w;
     const float mi = max_abs3(pi4);
     const float vmi = max_abs3(vi4);
@@ -350,8 +402,38 @@ __global__ void __launch_bounds__(128, 8) contact_kernel(BatchDev b, int kofs, u
                                                    inv_m, ax, ay, az, eax, eay, eaz, er);
                         continue;
                     }
-                    const float r = sqrtf(d2);
-                    const float depth = gap2 / (Rs + r);
+                    // The distance and the depth Rs - r in double-float: the
+                    // many large pair forces of an element pressed from all
+                    // sides nearly cancel, and an FP32 depth (and distance)
+                    // left ~5e-6 of its net acceleration after 10,000 steps of
+                    // the growing 65,536-element donor; with these two in
+                    // double-float, ~2e-7 (the rest of the magnitude stays
+                    // FP32: its rounding is common to a star's pairs or is not
+                    // amplified).
+                    float r, depth;
+                    {
+                        float hx, lx, hy, ly, hz, lz, s2h, s2l, th, tl;
+                        {
+                            float s, e;
+                            two_sum_ef(pj.x, -pi4.x, s, e);
+                            df_norm(s, __fadd_rn(e, __fsub_rn(lj4.x, li4.x)), hx, lx);
+                            two_sum_ef(pj.y, -pi4.y, s, e);
+                            df_norm(s, __fadd_rn(e, __fsub_rn(lj4.y, li4.y)), hy, ly);
+                            two_sum_ef(pj.z, -pi4.z, s, e);
+                            df_norm(s, __fadd_rn(e, __fsub_rn(lj4.z, li4.z)), hz, lz);
+                        }
+                        df_sqr(hx, lx, s2h, s2l);
+                        df_sqr(hy, ly, th, tl);
+                        df_add(s2h, s2l, th, tl, s2h, s2l);
+                        df_sqr(hz, lz, th, tl);
+                        df_add(s2h, s2l, th, tl, s2h, s2l);
+                        float rh, rl, Rh, Rl, dh, dl;
+                        df_sqrt(s2h, s2l, rh, rl);
+                        df_add(Rif, Rilo, pj.w, b.srlo[slot], Rh, Rl);  // Rs
+                        df_add(Rh, Rl, -rh, -rl, dh, dl);              // Rs - r
+                        r = rh;
+                        depth = __fadd_rn(dh, dl);
+                    }
                     const float vol = pif / 12.f * (2.f * Rs + r) * depth * depth;
                     const float g = 0.5f * (gif + lj4.w);
                     const float cf = closing < 0.f ? 1.f : beta;

@@ -155,6 +155,7 @@ struct BatchDev {
     float4* spos;          // ntot: FP32 position and current radius of sorted[slot]
     float4* slo;           // ntot: low FP32 parts of the position, gamma
     float4* svel;          // ntot: FP32 velocity, owning system (int bits)
+    float* srlo;           // ntot: low FP32 part of the current radius (R - (float)R)
     // diagnostics scratch
     double* red;           // per-block partial sums
     double* diag_out;      // final diagnostic values

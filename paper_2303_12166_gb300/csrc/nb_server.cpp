@@ -71,7 +71,7 @@ size_t bytes_per_element_base() {
            + 16        // E
            + 16 + 32   // FP32 copy, duplicated copy
            + 4 + 4 + 8 // owner, key, cell id
-           + 4 + 8 + 16 + 16 + 16  // sorted index, cell, position, low parts, velocity
+           + 4 + 8 + 16 + 16 + 16 + 4  // sorted index, cell, position, low parts, velocity, radius low part
            + 2 * 12    // bucket counts, fills, starts
            + 24        // FP32 low parts and velocity copy
            + 24;       // fixed-point pair sums

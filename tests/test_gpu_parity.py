@@ -188,7 +188,8 @@ def _grown_radii(orc, R0, n_donor, desc, k):
 def test_binary_64k_growing_donor_sampled(nbm, orc):
     """The 65,536-element binary (q = 0.3, eps 0.005, dt 5e-4) with the donor
     growing from 0.9 to 1.15 r_L over 10^4 steps, stepped on the GPU at full
-    size.  At steps 25, 50 and 1,000: the accelerations at the state (x^k,
+    size.  At steps 25, 50, 1,000 and 10,000 (the donor at 1.15 r_L, many
+    elements pressed from all sides): the accelerations at the state (x^k,
     v^k) with the radii of step k, and the stored a^k of the integrator at
     (x^k, v^{k-1/2}), against the oracle on sampled rows -- 320 random rows,
     the donor/accretor index boundary and the 64 donor elements nearest the
@@ -202,7 +203,7 @@ def test_binary_64k_growing_donor_sampled(nbm, orc):
     with _make(nbm, desc, params) as s:
         n = s.n
         k = 0
-        for k_next in (25, 50, 1000):
+        for k_next in (25, 50, 1000, 10000):
             s.step(k_next - k)
             s.sync()
             k = k_next
@@ -216,11 +217,14 @@ def test_binary_64k_growing_donor_sampled(nbm, orc):
             Rk = _grown_radii(orc, oR, nd, desc, k)
             kw = dict(G=1.0, eps=params["eps"], beta=params["beta"])
             ref = orc.forces_rows(rows, x, v, om, Rk, og, **kw)
-            assert rms_rel(a[rows], ref) <= 1e-5
+            # 1e-5 is the stated tolerance; the contact depth and distance in
+            # double-float keep the compressed late states near 3e-7 (FP32
+            # depths reached 5e-6 at step 10,000)
+            assert rms_rel(a[rows], ref) <= 1e-6
             # the integrator's a^k used the half-step velocity v^{k-1/2}
             vh = v - 0.5 * dt * a_stored
             ref_h = orc.forces_rows(rows, x, vh, om, Rk, og, **kw)
-            assert rms_rel(a_stored[rows], ref_h) <= 1e-5
+            assert rms_rel(a_stored[rows], ref_h) <= 1e-6
             if k <= 50:
                 # the growth is visible at this tolerance: the initial radii
                 # give accelerations farther off than the tolerance
