@@ -526,17 +526,10 @@ def measure_config1_run(nbm, torch, dev, stream, args):
                     "reaches 1.15 r_L at step 10,000"}
 
 
-def measure_served(nbm, stream, args):
-    """Poisson arrivals (20/s) of sweep runs: element count log-uniform in
-    [4,096, 262,144], donor expansion rate in [0.5, 2]e-5 r_L per step, steps
-    uniform in [1,000, 20,000] divided by --served-steps-div; served by
-    continuous batching (nb_server) under the 150 GB budget.  Compared with
-    the same requests run one at a time through the single-system API with
-    the FP64 diagnostics every step (and without them), each request timed
-    alone for a few steps and charged its full step count."""
-    import synth
-    trace = synth.served_trace(args.served_requests, seed=0, steps_div=args.served_steps_div)
-    budget = int(150e9)
+def _serve(nbm, stream, trace, budget):
+    """One served run of `trace` (arrivals replayed in real time) under an
+    HBM budget of `budget` bytes; returns the results, the admission
+    statistics, the server's shape and its pair configuration."""
     srv = nbm.nb_server_create(budget, 64, 262144, 32, stream)
     try:
         info = nbm.nb_server_info(srv)
@@ -554,11 +547,30 @@ def measure_served(nbm, stream, args):
         adm = nbm.nb_server_stats_read(srv)
     finally:
         nbm.nb_server_destroy(srv)
-    bad = [r for r in res if r["status"] != 0]
+    return res, adm, info, scfg
+
+
+def _served_figures(res):
     lat = np.array([r["t_finish"] - r["t_submit"] for r in res])
     span = max(r["t_finish"] for r in res) - min(r["t_submit"] for r in res)
     pairs = float(sum(r["n"] ** 2 * r["steps"] for r in res))
     steps = float(sum(r["steps"] for r in res))
+    return lat, span, pairs, steps
+
+
+def measure_served(nbm, stream, args):
+    """Poisson arrivals (20/s) of sweep runs: element count log-uniform in
+    [4,096, 262,144], donor expansion rate in [0.5, 2]e-5 r_L per step, steps
+    uniform in [1,000, 20,000] divided by --served-steps-div; served by
+    continuous batching (nb_server) under the 150 GB budget.  Compared with
+    the same requests run one at a time through the single-system API with
+    the FP64 diagnostics every step (and without them), each request timed
+    alone for a few steps and charged its full step count."""
+    import synth
+    trace = synth.served_trace(args.served_requests, seed=0, steps_div=args.served_steps_div)
+    res, adm, info, scfg = _serve(nbm, stream, trace, int(150e9))
+    bad = [r for r in res if r["status"] != 0]
+    lat, span, pairs, steps = _served_figures(res)
     mix_elems = sum(r["desc"]["n_donor"] + r["desc"]["n_accretor"] for r in trace)
 
     # the same requests one at a time (single-system API, the library's
@@ -639,6 +651,27 @@ def measure_served(nbm, stream, args):
            "accuracy": {"requests": acc,
                         "max_force_rms_rel": max((a["force_rms_rel"] for a in acc), default=None),
                         "tolerance": 1e-5}}
+
+    # the same arrivals with steps / 100 under a budget of two of the largest
+    # runs, well below what the mix holds at once: admission binds, queued
+    # runs wait for retirements, and every run still completes
+    if args.served_bound:
+        trace_b = synth.served_trace(args.served_requests, seed=0, steps_div=100)
+        budget_b = 2 * int(adm["max_request_bytes"])
+        res_b, adm_b, _, _ = _serve(nbm, stream, trace_b, budget_b)
+        lat_b, span_b, pairs_b, steps_b = _served_figures(res_b)
+        out["budget_bound"] = {
+            "requests": len(trace_b), "steps_range": [10, 200],
+            "steps_scaled": "config steps [1000, 20000] / 100",
+            "budget_bytes": budget_b,
+            "failed": sum(1 for r in res_b if r["status"] != 0),
+            "p50_latency_s": float(np.percentile(lat_b, 50)),
+            "p99_latency_s": float(np.percentile(lat_b, 99)),
+            "makespan_s": span_b, "value": pairs_b / span_b, "unit": "pairs/s",
+            "system_steps_per_s": steps_b / span_b,
+            "peak_requests_in_flight": adm_b["peak_requests"],
+            "peak_bytes_in_flight": adm_b["peak_bytes"],
+            "admissions_deferred": adm_b["admissions_deferred"]}
     return out
 
 
@@ -901,6 +934,8 @@ def main(argv=None):
     ap.add_argument("--config1-steps", type=int, default=10000,
                     help="steps of the 65,536-element growing-donor run (0: skip)")
     ap.add_argument("--served-steps-div", type=int, default=10)
+    ap.add_argument("--no-served-bound", dest="served_bound", action="store_false",
+                    help="skip the served run under a budget that makes admission bind")
     ap.add_argument("--per-request-steps", type=int, default=3,
                     help="steps each served request is timed for alone")
     ap.add_argument("--pair-cfg", default="",

@@ -522,6 +522,13 @@ nb_status Batch::load(int s, const SystemInit& si, bool defer_forces) {
         c.fx_scale = std::ldexp(1.0, sh);
         c.fx_inv = std::ldexp(1.0, -sh);
         c.fx_scale_f = std::ldexp(1.0f, sh);
+        // the potential pass: each share G m_j / (r + eps) <= G m_j / eps
+        const double pbound = si.eps > 0 ? si.G * msum / si.eps : 0.0;
+        int ph = pbound > 0 ? (int)std::floor(60.0 - std::log2(pbound)) : 120;
+        ph = std::min(120, std::max(-120, ph));
+        c.pot_scale = std::ldexp(1.0, ph);
+        c.pot_inv = std::ldexp(1.0, -ph);
+        c.pot_scale_f = std::ldexp(1.0f, ph);
         fx_ok_[s] = si.eps > 0 && std::sqrt(l2) <= 16384.0 * si.eps ? 1 : 0;
     }
     k_[s] = 0;
@@ -785,7 +792,10 @@ nb_status Batch::plan_pairs_() {
 }
 
 nb_status Batch::launch_pairs_(bool pot, int nitems_limit, const PairItem* list) {
-    const bool sym = prec_ == 32 && cfg_.sym && !pot;
+    // the potential pass runs the symmetric items too where the variant has
+    // a potential form, else the one-sided items
+    const bool sym = prec_ == 32 && cfg_.sym && (!pot || pair_sym_has_pot(cfg_));
+    if (pot) pot_sym_ = sym;
     int n = (int)(sym ? sitems_ : items_).size();
     if (nitems_limit >= 0 && nitems_limit < n) n = nitems_limit;
     if (n == 0) return NB_OK;
@@ -804,7 +814,7 @@ nb_status Batch::launch_pairs_(bool pot, int nitems_limit, const PairItem* list)
         if (fx)
             NB_CU(cudaMemsetAsync(d_.facc.x, 0, 3 * (size_t)d_.ntot * sizeof(unsigned long long),
                                   stream_));
-        NB_CU(launch_pair_sym(d_, tmass_d_, sl, n, cfg_, ctr, stream_));
+        NB_CU(launch_pair_sym(d_, tmass_d_, sl, n, cfg_, pot, ctr, stream_));
     } else if (prec_ == 32) {
         PairCfg c = cfg_;
         c.grid = pot_grid_;
@@ -1179,7 +1189,7 @@ nb_status Batch::diagnostics(int s, nb_diag* out, bool energy) {
     if (s < 0 || s >= nslots() || !sc_[s].active) return set_error(NB_ENOTFOUND, "no system %d", s);
     if (!out) return set_error(NB_EINVAL, "null output");
     if (energy) NB_TRY(eval_forces(0, true, true));
-    NB_CU(launch_diag(d_, s, stream_));
+    NB_CU(launch_diag(d_, s, energy && pot_sym_ && sc_[s].fxp, stream_));
     double v[NB_DIAG_OUT];
     SysMut m{};
     NB_CU(cudaMemcpyAsync(v, d_.diag_out, sizeof v, cudaMemcpyDeviceToHost, stream_));

@@ -217,6 +217,7 @@ private:
     PairItem* ritems_d_ = nullptr;     // the items of a row-range evaluation
     int ritems_cap_ = 0;
     int pot_grid_ = 0;                 // persistent grid of the one-sided list
+    bool pot_sym_ = false;             // the last potential pass ran the symmetric items
     int* counter_d_ = nullptr;
     bool dynamic_ = false;
     bool planned_ = false;

@@ -72,6 +72,11 @@ struct SysConst {
     float fx_scale_f;   // 2^s in FP32
     double fx_scale;    // 2^s
     double fx_inv;      // 2^-s
+    // the same for the potential pass (G m / (r + eps) per share: the bound
+    // G M_sys / eps, scale 2^p keeping it <= 2^60)
+    float pot_scale_f;
+    double pot_scale;
+    double pot_inv;
 };
 
 // Index of partial slot ch of element i (batch index) of system c in `part`.
@@ -184,8 +189,13 @@ cudaError_t launch_pair_f32(const BatchDev& b, const float* tmass, const PairIte
 // Pair term with each unordered pair evaluated once (cfg.sym): items of the
 // layout in SysConst (block against itself: j0 == i0, one-sided; block
 // against later blocks: j0 > i0, both sides).
+// pot: the potential pass (energy diagnostic) with the same items: the
+// potential of systems with SysConst::fxp in facc.x (on the pot_scale), of
+// the others in part.w; rotating j-packed variants only (pair_sym_has_pot)
 cudaError_t launch_pair_sym(const BatchDev& b, const float* tmass, const PairItem* items,
-                            int nitems, const PairCfg& cfg, int* counter, cudaStream_t s);
+                            int nitems, const PairCfg& cfg, bool pot, int* counter,
+                            cudaStream_t s);
+bool pair_sym_has_pot(const PairCfg& cfg);
 int pair_sym_occupancy(const PairCfg& cfg);
 bool pair_cfg_supported(const PairCfg& cfg);
 std::vector<PairCfg> pair_cfgs();         // every built variant
@@ -244,7 +254,8 @@ uint64_t contact_max_buckets();
 //   lobe  [41] their mass  [42] unbound  [43] their mass
 constexpr int NB_DIAG_NV = 22;
 constexpr int NB_DIAG_OUT = 48;
-cudaError_t launch_diag(const BatchDev& b, int sys, cudaStream_t s);
+// pot_fx: the last potential pass left system sys's potential in facc.x
+cudaError_t launch_diag(const BatchDev& b, int sys, bool pot_fx, cudaStream_t s);
 size_t diag_scratch_doubles();
 
 }  // namespace nb

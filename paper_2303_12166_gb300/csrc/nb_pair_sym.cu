@@ -293,6 +293,54 @@ __device__ __forceinline__ void sym_tile_rot(const JTile<TILE>& tj, const f2 (&x
     }
 }
 
+// The potential of the rotating form (the energy diagnostic): each
+// unordered pair once, G m_j / (r + eps) to element i and G m_i / (r + eps)
+// to element j, coincident pairs excluded (as the direct sum does).  Two
+// MUFU and ~12 FP32 operations per evaluation.  The i-side sums go to the
+// x accumulators, the j-side shares to row component 0.
+template <int TILE, int BI, bool JUNI, bool IUNI>
+__device__ __forceinline__ void sym_tile_rot_pot(const JTile<TILE>& tj, const f2 (&xi)[BI],
+                                                 const f2 (&yi)[BI], const f2 (&zi)[BI],
+                                                 const f2 (&gmi)[BI], f2 eps2, f2 (&ap)[BI],
+                                                 float* row, int lane) {
+    static_assert(TILE % 64 == 0, "the rotating form walks groups of 64 j");
+    const f2 floor2 = pk(kD2Floor, kD2Floor);
+    const int next = (lane + 1) & 31;
+#pragma unroll 1
+    for (int g = 0; g < TILE; g += 64) {
+        f2 sp = 0ull;  // j-side potential of the pair this lane holds
+#pragma unroll 8
+        for (int s = 0; s < 32; ++s) {
+            const int j = g + 2 * ((lane + s) & 31);
+            const f2 px = *reinterpret_cast<const f2*>(&tj.x[j]);
+            const f2 py = *reinterpret_cast<const f2*>(&tj.y[j]);
+            const f2 pz = *reinterpret_cast<const f2*>(&tj.z[j]);
+            f2 pm = 0;
+            if (!JUNI) pm = *reinterpret_cast<const f2*>(&tj.m[j]);
+#pragma unroll
+            for (int b = 0; b < BI; ++b) {
+                const f2 dx = sub2(px, xi[b]);
+                const f2 dy = sub2(py, yi[b]);
+                const f2 dz = sub2(pz, zi[b]);
+                const f2 d2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, floor2)));
+                const f2 r = sqrt2(d2);
+                f2 q = rcp2(add2(r, eps2));  // 1 / (r + eps)
+                float d2l, d2h, ql, qh;
+                upk(d2, d2l, d2h);
+                upk(q, ql, qh);
+                q = pk(d2l > kD2Floor ? ql : 0.f, d2h > kD2Floor ? qh : 0.f);
+                ap[b] = JUNI ? add2(ap[b], q) : fma2(q, pm, ap[b]);
+                sp = IUNI ? add2(sp, q) : fma2(q, gmi[b], sp);
+            }
+            if (s < 31) sp = __shfl_sync(0xffffffffu, sp, next);
+        }
+        const int j = g + 2 * ((lane + 31) & 31);
+        *reinterpret_cast<f2*>(&row[0 * (TILE + kRowPad) + j]) = sp;
+        *reinterpret_cast<f2*>(&row[1 * (TILE + kRowPad) + j]) = 0ull;
+        *reinterpret_cast<f2*>(&row[2 * (TILE + kRowPad) + j]) = 0ull;
+    }
+}
+
 // sym_tile (U = 1, 2) or sym_tile_rot (U = 3) for the tile's and the
 // i-block's mass cases
 template <int TILE, int BI, int U, int SHR>
@@ -336,7 +384,7 @@ __device__ __forceinline__ void sym_dispatch(const JTile<TILE>& tj, const f2 (&x
     }
 }
 
-template <int TILE, int BI, int NT, int MINB, int U, bool IPK, int SHR>
+template <int TILE, int BI, int NT, int MINB, int U, bool IPK, int SHR, bool POT = false>
 __global__ void __launch_bounds__(NT, MINB)
     pair_sym_kernel(PosSoA pj, const float4* __restrict__ jd, const float* __restrict__ tmass,
                     const PairItem* __restrict__ items, int nitems,
@@ -349,6 +397,7 @@ __global__ void __launch_bounds__(NT, MINB)
     static_assert(B % TILE == 0, "a block is a whole number of tiles");
     static_assert(!IPK || BI % 2 == 0, "the i-packed form needs an even slot count");
     static_assert(SHR >= 0 && SHR <= BI && !(IPK && SHR), "shared reciprocal: j-packed only");
+    static_assert(!POT || (U == 3 && !IPK), "the potential pass: rotating, j-packed form");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     SymSmem<TILE, BI, NT, IPK>& S = *reinterpret_cast<SymSmem<TILE, BI, NT, IPK>*>(smem_raw);
     __shared__ alignas(8) uint64_t full[kStages];
@@ -488,6 +537,34 @@ __global__ void __launch_bounds__(NT, MINB)
                 } else {
                     tile_pairs_ip<TILE, NP, 0, false, false>(tj, xi, yi, zi, eps2, ax, ay, az, ap);
                 }
+            } else if constexpr (POT) {
+                // the potential (energy diagnostic) in the x accumulators
+                if (both) {
+                    if (m > 0.f) {
+                        if (gI > 0.f)
+                            sym_tile_rot_pot<TILE, NP, true, true>(tj, xi, yi, zi, gmi, eps2, ap,
+                                                                   row, lane);
+                        else
+                            sym_tile_rot_pot<TILE, NP, true, false>(tj, xi, yi, zi, gmi, eps2, ap,
+                                                                    row, lane);
+                    } else {
+                        if (gI > 0.f)
+                            sym_tile_rot_pot<TILE, NP, false, true>(tj, xi, yi, zi, gmi, eps2, ap,
+                                                                    row, lane);
+                        else
+                            sym_tile_rot_pot<TILE, NP, false, false>(tj, xi, yi, zi, gmi, eps2,
+                                                                     ap, row, lane);
+                    }
+                } else if (m > 0.f) {
+                    tile_pairs<TILE, NP, 0, 0, true, true>(tj, xi, yi, zi, eps2, ax, ay, az, ap);
+                } else {
+                    tile_pairs<TILE, NP, 0, 0, false, true>(tj, xi, yi, zi, eps2, ax, ay, az, ap);
+                }
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    ax[p] = ap[p];
+                    ay[p] = az[p] = 0ull;
+                }
             } else {
                 if (both) {
                     // the shared reciprocal needs eps >= 1e-4 (see rcp2_shared)
@@ -544,8 +621,10 @@ __global__ void __launch_bounds__(NT, MINB)
                 last = __shfl_sync(0xffffffffu, last, 0);
                 if (last) {
                     __threadfence_block();
-                    // -G m_i (uniform i-block) and the fixed-point scale 2^s
-                    const float fs = c.fx_scale_f * (gI > 0.f ? -gI : -1.f);
+                    // -G m_i (uniform i-block) and the fixed-point scale 2^s;
+                    // the potential share is +G m_i, on its own scale
+                    const float fs = POT ? c.pot_scale_f * (gI > 0.f ? gI : 1.f)
+                                         : c.fx_scale_f * (gI > 0.f ? -gI : -1.f);
                     const int64_t jg = item.j0 + (int64_t)t * TILE;
                     for (int jj = lane; jj < TILE; jj += 32) {
                         float sx = 0.f, sy = 0.f, sz = 0.f;
@@ -556,8 +635,10 @@ __global__ void __launch_bounds__(NT, MINB)
                             sz += S.row[st][w][2][jj];
                         }
                         fx_add(facc.x + jg + jj, __float2ll_rn(fs * sx));
-                        fx_add(facc.y + jg + jj, __float2ll_rn(fs * sy));
-                        fx_add(facc.z + jg + jj, __float2ll_rn(fs * sz));
+                        if (!POT) {
+                            fx_add(facc.y + jg + jj, __float2ll_rn(fs * sy));
+                            fx_add(facc.z + jg + jj, __float2ll_rn(fs * sz));
+                        }
                     }
                     if (lane == 0) s_cnt[st] = 0;
                     __syncwarp();
@@ -567,7 +648,25 @@ __global__ void __launch_bounds__(NT, MINB)
         }
         if (tid == 0 && !prod_ok) s_abort[parity] = 1;
 
-        if (c.fxp) {
+        if (c.fxp && POT) {
+#pragma unroll
+            for (int b = 0; b < BI; ++b) {
+                const int rel = b * NT + tid;
+                if (rel < item.iend_rel)
+                    fx_add(facc.x + item.i0 + rel,
+                           __double2ll_rn(c.pot_scale * ((double)S.acc[0][b][tid] +
+                                                         (double)S.acc[3][b][tid])));
+            }
+        } else if (POT) {
+            double4_32a* out = part + part_index(c, item.chunk, item.i0);
+#pragma unroll
+            for (int b = 0; b < BI; ++b) {
+                const int rel = b * NT + tid;
+                if (rel < item.iend_rel)
+                    out[rel] = make_double4_32a(
+                        0.0, 0.0, 0.0, (double)S.acc[0][b][tid] + (double)S.acc[3][b][tid]);
+            }
+        } else if (c.fxp) {
             const double fs = c.fx_scale;
 #pragma unroll
             for (int b = 0; b < BI; ++b) {
@@ -626,6 +725,26 @@ cudaError_t launch_sym_t(const BatchDev& b, const float* tmass, const PairItem* 
     return cudaGetLastError();
 }
 
+// the potential pass with a variant's launch shape and work items (the
+// rotating, j-packed forms); the others report cudaErrorNotSupported
+template <int TILE, int BI, int NT, int MINB, int U, bool IPK, int SHR>
+cudaError_t launch_sym_pot_t(const BatchDev& b, const float* tmass, const PairItem* items,
+                             int nitems, int grid, int* counter, cudaStream_t s) {
+    if constexpr (U == 3 && !IPK) {
+        constexpr size_t smem = sizeof(SymSmem<TILE, BI, NT, IPK>);
+        // (the diagnostics that launch it are never captured in a graph)
+        cudaError_t e = cudaFuncSetAttribute(pair_sym_kernel<TILE, BI, NT, MINB, U, IPK, 0, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        pair_sym_kernel<TILE, BI, NT, MINB, U, IPK, 0, true><<<grid, NT, smem, s>>>(
+            b.pj, b.jd, tmass, items, nitems, b.part, b.facc, b.sc, b.sm, counter);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorNotSupported;
+    }
+}
+
 // raises the kernel's dynamic shared-memory limit, then asks for occupancy
 template <int TILE, int BI, int NT, int MINB, int U, bool IPK, int SHR>
 int occupancy_sym() {
@@ -647,16 +766,21 @@ int occupancy_sym() {
      c.ipk == P && c.shr == D)
 
 cudaError_t launch_pair_sym(const BatchDev& b, const float* tmass, const PairItem* items,
-                            int nitems, const PairCfg& c, int* counter, cudaStream_t s) {
+                            int nitems, const PairCfg& c, bool pot, int* counter,
+                            cudaStream_t s) {
     if (nitems <= 0) return cudaSuccess;
     const int grid = c.grid > 0 ? c.grid : nitems;
-#define NB_LAUNCH_SYM(T, B, N, M, U, P, D) \
-    if (NB_SYM_IS(T, B, N, M, U, P, D))    \
-        return launch_sym_t<T, B, N, M, U, P, D>(b, tmass, items, nitems, grid, counter, s);
+#define NB_LAUNCH_SYM(T, B, N, M, U, P, D)                                                     \
+    if (NB_SYM_IS(T, B, N, M, U, P, D))                                                       \
+        return pot ? launch_sym_pot_t<T, B, N, M, U, P, D>(b, tmass, items, nitems, grid,      \
+                                                           counter, s)                        \
+                   : launch_sym_t<T, B, N, M, U, P, D>(b, tmass, items, nitems, grid, counter, s);
     NB_PAIR_SYM_CFGS(NB_LAUNCH_SYM)
 #undef NB_LAUNCH_SYM
     return cudaErrorInvalidValue;
 }
+
+bool pair_sym_has_pot(const PairCfg& c) { return c.sym == 3 && c.ipk == 0; }
 
 int pair_sym_occupancy(const PairCfg& c) {
 #define NB_OCC_SYM(T, B, N, M, U, P, D) \

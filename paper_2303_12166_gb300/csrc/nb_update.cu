@@ -185,7 +185,7 @@ __device__ void block_reduce_store(double (&v)[NVAL], double* dst) {
     }
 }
 
-__global__ void __launch_bounds__(kDiagThreads) diag_pass1_kernel(BatchDev b, int s) {
+__global__ void __launch_bounds__(kDiagThreads) diag_pass1_kernel(BatchDev b, int s, int pot_fx) {
     const SysConst& c = b.sc[s];
     double v[NV];
 #pragma unroll
@@ -218,9 +218,13 @@ __global__ void __launch_bounds__(kDiagThreads) diag_pass1_kernel(BatchDev b, in
             v[17] += m * x.y;
             v[18] += m * x.z;
         }
-        // pair potential: sum_j G m_j/(r+eps) was accumulated in part.w
+        // pair potential sum_j G m_j/(r+eps): the symmetric potential pass's
+        // fixed-point sum, or the one-sided pass's partial slots (w)
         double pot = 0.0;
-        for (int ch = 0; ch < c.nchunks; ++ch) pot += b.part[part_index(c, ch, i)].w;
+        if (pot_fx)
+            pot = (double)(long long)b.facc.x[i] * c.pot_inv;
+        else
+            for (int ch = 0; ch < c.nchunks; ++ch) pot += b.part[part_index(c, ch, i)].w;
         v[19] += -0.5 * m * pot;
         if (c.contacts) v[20] += b.cont[i].w;
         if (!(isfinite(x.x) && isfinite(x.y) && isfinite(x.z) && isfinite(u.x) &&
@@ -456,8 +460,8 @@ cudaError_t launch_sum_forces(const BatchDev& b, int sys, int64_t r0, int64_t co
     return cudaGetLastError();
 }
 
-cudaError_t launch_diag(const BatchDev& b, int sys, cudaStream_t s) {
-    diag_pass1_kernel<<<kDiagBlocks, kDiagThreads, 0, s>>>(b, sys);
+cudaError_t launch_diag(const BatchDev& b, int sys, bool pot_fx, cudaStream_t s) {
+    diag_pass1_kernel<<<kDiagBlocks, kDiagThreads, 0, s>>>(b, sys, pot_fx ? 1 : 0);
     diag_final1_kernel<<<1, 64, 0, s>>>(b, sys, kDiagBlocks);
     diag_pass2_kernel<<<kDiagBlocks, kDiagThreads, 0, s>>>(b, sys);
     diag_final2_kernel<<<1, 32, 0, s>>>(b, kDiagBlocks);

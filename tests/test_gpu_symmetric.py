@@ -167,21 +167,43 @@ def test_symmetric_checkpoint_resume_bitwise(nbm):
     assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
 
 
-def test_symmetric_diagnostics_energy_uses_potential_pass(nbm, orc):
-    """The potential (diagnostics) is a one-sided pass; the symmetric layout
-    of the step passes is rebuilt afterwards."""
-    cfg = _sym_variants()[0]
+@pytest.mark.parametrize("cfg", _sym_variants())
+def test_symmetric_diagnostics_energy(nbm, orc, cfg):
+    """The potential of the energy diagnostic: the rotating variants run it
+    on their own symmetric items (each unordered pair once, fixed-point
+    sums), the others as a one-sided pass; either way E_grav matches the
+    oracle, and the forces of the step passes that follow are unchanged."""
     with _make(nbm, BINARY, BINARY_P) as s:
         s.set_pair_cfg(*cfg)
+        a0 = s.forces()
         d = s.diagnostics()
         a = s.forces()
-        x = s.get_state()[0]
     p = dict(BINARY_P, G=1.0, kappa_gamma=8.0, rl_coeff=0.69)
     ox, ov, om, oR, og = oracle_ic(orc, BINARY, p)
     od = orc.diagnostics(ox, ov, om, oR, og, G=1.0, eps=p["eps"], n_donor=BINARY["n_donor"])
     assert d["e_grav"] == pytest.approx(od["E_grav"], rel=1e-6)
+    assert d["e_rep"] == pytest.approx(od["E_rep"], rel=1e-10)
+    assert np.array_equal(a, a0)
     ref = orc.forces(ox, ov, om, oR, og, G=1.0, eps=p["eps"], beta=p["beta"])
     assert rms_rel(a, ref) <= 1e-5
+
+
+def test_symmetric_potential_mixed_masses_and_coincident_elements(nbm, orc):
+    """Per-element masses (no uniform tile or block), two coincident elements
+    (the pair contributes nothing) and several blocks: the symmetric
+    potential pass's E_grav against the oracle's, for the default variant."""
+    n = 5000
+    x, v = synth.cloud(n, 77, radius=0.4, speed=0.2)
+    x[4321] = x[17]  # coincident, in different blocks
+    m = 0.5 + synth.u01(77, 3, n)
+    desc = dict(n_donor=n // 2, n_accretor=n - n // 2, q=0.5)
+    params = dict(eps=0.003, dt=1e-3, beta=0.35, flags=nbm.NB_GRAVITY_ONLY)
+    mrg = np.stack([m, np.zeros(n), np.zeros(n)], 1)
+    with _make(nbm, desc, params, xv_in=np.concatenate([x, v], 1), mrg_in=mrg) as s:
+        assert s.pair_cfg()["symmetric"] == 3
+        d = s.diagnostics()
+    eg, _ = orc.potential(x, m, np.zeros(n), np.zeros(n), G=1.0, eps=0.003)
+    assert d["e_grav"] == pytest.approx(float(np.sum(eg)), rel=1e-6)
 
 
 @pytest.mark.parametrize("name,nrows", [("binary_64k", 256), ("binary_1m", 128)])
