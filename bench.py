@@ -848,7 +848,8 @@ def run_ours(args):
     if not args.no_extras:
         batched = measure_batched(nbm, torch, dev, stream, args, ws, rank)
         if rank == 0 and ws == 1:
-            served = measure_served(nbm, stream, args)
+            if args.served_requests > 0:
+                served = measure_served(nbm, stream, args)
             fp64_path = measure_fp64_path(nbm, torch, dev, stream, args)
             if args.config1_steps > 0:
                 config1 = measure_config1_run(nbm, torch, dev, stream, args)

@@ -373,7 +373,8 @@ def test_small_softening_runs_one_sided_items(nbm, orc, eps):
     for a binary of extent ~1): the symmetric plan gives the system one-sided
     items summed into partial slots.  The forces still match the oracle, and
     the system gives the same bits alone and in a batch next to a system
-    summed in fixed point."""
+    summed in fixed point; in that batch the potential pass runs both kinds
+    of items in one launch and each system's E_grav matches the oracle's."""
     desc = dict(n_donor=2000, n_accretor=1000, q=0.5, f_donor=0.8, f_accretor=0.5,
                 sigma_v=1e-3, seed=8, stream=0)
     params = dict(eps=eps, dt=5e-4, beta=0.5)
@@ -390,6 +391,18 @@ def test_small_softening_runs_one_sided_items(nbm, orc, eps):
     with nbm.Batch([nbm.nb_desc_default(**BINARY), nbm.nb_desc_default(**desc)],
                    [nbm.nb_params_default(**BINARY_P), nbm.nb_params_default(**params)]) as b:
         assert np.array_equal(b.forces(1), a)
+        # the potential pass of the mixed launch: system 0's symmetric items
+        # (fixed point), system 1's one-sided items (partial slots)
+        d1 = b.diagnostics(1)
+        og1, _ = orc.potential(ox, om, np.zeros(len(om)), np.zeros(len(om)), G=1.0, eps=eps)
+        assert d1["e_grav"] == pytest.approx(float(np.sum(og1)), rel=1e-6)
+        d0 = b.diagnostics(0)
+        p0 = dict(BINARY_P, G=1.0, kappa_gamma=8.0, rl_coeff=0.69)
+        bx, _, bm, _, _ = oracle_ic(orc, BINARY, p0)
+        og0, _ = orc.potential(bx, bm, np.zeros(len(bm)), np.zeros(len(bm)), G=1.0,
+                               eps=BINARY_P["eps"])
+        assert d0["e_grav"] == pytest.approx(float(np.sum(og0)), rel=1e-6)
+        # diagnostics leave the trajectory as it was
         b.step(3)
         b.sync()
         mixed = b.get_state(1)
