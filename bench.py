@@ -299,6 +299,52 @@ def _oracle_sample(w, target_s=10.0, seed_rows=11):
         f"elements ({pairs:.3e} pairs, {el:.1f} s)"), (x, v, m, R, g), el, rows, ref
 
 
+def _oracle_configs():
+    """The FP64 oracle as it stands on the host cores for the other
+    workloads: the 1,024-element binary run in full (100 steps), one step of
+    the 65,536-element growing donor, and 8 systems of the 256-system sweep
+    for 2 steps each, the last extrapolated to the whole sweep per pair."""
+    from oracle import oracle
+    import synth
+    out = {}
+
+    def timed_run(nd, na, q, fd, fa, eps, dt, steps, rate=0.0, cap=-1, seed=0, stream=0):
+        x, v, m, R, g = oracle.make_ic(nd, na, q, f_donor=fd, f_accretor=fa, sigma_v=1e-3,
+                                       seed=seed, stream=stream)
+        t0 = time.perf_counter()
+        oracle.run(x, v, m, R, g, G=1.0, eps=eps, beta=0.5, dt=dt, nsteps=steps, n_donor=nd,
+                   grow_f0=fd, grow_rate=rate, grow_cap=cap)
+        el = time.perf_counter() - t0
+        n = nd + na
+        return el, float(n) * n * (steps + 1)  # a^0 and one pass per step
+
+    el, pairs = timed_run(512, 512, 0.5, 0.8, 0.5, 0.01, 1e-3, 100)
+    out["binary_1k"] = {"steps": 100, "seconds": el, "pairs_per_s": pairs / el,
+                        "steps_per_s": 100 / el, "sample": "the whole run, 101 force passes"}
+    w = WORKLOADS["binary_64k"]
+    el, pairs = timed_run(w[0], w[1], w[2], w[3], w[4], w[5], w[6], 1, w[7], w[8])
+    out["binary_64k"] = {"steps": 1, "seconds": el, "pairs_per_s": pairs / el,
+                         "sample": "one step of the 10,000 (2 force passes)"}
+    systems = synth.sweep_systems(256, seed=0)
+    pick = systems[::32]
+    el = pairs = 0.0
+    for d in pick:
+        e, p_ = timed_run(d["n_donor"], d["n_accretor"], d["q"], d["f_donor"], d["f_accretor"],
+                          SWEEP_PARAMS["eps"], SWEEP_PARAMS["dt"], 2, d["expand_rate"],
+                          d["expand_steps"], d["seed"], d["stream"])
+        el += e
+        pairs += p_
+    mean_pairs = float(np.mean([(d["n_donor"] + d["n_accretor"]) ** 2 for d in systems]))
+    out["sweep_256"] = {"systems_timed": len(pick), "steps_each": 2, "seconds": el,
+                        "pairs_per_s": pairs / el,
+                        "system_steps_per_s": pairs / el / mean_pairs,
+                        "sample": "every 32nd system of the sweep, 2 steps each (3 force "
+                                  "passes); system-steps/s extrapolated per pair to the "
+                                  "whole sweep"}
+    out["cores"] = oracle.num_threads()
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -814,6 +860,7 @@ def run_ours(args):
 
     cpu = None
     accuracy = None
+    oracle_configs = None
     if rank == 0:
         eps, beta = w["eps"], 0.5
         ic = None
@@ -822,6 +869,8 @@ def run_ours(args):
                 w, target_s=args.cpu_seconds)
             cpu = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle",
                    "sample": sample}
+            if not args.no_extras:
+                oracle_configs = _oracle_configs()
             ic = full_ic[2:]
             initial = {"force_rms_rel": _rms_rel(a_initial[rows0], ref0),
                        "force_max_abs_rel": float(np.abs(a_initial[rows0] - ref0).max() /
@@ -897,6 +946,7 @@ def run_ours(args):
                          "kernel": "pair_sym_kernel" if sym else "pair_f32_kernel",
                          "kernel_ms": pair_ms},
             "cpu_baseline": cpu,
+            "oracle_other_workloads": oracle_configs,
             "accuracy": accuracy,
             "e2e": e2e,
             "gpu_launches": int(prof["kernels"]),

@@ -302,7 +302,10 @@ nb_status nb_set_state(nb_system_t sys, const double* xv_in, const double* a_in,
                        const nb_ckpt_meta* meta);
 
 /* Time every built pair-kernel variant on this system's current state
- * (reps launches each, CUDA events) and keep the fastest; best (may be
+ * (reps launches each, CUDA events; a large system times the first two
+ * waves of its persistent grid) and keep the fastest; the variants within
+ * 2 % of the fastest (at most 4) are timed again over whole passes, in two
+ * rounds of reps launches each, and the lowest total wins.  best (may be
  * NULL) receives it.  Results are cached per element count and precision
  * for the life of the process.  The state is not changed. */
 nb_status nb_autotune(nb_system_t sys, int reps, nb_pair_cfg* best);
