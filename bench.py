@@ -537,6 +537,7 @@ def measure_config1_run(nbm, torch, dev, stream, args):
     total, chunk = args.config1_steps, 500
     with nbm.System(desc, params, stream=stream) as sy:
         tuned = sy.autotune(1)
+        lanes = sy.contact_lanes()
         d0 = sy.diagnostics()
         torch.cuda.synchronize(dev)
         ev0 = torch.cuda.Event(enable_timing=True)
@@ -558,7 +559,7 @@ def measure_config1_run(nbm, torch, dev, stream, args):
                       _sample_rows(n, w["n_donor"], 1024, 5), int(meta.step))
     return {"workload": "binary_64k", "steps": total, "ms": ms, "ms_per_step": ms / total,
             "value": float(n) * n * total / (ms * 1e-3), "unit": "pairs/s",
-            "pair_cfg": {k: tuned[k] for k in PAIR_CFG_KEYS},
+            "pair_cfg": {k: tuned[k] for k in PAIR_CFG_KEYS}, "contact_lanes": lanes,
             "r_donor": [float(d0["r_donor"]), float(d1["r_donor"])],
             "donor_past_L1": [int(d0["n_past_L1"]), int(d1["n_past_L1"])],
             "donor_in_accretor_lobe": [int(d0["n_in_accretor_lobe"]),
@@ -751,6 +752,7 @@ def run_ours(args):
         tuned = sysm.pair_cfg()
     else:
         tuned = sysm.autotune(2) if not args.fp64 else sysm.pair_cfg()
+    contact_lanes = sysm.contact_lanes()
     # accelerations at the initial state with the configuration timed below
     # (compared with the oracle after the timed region)
     a_initial = sysm.forces()
@@ -906,6 +908,7 @@ def run_ours(args):
         cfg = _config(args.workload, w, {
             "force_prec": 64 if args.fp64 else 32,
             "pair_cfg": {k: tuned[k] for k in PAIR_CFG_KEYS},
+            "contact_lanes": contact_lanes,
             "l2": f"no flush: per-step working set {working_set / 1e6:.0f} MB > 2 x L2 (129 MB)"
             if flush is None else
             f"L2 flushed (a {2 * L2_BYTES / 1e6:.0f} MB write) before every timed step, each "

@@ -336,6 +336,18 @@ nb_status nb_measure_unit_rates(nb_unit_rates* out, void* stream);
  * sums both sides of every pair into O(N) fixed-point accumulators. */
 nb_status nb_set_pair_cfg(nb_system_t sys, const nb_pair_cfg* cfg);
 nb_status nb_get_pair_cfg(nb_system_t sys, nb_pair_cfg* cfg);
+
+/* Layout of the contact kernel (Eqs. 5/6): lanes = 1, one thread per
+ * element visiting the three z-planes of its 27 neighbour cells in turn, or
+ * 3, three threads per element with one plane each, which spreads the
+ * candidates of densely packed elements over more lanes.  Each plane's
+ * contributions are summed in the same order and the three plane sums are
+ * added in plane order in both layouts, so the forces are the same bits
+ * either way; only the speed differs.  The FP64 force path and the energy
+ * diagnostic always use one thread per element.  NB_EINVAL for other
+ * values.  nb_autotune chooses the faster layout for the system. */
+nb_status nb_set_contact_lanes(nb_system_t sys, int32_t lanes);
+nb_status nb_get_contact_lanes(nb_system_t sys, int32_t* lanes);
 /* The built pair-kernel variants (an implementation detail of this library;
  * the paper has no counterpart).  Writes min(cap, total) of them to out
  * (caller-owned, may be NULL when cap is 0) and the total to *count.  Needs
@@ -386,6 +398,8 @@ nb_status nb_batch_get_state(nb_batch_t b, int32_t sys, double* xv_out, double* 
 nb_status nb_batch_set_state(nb_batch_t b, int32_t sys, const double* xv_in, const double* a_in,
                              const nb_ckpt_meta* meta);
 nb_status nb_batch_set_pair_cfg(nb_batch_t b, const nb_pair_cfg* cfg);
+/* nb_set_contact_lanes for every system of the batch. */
+nb_status nb_batch_set_contact_lanes(nb_batch_t b, int32_t lanes);
 nb_status nb_batch_autotune(nb_batch_t b, int reps, nb_pair_cfg* best);
 nb_status nb_batch_profile(nb_batch_t b, int enable);
 nb_status nb_batch_profile_read(nb_batch_t b, nb_prof* out, int reset);

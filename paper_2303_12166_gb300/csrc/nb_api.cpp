@@ -45,7 +45,14 @@ nb_status guarded(F&& f) {
 // Process-wide tuning cache: (element count, precision, device) -> best
 // variant and its time.
 std::mutex g_tune_mu;
-std::map<std::tuple<int64_t, int, int>, std::pair<nb::PairCfg, double>> g_tune_cache;
+// per (element count, precision, device): the tuned pair variant, its time
+// per pass and the contact layout
+struct Tuned {
+    nb::PairCfg cfg;
+    double ms;
+    int contact_lanes;
+};
+std::map<std::tuple<int64_t, int, int>, Tuned> g_tune_cache;
 
 nb_pair_cfg to_abi(const nb::PairCfg& c, double ms) {
     nb_pair_cfg o{};
@@ -298,8 +305,9 @@ nb_status nb_autotune(nb_system_t sys, int reps, nb_pair_cfg* best) {
             std::lock_guard<std::mutex> g(g_tune_mu);
             auto it = g_tune_cache.find(key);
             if (it != g_tune_cache.end()) {
-                nb_status st = sys->batch.set_pair_cfg(it->second.first);
-                if (st == NB_OK && best) *best = to_abi(it->second.first, it->second.second);
+                nb_status st = sys->batch.set_pair_cfg(it->second.cfg);
+                if (st == NB_OK) st = sys->batch.set_contact_lanes(it->second.contact_lanes);
+                if (st == NB_OK && best) *best = to_abi(it->second.cfg, it->second.ms);
                 return st;
             }
         }
@@ -309,7 +317,7 @@ nb_status nb_autotune(nb_system_t sys, int reps, nb_pair_cfg* best) {
         if (st != NB_OK) return st;
         {
             std::lock_guard<std::mutex> g(g_tune_mu);
-            g_tune_cache[key] = {c, ms};
+            g_tune_cache[key] = Tuned{c, ms, sys->batch.contact_lanes()};
         }
         if (best) *best = to_abi(c, ms);
         return NB_OK;
@@ -324,6 +332,17 @@ nb_status nb_set_pair_cfg(nb_system_t sys, const nb_pair_cfg* cfg) {
                       cfg->symmetric};
         return sys->batch.set_pair_cfg(c);
     });
+}
+
+nb_status nb_set_contact_lanes(nb_system_t sys, int32_t lanes) {
+    if (!sys) return set_error(NB_EINVAL, "null system");
+    return guarded([&] { return sys->batch.set_contact_lanes(lanes); });
+}
+
+nb_status nb_get_contact_lanes(nb_system_t sys, int32_t* lanes) {
+    if (!sys || !lanes) return set_error(NB_EINVAL, "null argument");
+    *lanes = sys->batch.contact_lanes();
+    return NB_OK;
 }
 
 nb_status nb_get_pair_cfg(nb_system_t sys, nb_pair_cfg* cfg) {
@@ -504,6 +523,11 @@ nb_status nb_batch_set_pair_cfg(nb_batch_t b, const nb_pair_cfg* cfg) {
                       cfg->symmetric};
         return b->batch.set_pair_cfg(c);
     });
+}
+
+nb_status nb_batch_set_contact_lanes(nb_batch_t b, int32_t lanes) {
+    if (!b) return set_error(NB_EINVAL, "null batch");
+    return guarded([&] { return b->batch.set_contact_lanes(lanes); });
 }
 
 nb_status nb_batch_autotune(nb_batch_t b, int reps, nb_pair_cfg* best) {

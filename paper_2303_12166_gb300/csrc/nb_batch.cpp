@@ -607,6 +607,19 @@ nb_status Batch::set_pair_cfg(const PairCfg& c) {
     return NB_OK;
 }
 
+nb_status Batch::set_contact_lanes(int lanes) {
+    if (lanes != 1 && lanes != 3)
+        return set_error(NB_EINVAL, "contact lanes per element: 1 or 3, not %d", lanes);
+    if (lanes != contact_lanes_ && graph_exec_) {
+        // a captured step holds the old contact launch
+        cudaGraphExecDestroy(graph_exec_);
+        graph_exec_ = nullptr;
+        graph_n_ = -1;
+    }
+    contact_lanes_ = lanes;
+    return NB_OK;
+}
+
 double Batch::pairs_per_step() const {
     double p = 0;
     for (const SysConst& c : sc_)
@@ -843,7 +856,7 @@ nb_status Batch::contact_pass_(int kofs, bool energy, bool with_keys) {
         NB_CU(launch_cell_keys(d_, kofs, stream_));
         kernels_ += 1;
     }
-    NB_CU(launch_contact(d_, kofs, energy, prec_ == 64, stream_));
+    NB_CU(launch_contact(d_, kofs, energy, prec_ == 64, contact_lanes_, stream_));
     kernels_ += kContactKernels;
     return prof_end_(ev, PH_CONTACT);
 }
@@ -973,6 +986,31 @@ nb_status Batch::autotune(int reps, PairCfg* best, double* best_ms) {
                 best_t = sum[kb] / 2;
             }
         }
+    }
+    // the contact layout (one or three lanes per element): both give the
+    // same bits, so the faster one over two alternating rounds is kept
+    if (st == NB_OK && prec_ == 32 && any_contacts_()) {
+        const int keep_lanes = contact_lanes_;
+        const int lanes_of[2] = {1, 3};
+        double tl[2] = {0.0, 0.0};
+        for (int round = 0; round < 2 && st == NB_OK; ++round)
+            for (int v = 0; v < 2 && st == NB_OK; ++v) {
+                contact_lanes_ = lanes_of[v];
+                if ((st = contact_pass_(0, false, true)) != NB_OK) break;  // warm-up
+                cudaEventRecord(e0, stream_);
+                for (int r = 0; r < reps && st == NB_OK; ++r) st = contact_pass_(0, false, true);
+                cudaEventRecord(e1, stream_);
+                if (st != NB_OK) break;
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    st = set_error(NB_ECUDA, "autotune: %s",
+                                   cudaGetErrorString(cudaGetLastError()));
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                tl[v] += ms;
+            }
+        contact_lanes_ = st == NB_OK ? (tl[1] < tl[0] ? 3 : 1) : keep_lanes;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -120,6 +120,10 @@ public:
     // Pair-kernel configuration (tile, i-blocking, threads).
     nb_status set_pair_cfg(const PairCfg& c);
     const PairCfg& pair_cfg() const { return cfg_; }
+    // Contact-kernel layout: threads per element (1, or 3: one z-plane of the
+    // 27 cells each); the results are the same bits either way.
+    nb_status set_contact_lanes(int lanes);
+    int contact_lanes() const { return contact_lanes_; }
 
     // Enqueue n leap-frog steps of every active system.
     nb_status step(int64_t n);
@@ -220,6 +224,7 @@ private:
     bool pot_sym_ = false;             // the last potential pass ran the symmetric items
     int* counter_d_ = nullptr;
     bool dynamic_ = false;
+    int contact_lanes_ = 1;            // threads per element in the contact kernel
     bool planned_ = false;
     bool consts_dirty_ = true;
     int64_t bytes_ = 0;

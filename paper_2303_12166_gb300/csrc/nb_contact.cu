@@ -20,7 +20,10 @@
 //      share warps and cache lines): visit the 27 surrounding cells in a
 //      fixed order; a candidate must carry the visited cell's id (hash
 //      collisions are skipped) and pass an FP32 distance pre-test on the
-//      FP32 copy with a margin that covers its rounding.
+//      FP32 copy with a margin that covers its rounding.  Or three threads
+//      per element, one z-plane of the 27 cells each (densely packed
+//      elements with many candidates); the sum is taken per plane in both
+//      layouts and the plane sums added in plane order: the same bits.
 // Precision.  Both decisions of a pair -- contact, (R_i + R_j)^2 - d^2 > 0,
 // and closing, d.(v_j - v_i) < 0 -- come out as the direct FP64 sum takes
 // them.  The common case settles them in FP32: d is the difference of the
@@ -307,146 +310,186 @@ __device__ __forceinline__ void contact_fp64(const BatchDev& b, const SysConst& 
 
 // FULL64: every candidate through contact_fp64 in FP64 (the FP64 force path
 // and the diagnostics); ENERGY: also the repulsion energy (implies FULL64).
-template <bool FULL64, bool ENERGY>
-__global__ void __launch_bounds__(128, 8) contact_kernel(BatchDev b, int kofs, uint32_t total_idx) {
-    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= b.blocksum[total_idx]) return;
-    // the element's own payload (in bucket order); of its FP64 state only
-    // the mass unless a pair needs the FP64 decision (rare, loaded there)
-    const uint32_t i = b.sorted[t];
-    const float4 pi4 = b.spos[t];  // hi position, current radius
-    const float4 li4 = b.slo[t];   // lo position, gamma
-    const float4 vi4 = b.svel[t];  // FP32 velocity, system
-    const int s = __float_as_int(vi4.w);
-    const SysConst& c = b.sc[s];
-    const int64_t k = b.sm[s].k + kofs;
-    const double scale = donor_scale(c, k);
-    const int64_t dend = c.off + c.n_donor;
-    const double4_32a xi = b.X[i];
-    double4_32a vi{};
-    double2 ei{};
-    double Ri = 0.0;
-    if (FULL64) {
-        vi = b.V[i];
-        ei = b.E[i];
-        Ri = ei.x * ((int64_t)i < dend ? scale : 1.0);
-    }
-    const float Rif = pi4.w;
-    const float Rilo = b.srlo[t];
-    const float gif = li4.w;
-    const float mi = max_abs3(pi4);
-    const float vmi = max_abs3(vi4);
-    const float inv_m = 1.0f / (float)xi.w;
-    long long cx, cy, cz;
-    unpack_cell(b.scell[t], cx, cy, cz);
-    const uint32_t mask = b.nbucket - 1;
-    const float beta = (float)c.beta;
-    const float pif = 3.14159265358979f;
-
+// LANES: 1 -- one thread per element, the three z-planes of its 27 cells in
+// turn; 3 -- three consecutive threads per element, one plane each (FP32
+// mode only), which spreads an element's candidates over more lanes where
+// elements have many.  Either way the FP32 sum is taken per plane and the
+// three plane sums are added in plane order, so both layouts give the same
+// bits and the layout can be chosen per launch by speed alone.
+template <bool FULL64, bool ENERGY, int LANES>
+__global__ void __launch_bounds__(LANES == 1 ? 128 : 96, LANES == 1 ? 6 : 8)
+    contact_kernel(BatchDev b, int kofs, uint32_t total_idx) {
+    static_assert(LANES == 1 || (LANES == 3 && !FULL64), "three lanes: the FP32 mode only");
+    __shared__ float plane_sum[LANES == 3 ? 96 : 1][3];
+    const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t t = gt / LANES;  // the element, in bucket order
+    const int plane = LANES == 1 ? 0 : (int)(gt % LANES);
+    const bool valid = t < b.blocksum[total_idx];
+    if (LANES == 1 && !valid) return;
+    // the element's FP32 force: its total (one lane) or this lane's plane sum
     float ax = 0.f, ay = 0.f, az = 0.f;
     double eax = 0.0, eay = 0.0, eaz = 0.0, er = 0.0;
-    for (int oz = -1; oz <= 1; ++oz)
-        for (int oy = -1; oy <= 1; ++oy)
-            for (int ox = -1; ox <= 1; ++ox) {
-                const long long nx = cx + ox, ny = cy + oy, nz = cz + oz;
-                if (nx < -kCellLim || ny < -kCellLim || nz < -kCellLim || nx >= kCellLim ||
-                    ny >= kCellLim || nz >= kCellLim)
-                    continue;
-                const uint64_t cell = pack_cell(nx, ny, nz);
-                const uint32_t key = bucket_of(s, cell, mask);
-                const uint32_t beg = b.start[key];
-                const uint32_t end = b.start[key + 1];
-                for (uint32_t slot = beg; slot < end; ++slot) {
-                    const float4 pj = b.spos[slot];
-                    const float dxh = pj.x - pi4.x, dyh = pj.y - pi4.y, dzh = pj.z - pi4.z;
-                    // pre-test on the hi parts; the margin covers their rounding
-                    // (2^-24 relative per coordinate) and that of the radii
-                    const float tol = (Rif + pj.w) * 1.0001f + 2.5e-7f * (mi + max_abs3(pj));
-                    if (dxh * dxh + dyh * dyh + dzh * dzh > tol * tol) continue;
-                    // another cell hashed to this bucket (checked after the distance
-                    // test, which rejects most candidates: a colliding cell's
-                    // elements would otherwise be visited twice)
-                    if (b.scell[slot] != cell) continue;
-                    const float4 vj4 = b.svel[slot];
-                    if (__float_as_int(vj4.w) != s) continue;  // another system
-                    const uint32_t j = b.sorted[slot];
-                    if (j == i) continue;
-                    if (FULL64) {
-                        contact_fp64<true, ENERGY>(b, c, i, j, dend, scale, xi, vi, ei, Ri, inv_m,
-                                                   ax, ay, az, eax, eay, eaz, er);
+    uint32_t i = 0;
+    if (valid) {
+        // the element's own payload (in bucket order); of its FP64 state only
+        // the mass unless a pair needs the FP64 decision (rare, loaded there)
+        i = b.sorted[t];
+        const float4 pi4 = b.spos[t];  // hi position, current radius
+        const float4 li4 = b.slo[t];   // lo position, gamma
+        const float4 vi4 = b.svel[t];  // FP32 velocity, system
+        const int s = __float_as_int(vi4.w);
+        const SysConst& c = b.sc[s];
+        const int64_t k = b.sm[s].k + kofs;
+        const double scale = donor_scale(c, k);
+        const int64_t dend = c.off + c.n_donor;
+        const double4_32a xi = b.X[i];
+        double4_32a vi{};
+        double2 ei{};
+        double Ri = 0.0;
+        if (FULL64) {
+            vi = b.V[i];
+            ei = b.E[i];
+            Ri = ei.x * ((int64_t)i < dend ? scale : 1.0);
+        }
+        const float Rif = pi4.w;
+        const float Rilo = b.srlo[t];
+        const float gif = li4.w;
+        const float mi = max_abs3(pi4);
+        const float vmi = max_abs3(vi4);
+        const float inv_m = 1.0f / (float)xi.w;
+        long long cx, cy, cz;
+        unpack_cell(b.scell[t], cx, cy, cz);
+        const uint32_t mask = b.nbucket - 1;
+        const float beta = (float)c.beta;
+        const float pif = 3.14159265358979f;
+
+        const int oz_lo = LANES == 1 ? -1 : plane - 1;
+        const int oz_hi = LANES == 1 ? 1 : plane - 1;
+        for (int oz = oz_lo; oz <= oz_hi; ++oz) {
+            float px = 0.f, py = 0.f, pz = 0.f;  // this plane's sum
+            for (int oy = -1; oy <= 1; ++oy)
+                for (int ox = -1; ox <= 1; ++ox) {
+                    const long long nx = cx + ox, ny = cy + oy, nz = cz + oz;
+                    if (nx < -kCellLim || ny < -kCellLim || nz < -kCellLim || nx >= kCellLim ||
+                        ny >= kCellLim || nz >= kCellLim)
                         continue;
-                    }
-                    // double-float difference: hi parts exact-ish, lo parts small
-                    const float4 lj4 = b.slo[slot];
-                    const float dx = dxh + (lj4.x - li4.x);
-                    const float dy = dyh + (lj4.y - li4.y);
-                    const float dz = dzh + (lj4.z - li4.z);
-                    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const float Rs = Rif + pj.w;
-                    const float Rs2 = Rs * Rs;
-                    const float gap2 = Rs2 - d2;
-                    // |rounding of gap2| <= ~1.2e-6 Rs^2 near the contact distance
-                    const float eb = 4e-6f * Rs2;
-                    if (gap2 < -eb) continue;  // certainly apart
-                    const float dvx = vj4.x - vi4.x, dvy = vj4.y - vi4.y, dvz = vj4.z - vi4.z;
-                    const float closing = fmaf(dx, dvx, fmaf(dy, dvy, dz * dvz));
-                    // rounding of the FP32 velocities and products
-                    const float cb = 1e-6f * (fabsf(dx) + fabsf(dy) + fabsf(dz)) *
-                                     (vmi + max_abs3(vj4) + 1e-30f);
-                    if (gap2 <= 1e-3f * Rs2 || !(d2 > 0.f) || fabsf(closing) <= cb) {
-                        // ambiguous, very shallow or coincident: from the FP64 state
-                        const double4_32a vi64 = b.V[i];
-                        const double2 ei64 = b.E[i];
-                        const double Ri64 = ei64.x * ((int64_t)i < dend ? scale : 1.0);
-                        contact_fp64<false, false>(b, c, i, j, dend, scale, xi, vi64, ei64, Ri64,
-                                                   inv_m, ax, ay, az, eax, eay, eaz, er);
-                        continue;
-                    }
-                    // The distance and the depth Rs - r in double-float: the
-                    // many large pair forces of an element pressed from all
-                    // sides nearly cancel, and an FP32 depth (and distance)
-                    // left ~5e-6 of its net acceleration after 10,000 steps of
-                    // the growing 65,536-element donor; with these two in
-                    // double-float, ~2e-7 (the rest of the magnitude stays
-                    // FP32: its rounding is common to a star's pairs or is not
-                    // amplified).
-                    float r, depth;
-                    {
-                        float hx, lx, hy, ly, hz, lz, s2h, s2l, th, tl;
-                        {
-                            float s, e;
-                            two_sum_ef(pj.x, -pi4.x, s, e);
-                            df_norm(s, __fadd_rn(e, __fsub_rn(lj4.x, li4.x)), hx, lx);
-                            two_sum_ef(pj.y, -pi4.y, s, e);
-                            df_norm(s, __fadd_rn(e, __fsub_rn(lj4.y, li4.y)), hy, ly);
-                            two_sum_ef(pj.z, -pi4.z, s, e);
-                            df_norm(s, __fadd_rn(e, __fsub_rn(lj4.z, li4.z)), hz, lz);
+                    const uint64_t cell = pack_cell(nx, ny, nz);
+                    const uint32_t key = bucket_of(s, cell, mask);
+                    const uint32_t beg = b.start[key];
+                    const uint32_t end = b.start[key + 1];
+                    for (uint32_t slot = beg; slot < end; ++slot) {
+                        const float4 pj = b.spos[slot];
+                        const float dxh = pj.x - pi4.x, dyh = pj.y - pi4.y, dzh = pj.z - pi4.z;
+                        // pre-test on the hi parts; the margin covers their rounding
+                        // (2^-24 relative per coordinate) and that of the radii
+                        const float tol = (Rif + pj.w) * 1.0001f + 2.5e-7f * (mi + max_abs3(pj));
+                        if (dxh * dxh + dyh * dyh + dzh * dzh > tol * tol) continue;
+                        // another cell hashed to this bucket (checked after the distance
+                        // test, which rejects most candidates: a colliding cell's
+                        // elements would otherwise be visited twice)
+                        if (b.scell[slot] != cell) continue;
+                        const float4 vj4 = b.svel[slot];
+                        if (__float_as_int(vj4.w) != s) continue;  // another system
+                        const uint32_t j = b.sorted[slot];
+                        if (j == i) continue;
+                        if (FULL64) {
+                            contact_fp64<true, ENERGY>(b, c, i, j, dend, scale, xi, vi, ei, Ri,
+                                                       inv_m, px, py, pz, eax, eay, eaz, er);
+                            continue;
                         }
-                        df_sqr(hx, lx, s2h, s2l);
-                        df_sqr(hy, ly, th, tl);
-                        df_add(s2h, s2l, th, tl, s2h, s2l);
-                        df_sqr(hz, lz, th, tl);
-                        df_add(s2h, s2l, th, tl, s2h, s2l);
-                        float rh, rl, Rh, Rl, dh, dl;
-                        df_sqrt(s2h, s2l, rh, rl);
-                        df_add(Rif, Rilo, pj.w, b.srlo[slot], Rh, Rl);  // Rs
-                        df_add(Rh, Rl, -rh, -rl, dh, dl);              // Rs - r
-                        r = rh;
-                        depth = __fadd_rn(dh, dl);
+                        // double-float difference: hi parts exact-ish, lo parts small
+                        const float4 lj4 = b.slo[slot];
+                        const float dx = dxh + (lj4.x - li4.x);
+                        const float dy = dyh + (lj4.y - li4.y);
+                        const float dz = dzh + (lj4.z - li4.z);
+                        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        const float Rs = Rif + pj.w;
+                        const float Rs2 = Rs * Rs;
+                        const float gap2 = Rs2 - d2;
+                        // |rounding of gap2| <= ~1.2e-6 Rs^2 near the contact distance
+                        const float eb = 4e-6f * Rs2;
+                        if (gap2 < -eb) continue;  // certainly apart
+                        const float dvx = vj4.x - vi4.x, dvy = vj4.y - vi4.y, dvz = vj4.z - vi4.z;
+                        const float closing = fmaf(dx, dvx, fmaf(dy, dvy, dz * dvz));
+                        // rounding of the FP32 velocities and products
+                        const float cb = 1e-6f * (fabsf(dx) + fabsf(dy) + fabsf(dz)) *
+                                         (vmi + max_abs3(vj4) + 1e-30f);
+                        if (gap2 <= 1e-3f * Rs2 || !(d2 > 0.f) || fabsf(closing) <= cb) {
+                            // ambiguous, very shallow or coincident: from the FP64 state
+                            const double4_32a vi64 = b.V[i];
+                            const double2 ei64 = b.E[i];
+                            const double Ri64 = ei64.x * ((int64_t)i < dend ? scale : 1.0);
+                            contact_fp64<false, false>(b, c, i, j, dend, scale, xi, vi64, ei64,
+                                                       Ri64, inv_m, px, py, pz, eax, eay, eaz,
+                                                       er);
+                            continue;
+                        }
+                        // The distance and the depth Rs - r in double-float: the
+                        // many large pair forces of an element pressed from all
+                        // sides nearly cancel, and an FP32 depth (and distance)
+                        // left ~5e-6 of its net acceleration after 10,000 steps of
+                        // the growing 65,536-element donor; with these two in
+                        // double-float, ~2e-7 (the rest of the magnitude stays
+                        // FP32: its rounding is common to a star's pairs or is not
+                        // amplified).
+                        float r, depth;
+                        {
+                            float hx, lx, hy, ly, hz, lz, s2h, s2l, th, tl;
+                            {
+                                float s, e;
+                                two_sum_ef(pj.x, -pi4.x, s, e);
+                                df_norm(s, __fadd_rn(e, __fsub_rn(lj4.x, li4.x)), hx, lx);
+                                two_sum_ef(pj.y, -pi4.y, s, e);
+                                df_norm(s, __fadd_rn(e, __fsub_rn(lj4.y, li4.y)), hy, ly);
+                                two_sum_ef(pj.z, -pi4.z, s, e);
+                                df_norm(s, __fadd_rn(e, __fsub_rn(lj4.z, li4.z)), hz, lz);
+                            }
+                            df_sqr(hx, lx, s2h, s2l);
+                            df_sqr(hy, ly, th, tl);
+                            df_add(s2h, s2l, th, tl, s2h, s2l);
+                            df_sqr(hz, lz, th, tl);
+                            df_add(s2h, s2l, th, tl, s2h, s2l);
+                            float rh, rl, Rh, Rl, dh, dl;
+                            df_sqrt(s2h, s2l, rh, rl);
+                            df_add(Rif, Rilo, pj.w, b.srlo[slot], Rh, Rl);  // Rs
+                            df_add(Rh, Rl, -rh, -rl, dh, dl);              // Rs - r
+                            r = rh;
+                            depth = __fadd_rn(dh, dl);
+                        }
+                        const float vol = pif / 12.f * (2.f * Rs + r) * depth * depth;
+                        const float g = 0.5f * (gif + lj4.w);
+                        const float cf = closing < 0.f ? 1.f : beta;
+                        const float f = -cf * g * vol * inv_m / r;
+                        px = fmaf(f, dx, px);
+                        py = fmaf(f, dy, py);
+                        pz = fmaf(f, dz, pz);
                     }
-                    const float vol = pif / 12.f * (2.f * Rs + r) * depth * depth;
-                    const float g = 0.5f * (gif + lj4.w);
-                    const float cf = closing < 0.f ? 1.f : beta;
-                    const float f = -cf * g * vol * inv_m / r;
-                    ax = fmaf(f, dx, ax);
-                    ay = fmaf(f, dy, ay);
-                    az = fmaf(f, dz, az);
                 }
-            }
-    if (FULL64)
-        b.cont[i] = make_double4_32a(eax, eay, eaz, er);
-    else
-        b.cont[i] = make_double4_32a(ax, ay, az, 0.0);
+            // the plane sums in plane order (the first: 0 + p, exact)
+            ax += px;
+            ay += py;
+            az += pz;
+        }
+    }
+    if (LANES == 1) {
+        if (FULL64)
+            b.cont[i] = make_double4_32a(eax, eay, eaz, er);
+        else
+            b.cont[i] = make_double4_32a(ax, ay, az, 0.0);
+    } else {
+        // an element's three lanes are consecutive threads of one block
+        plane_sum[threadIdx.x][0] = ax;
+        plane_sum[threadIdx.x][1] = ay;
+        plane_sum[threadIdx.x][2] = az;
+        __syncthreads();
+        if (valid && plane == 0) {
+            const int l = threadIdx.x;
+            b.cont[i] = make_double4_32a(
+                (plane_sum[l][0] + plane_sum[l + 1][0]) + plane_sum[l + 2][0],
+                (plane_sum[l][1] + plane_sum[l + 1][1]) + plane_sum[l + 2][1],
+                (plane_sum[l][2] + plane_sum[l + 1][2]) + plane_sum[l + 2][2], 0.0);
+        }
+    }
 }
 
 }  // namespace
@@ -458,7 +501,7 @@ cudaError_t launch_cell_keys(const BatchDev& b, int kofs, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_contact(const BatchDev& b, int kofs, bool with_energy, bool full64,
+cudaError_t launch_contact(const BatchDev& b, int kofs, bool with_energy, bool full64, int lanes,
                            cudaStream_t s) {
     if (b.ntot == 0) return cudaSuccess;
     const uint32_t nblk = (b.nbucket + kScanBlock - 1) / kScanBlock;
@@ -472,11 +515,14 @@ cudaError_t launch_contact(const BatchDev& b, int kofs, bool with_energy, bool f
     bucket_sort_kernel<<<(b.nbucket + 255) / 256, 256, 0, s>>>(b);
     const unsigned ngc = (unsigned)((b.ntot + 127) / 128);
     if (with_energy)
-        contact_kernel<true, true><<<ngc, 128, 0, s>>>(b, kofs, nblk);
+        contact_kernel<true, true, 1><<<ngc, 128, 0, s>>>(b, kofs, nblk);
     else if (full64)
-        contact_kernel<true, false><<<ngc, 128, 0, s>>>(b, kofs, nblk);
+        contact_kernel<true, false, 1><<<ngc, 128, 0, s>>>(b, kofs, nblk);
+    else if (lanes == 3)
+        contact_kernel<false, false, 3><<<(unsigned)((b.ntot + 31) / 32), 96, 0, s>>>(b, kofs,
+                                                                                    nblk);
     else
-        contact_kernel<false, false><<<ngc, 128, 0, s>>>(b, kofs, nblk);
+        contact_kernel<false, false, 1><<<ngc, 128, 0, s>>>(b, kofs, nblk);
     return cudaGetLastError();
 }
 

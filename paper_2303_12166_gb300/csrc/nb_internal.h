@@ -238,8 +238,10 @@ cudaError_t launch_store_acc(const BatchDev& b, int only, cudaStream_t s);
 // runs the scan, the scatter, the bucket sort and the repulsion with the
 // radii of step k + kofs.
 cudaError_t launch_cell_keys(const BatchDev& b, int kofs, cudaStream_t s);
-// full64: evaluate the force magnitude in FP64 too (the FP64 force path)
-cudaError_t launch_contact(const BatchDev& b, int kofs, bool with_energy, bool full64,
+// full64: evaluate the force magnitude in FP64 too (the FP64 force path);
+// lanes: threads per element (1, or 3 in the FP32 mode: one z-plane of the
+// 27 cells each), the same bits either way
+cudaError_t launch_contact(const BatchDev& b, int kofs, bool with_energy, bool full64, int lanes,
                            cudaStream_t s);
 uint64_t contact_max_buckets();
 

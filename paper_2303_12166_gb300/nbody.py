@@ -140,6 +140,9 @@ _sig("nb_batch_forces", ctypes.c_int, [_P, _I32, _P, ctypes.c_int])
 _sig("nb_batch_diagnostics", ctypes.c_int, [_P, _I32, ctypes.POINTER(nb_diag)])
 _sig("nb_batch_get_state", ctypes.c_int, [_P, _I32, _P, _P, ctypes.POINTER(nb_ckpt_meta)])
 _sig("nb_batch_set_pair_cfg", ctypes.c_int, [_P, ctypes.POINTER(nb_pair_cfg)])
+_sig("nb_batch_set_contact_lanes", ctypes.c_int, [_P, _I32])
+_sig("nb_set_contact_lanes", ctypes.c_int, [_P, _I32])
+_sig("nb_get_contact_lanes", ctypes.c_int, [_P, ctypes.POINTER(_I32)])
 _sig("nb_batch_set_state", ctypes.c_int, [_P, _I32, _P, _P, ctypes.POINTER(nb_ckpt_meta)])
 _sig("nb_batch_autotune", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(nb_pair_cfg)])
 _sig("nb_batch_profile", ctypes.c_int, [_P, ctypes.c_int])
@@ -416,6 +419,16 @@ def nb_get_pair_cfg(h) -> dict:
     return _cfg_dict(c)
 
 
+def nb_set_contact_lanes(h, lanes: int) -> None:
+    _check(_lib.nb_set_contact_lanes(_P(h), int(lanes)), "nb_set_contact_lanes")
+
+
+def nb_get_contact_lanes(h) -> int:
+    v = _I32()
+    _check(_lib.nb_get_contact_lanes(_P(h), ctypes.byref(v)), "nb_get_contact_lanes")
+    return v.value
+
+
 def nb_measure_unit_rates(stream=None) -> dict:
     """MUFU and FP32 issue rates per SM per second on the current device."""
     r = nb_unit_rates()
@@ -538,6 +551,10 @@ def nb_batch_set_pair_cfg(h, tile, i_per_thread, threads, min_blocks, nr_slots=0
     _check(_lib.nb_batch_set_pair_cfg(_P(h), ctypes.byref(c)), "nb_batch_set_pair_cfg")
 
 
+def nb_batch_set_contact_lanes(h, lanes: int) -> None:
+    _check(_lib.nb_batch_set_contact_lanes(_P(h), int(lanes)), "nb_batch_set_contact_lanes")
+
+
 def nb_batch_autotune(h, reps: int = 2) -> dict:
     c = nb_pair_cfg()
     _check(_lib.nb_batch_autotune(_P(h), int(reps), ctypes.byref(c)), "nb_batch_autotune")
@@ -585,6 +602,9 @@ class Batch:
 
     def set_pair_cfg(self, *cfg):
         nb_batch_set_pair_cfg(self.h, *cfg)
+
+    def set_contact_lanes(self, lanes):
+        nb_batch_set_contact_lanes(self.h, lanes)
 
     def autotune(self, reps=2):
         return nb_batch_autotune(self.h, reps)
@@ -726,6 +746,12 @@ class System:
 
     def pair_cfg(self) -> dict:
         return nb_get_pair_cfg(self.h)
+
+    def set_contact_lanes(self, lanes: int):
+        nb_set_contact_lanes(self.h, lanes)
+
+    def contact_lanes(self) -> int:
+        return nb_get_contact_lanes(self.h)
 
     def profile(self, enable: bool = True):
         nb_profile(self.h, enable)
