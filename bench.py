@@ -752,6 +752,8 @@ def run_ours(args):
         tuned = sysm.pair_cfg()
     else:
         tuned = sysm.autotune(2) if not args.fp64 else sysm.pair_cfg()
+    if args.contact_lanes:
+        sysm.set_contact_lanes(args.contact_lanes)
     contact_lanes = sysm.contact_lanes()
     # accelerations at the initial state with the configuration timed below
     # (compared with the oracle after the timed region)
@@ -992,6 +994,8 @@ def main(argv=None):
                     help="skip the served run under a budget that makes admission bind")
     ap.add_argument("--per-request-steps", type=int, default=3,
                     help="steps each served request is timed for alone")
+    ap.add_argument("--contact-lanes", type=int, default=0, choices=[0, 1, 3],
+                    help="contact kernel threads per element (0: the tuner's or the default)")
     ap.add_argument("--pair-cfg", default="",
                     help="tile,i_per_thread,threads,min_blocks,nr_slots,i_packed,shared_rcp[,symmetric] (skips the "
                          "autotuner)")
