@@ -339,13 +339,16 @@ nb_status nb_get_pair_cfg(nb_system_t sys, nb_pair_cfg* cfg);
 
 /* Layout of the contact kernel (Eqs. 5/6): lanes = 1, one thread per
  * element visiting the three z-planes of its 27 neighbour cells in turn, or
- * 3, three threads per element with one plane each, which spreads the
- * candidates of densely packed elements over more lanes.  Each plane's
+ * 3, three threads per element with one plane each, which keeps the GPU busy
+ * when the elements are too few to fill it one thread each; 0 (the default)
+ * chooses per pass: 3 while the elements with contacts fit in one wave of
+ * the one-lane kernel (6 x 128 threads per SM), else 1.  Each plane's
  * contributions are summed in the same order and the three plane sums are
  * added in plane order in both layouts, so the forces are the same bits
  * either way; only the speed differs.  The FP64 force path and the energy
  * diagnostic always use one thread per element.  NB_EINVAL for other
- * values.  nb_autotune chooses the faster layout for the system. */
+ * values.  nb_autotune times both layouts and keeps the faster;
+ * nb_get_contact_lanes returns the selection (0: automatic). */
 nb_status nb_set_contact_lanes(nb_system_t sys, int32_t lanes);
 nb_status nb_get_contact_lanes(nb_system_t sys, int32_t* lanes);
 /* The built pair-kernel variants (an implementation detail of this library;

@@ -608,8 +608,9 @@ nb_status Batch::set_pair_cfg(const PairCfg& c) {
 }
 
 nb_status Batch::set_contact_lanes(int lanes) {
-    if (lanes != 1 && lanes != 3)
-        return set_error(NB_EINVAL, "contact lanes per element: 1 or 3, not %d", lanes);
+    if (lanes != 0 && lanes != 1 && lanes != 3)
+        return set_error(NB_EINVAL, "contact lanes per element: 0 (automatic), 1 or 3, not %d",
+                         lanes);
     if (lanes != contact_lanes_ && graph_exec_) {
         // a captured step holds the old contact launch
         cudaGraphExecDestroy(graph_exec_);
@@ -840,6 +841,19 @@ nb_status Batch::launch_pairs_(bool pot, int nitems_limit, const PairItem* list)
     return prof_end_(ev, PH_PAIR);
 }
 
+// The contact layout of the next pass: the selected one, or (automatic) three
+// lanes per element while the elements with contacts fit in one wave of the
+// one-lane kernel (6 blocks of 128 threads per SM): below that the GPU would
+// be partly idle with one thread per element.  Both layouts give the same
+// bits, so this may change from pass to pass.
+int Batch::effective_contact_lanes_() const {
+    if (contact_lanes_ != 0) return contact_lanes_;
+    int64_t elements = 0;
+    for (const SysConst& c : sc_)
+        if (c.active && c.contacts) elements += c.n;
+    return elements <= (int64_t)sm_count_ * 6 * 128 ? 3 : 1;
+}
+
 bool Batch::any_contacts_() const {
     for (const SysConst& c : sc_)
         if (c.active && c.contacts && (c.rmax_donor0 > 0 || c.rmax_acc > 0)) return true;
@@ -856,7 +870,7 @@ nb_status Batch::contact_pass_(int kofs, bool energy, bool with_keys) {
         NB_CU(launch_cell_keys(d_, kofs, stream_));
         kernels_ += 1;
     }
-    NB_CU(launch_contact(d_, kofs, energy, prec_ == 64, contact_lanes_, stream_));
+    NB_CU(launch_contact(d_, kofs, energy, prec_ == 64, effective_contact_lanes_(), stream_));
     kernels_ += kContactKernels;
     return prof_end_(ev, PH_CONTACT);
 }

@@ -121,7 +121,8 @@ public:
     nb_status set_pair_cfg(const PairCfg& c);
     const PairCfg& pair_cfg() const { return cfg_; }
     // Contact-kernel layout: threads per element (1, or 3: one z-plane of the
-    // 27 cells each); the results are the same bits either way.
+    // 27 cells each; 0: chosen per pass from the number of elements); the
+    // results are the same bits either way.
     nb_status set_contact_lanes(int lanes);
     int contact_lanes() const { return contact_lanes_; }
 
@@ -224,7 +225,7 @@ private:
     bool pot_sym_ = false;             // the last potential pass ran the symmetric items
     int* counter_d_ = nullptr;
     bool dynamic_ = false;
-    int contact_lanes_ = 1;            // threads per element in the contact kernel
+    int contact_lanes_ = 0;            // threads per element in the contact kernel (0: automatic)
     bool planned_ = false;
     bool consts_dirty_ = true;
     int64_t bytes_ = 0;
@@ -251,6 +252,7 @@ private:
     nb_status prof_end_(cudaEvent_t a, int phase);
     nb_status prof_collect_();
     bool any_contacts_() const;
+    int effective_contact_lanes_() const;
     nb_status contact_pass_(int kofs, bool energy, bool with_keys);
     // run f with only the listed slots active (flags restored afterwards;
     // the work plan is rebuilt for the subset and again after it)

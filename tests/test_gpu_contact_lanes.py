@@ -36,8 +36,8 @@ def _make(nbm, desc, params, **kw):
 
 def test_lanes_are_validated(nbm):
     with _make(nbm, BINARY, BINARY_P) as s:
-        assert s.contact_lanes() in (1, 3)
-        for bad in (0, 2, 4, -1):
+        assert s.contact_lanes() == 0  # automatic until selected or tuned
+        for bad in (2, 4, -1):
             with pytest.raises(nbm.NbError) as ei:
                 s.set_contact_lanes(bad)
             assert ei.value.status == nbm.NB_EINVAL
@@ -45,6 +45,8 @@ def test_lanes_are_validated(nbm):
         assert s.contact_lanes() == 3
         s.set_contact_lanes(1)
         assert s.contact_lanes() == 1
+        s.set_contact_lanes(0)
+        assert s.contact_lanes() == 0
 
 
 def test_three_lanes_match_oracle(nbm, orc):
@@ -59,11 +61,12 @@ def test_three_lanes_match_oracle(nbm, orc):
 
 def test_layouts_bitwise_same_forces_and_trajectory(nbm):
     """Forces of the initial state, 60 steps (graph-replayed), and a run that
-    changes layout every 20 steps: the same bits throughout."""
+    changes layout every 20 steps: the same bits throughout, and the same as
+    the automatic choice."""
     res = {}
-    for lanes in (1, 3, "switch"):
+    for lanes in (1, 3, 0, "switch"):
         with _make(nbm, BINARY, BINARY_P) as s:
-            s.set_contact_lanes(3 if lanes == 3 else 1)
+            s.set_contact_lanes(1 if lanes == "switch" else lanes)
             a0 = s.forces()
             for k in range(3):
                 if lanes == "switch":
@@ -72,7 +75,7 @@ def test_layouts_bitwise_same_forces_and_trajectory(nbm):
             s.sync()
             xv, a, meta = s.get_state()
             res[lanes] = (a0, xv, a, s.forces())
-    for key in (3, "switch"):
+    for key in (3, 0, "switch"):
         for u, w in zip(res[1], res[key]):
             assert np.array_equal(u, w), key
 
