@@ -409,6 +409,7 @@ def measure_batched(nbm, torch, dev, stream, args, ws, rank):
     params = [nbm.nb_params_default(**SWEEP_PARAMS) for _ in mine]
     b = nbm.Batch(descs, params, stream=stream)
     tuned = b.autotune(3)
+    lanes = b.contact_lanes()
     b.step(3)
     b.sync()
     b.profile(True)
@@ -445,7 +446,7 @@ def measure_batched(nbm, torch, dev, stream, args, ws, rank):
            "value": len(systems) * args.batched_steps / el, "unit": "system-steps/s",
            "pairs_per_s": pairs * args.batched_steps / el,
            "ms_per_step": ms / args.batched_steps,
-           "pair_cfg": {k: tuned[k] for k in PAIR_CFG_KEYS},
+           "pair_cfg": {k: tuned[k] for k in PAIR_CFG_KEYS}, "contact_lanes": lanes,
            "phase_ms": {"pair": prof["pair_ms"], "contact": prof["contact_ms"],
                         "update": prof["update_ms"]},
            "gpu_launches": int(prof["kernels"]),

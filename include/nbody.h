@@ -401,8 +401,10 @@ nb_status nb_batch_get_state(nb_batch_t b, int32_t sys, double* xv_out, double* 
 nb_status nb_batch_set_state(nb_batch_t b, int32_t sys, const double* xv_in, const double* a_in,
                              const nb_ckpt_meta* meta);
 nb_status nb_batch_set_pair_cfg(nb_batch_t b, const nb_pair_cfg* cfg);
-/* nb_set_contact_lanes for every system of the batch. */
+/* nb_set_contact_lanes / nb_get_contact_lanes for the batch (one layout for
+ * all its systems). */
 nb_status nb_batch_set_contact_lanes(nb_batch_t b, int32_t lanes);
+nb_status nb_batch_get_contact_lanes(nb_batch_t b, int32_t* lanes);
 nb_status nb_batch_autotune(nb_batch_t b, int reps, nb_pair_cfg* best);
 nb_status nb_batch_profile(nb_batch_t b, int enable);
 nb_status nb_batch_profile_read(nb_batch_t b, nb_prof* out, int reset);

@@ -530,6 +530,12 @@ nb_status nb_batch_set_contact_lanes(nb_batch_t b, int32_t lanes) {
     return guarded([&] { return b->batch.set_contact_lanes(lanes); });
 }
 
+nb_status nb_batch_get_contact_lanes(nb_batch_t b, int32_t* lanes) {
+    if (!b || !lanes) return set_error(NB_EINVAL, "null argument");
+    *lanes = b->batch.contact_lanes();
+    return NB_OK;
+}
+
 nb_status nb_batch_autotune(nb_batch_t b, int reps, nb_pair_cfg* best) {
     if (!b) return set_error(NB_EINVAL, "null batch");
     return guarded([&]() -> nb_status {

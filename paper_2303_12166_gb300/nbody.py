@@ -141,6 +141,7 @@ _sig("nb_batch_diagnostics", ctypes.c_int, [_P, _I32, ctypes.POINTER(nb_diag)])
 _sig("nb_batch_get_state", ctypes.c_int, [_P, _I32, _P, _P, ctypes.POINTER(nb_ckpt_meta)])
 _sig("nb_batch_set_pair_cfg", ctypes.c_int, [_P, ctypes.POINTER(nb_pair_cfg)])
 _sig("nb_batch_set_contact_lanes", ctypes.c_int, [_P, _I32])
+_sig("nb_batch_get_contact_lanes", ctypes.c_int, [_P, ctypes.POINTER(_I32)])
 _sig("nb_set_contact_lanes", ctypes.c_int, [_P, _I32])
 _sig("nb_get_contact_lanes", ctypes.c_int, [_P, ctypes.POINTER(_I32)])
 _sig("nb_batch_set_state", ctypes.c_int, [_P, _I32, _P, _P, ctypes.POINTER(nb_ckpt_meta)])
@@ -555,6 +556,12 @@ def nb_batch_set_contact_lanes(h, lanes: int) -> None:
     _check(_lib.nb_batch_set_contact_lanes(_P(h), int(lanes)), "nb_batch_set_contact_lanes")
 
 
+def nb_batch_get_contact_lanes(h) -> int:
+    v = _I32()
+    _check(_lib.nb_batch_get_contact_lanes(_P(h), ctypes.byref(v)), "nb_batch_get_contact_lanes")
+    return v.value
+
+
 def nb_batch_autotune(h, reps: int = 2) -> dict:
     c = nb_pair_cfg()
     _check(_lib.nb_batch_autotune(_P(h), int(reps), ctypes.byref(c)), "nb_batch_autotune")
@@ -605,6 +612,9 @@ class Batch:
 
     def set_contact_lanes(self, lanes):
         nb_batch_set_contact_lanes(self.h, lanes)
+
+    def contact_lanes(self):
+        return nb_batch_get_contact_lanes(self.h)
 
     def autotune(self, reps=2):
         return nb_batch_autotune(self.h, reps)
