@@ -342,7 +342,7 @@ nb_status nb_get_pair_cfg(nb_system_t sys, nb_pair_cfg* cfg);
  * 3, three threads per element with one plane each, which keeps the GPU busy
  * when the elements are too few to fill it one thread each; 0 (the default)
  * chooses per pass: 3 while the elements with contacts fit in one wave of
- * the one-lane kernel (6 x 128 threads per SM), else 1.  Each plane's
+ * the one-lane kernel (7 x 128 threads per SM), else 1.  Each plane's
  * contributions are summed in the same order and the three plane sums are
  * added in plane order in both layouts, so the forces are the same bits
  * either way; only the speed differs.  The FP64 force path and the energy

@@ -843,7 +843,7 @@ nb_status Batch::launch_pairs_(bool pot, int nitems_limit, const PairItem* list)
 
 // The contact layout of the next pass: the selected one, or (automatic) three
 // lanes per element while the elements with contacts fit in one wave of the
-// one-lane kernel (6 blocks of 128 threads per SM): below that the GPU would
+// one-lane kernel (7 blocks of 128 threads per SM): below that the GPU would
 // be partly idle with one thread per element.  Both layouts give the same
 // bits, so this may change from pass to pass.
 int Batch::effective_contact_lanes_() const {
@@ -851,7 +851,7 @@ int Batch::effective_contact_lanes_() const {
     int64_t elements = 0;
     for (const SysConst& c : sc_)
         if (c.active && c.contacts) elements += c.n;
-    return elements <= (int64_t)sm_count_ * 6 * 128 ? 3 : 1;
+    return elements <= (int64_t)sm_count_ * 7 * 128 ? 3 : 1;
 }
 
 bool Batch::any_contacts_() const {

@@ -317,7 +317,7 @@ __device__ __forceinline__ void contact_fp64(const BatchDev& b, const SysConst& 
 // three plane sums are added in plane order, so both layouts give the same
 // bits and the layout can be chosen per launch by speed alone.
 template <bool FULL64, bool ENERGY, int LANES>
-__global__ void __launch_bounds__(LANES == 1 ? 128 : 96, LANES == 1 ? 6 : 8)
+__global__ void __launch_bounds__(LANES == 1 ? 128 : 96, LANES == 1 ? 7 : 8)
     contact_kernel(BatchDev b, int kofs, uint32_t total_idx) {
     static_assert(LANES == 1 || (LANES == 3 && !FULL64), "three lanes: the FP32 mode only");
     __shared__ float plane_sum[LANES == 3 ? 96 : 1][3];
