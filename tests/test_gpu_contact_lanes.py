@@ -149,3 +149,26 @@ def test_fp64_path_and_energy_ignore_the_layout(nbm, orc):
     assert rms_rel(got[3][0], ref) <= 1e-12
     od = orc.diagnostics(ox, ov, om, oR, og, G=1.0, eps=p["eps"], n_donor=BINARY["n_donor"])
     assert got[3][1] == pytest.approx(od["E_rep"], rel=1e-10)
+
+
+def test_tuner_picks_a_layout_and_keeps_the_bits(nbm):
+    """nb_autotune times both contact layouts and selects one (1 or 3, no
+    longer automatic); the forces are the same bits as before tuning with
+    the same pair variant, and the batch tuner does the same."""
+    with _make(nbm, BINARY, BINARY_P) as s:
+        s.set_contact_lanes(1)
+        tuned = s.autotune(1)
+        lanes = s.contact_lanes()
+        assert lanes in (1, 3)
+        a_tuned = s.forces()
+        s.set_contact_lanes(4 - lanes)  # the other layout
+        assert np.array_equal(s.forces(), a_tuned)
+    with _make(nbm, BINARY, BINARY_P) as s:
+        s.set_pair_cfg(*[tuned[k] for k in ("tile", "i_per_thread", "threads", "min_blocks",
+                                            "nr_slots", "i_packed", "shared_rcp", "symmetric")])
+        assert np.array_equal(s.forces(), a_tuned)
+    systems = synth.sweep_systems(6, seed=5, nmin=1024, nmax=8192)
+    with nbm.Batch([nbm.nb_desc_default(**x) for x in systems],
+                   [nbm.nb_params_default(**BINARY_P) for _ in systems]) as b:
+        b.autotune(1)
+        assert b.contact_lanes() in (1, 3)
